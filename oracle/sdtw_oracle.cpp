@@ -1,0 +1,363 @@
+// Oracle for subsequence DTW (sDTW) as used by HARU's Read Until.
+//
+// TEST INFRASTRUCTURE ONLY. This file is a plain, slow, single-threaded-per-
+// query CPU restatement of the method, written from the paper. Only the test
+// suite, the smoke check and the benchmark's CPU-baseline leg may load it. It
+// shares no code, header, constant or helper with the CUDA library.
+//
+// What it computes (paper sections):
+//   * Eq. 1 (Section 2.3): gamma(i,j) = delta(i,j) + min(gamma(i-1,j),
+//     gamma(i-1,j-1), gamma(i,j-1)), boundaries gamma(i,0) = inf for i >= 1 and
+//     gamma(0,j) = 0 for j >= 0 (free start), delta = |x_i - y_j| (Manhattan,
+//     the distance of the HARU processing elements, Section 4.3).
+//   * Algorithm 1 (Section 2.3): the full M x N cost matrix, then the minimum
+//     of the last row; the scan keeps the first column on ties (strict "<").
+//   * Algorithm 2 (Section 4.3): the same result with one cost array of M+1
+//     entries swept column by column.
+//   * Section 4.1: reference = k-mer model levels of the forward strand
+//     followed by those of the reverse complement; z-score normalisation of
+//     the reference and of every query; fixed-point scaling by a power of two.
+//
+// Readings where the paper is silent (each also listed in the design doc):
+//   * z-score: population standard deviation; mean and variance accumulated in
+//     double, in blocks of 4096 consecutive samples summed in index order, the
+//     block sums added in index order; z = (float)((x - mean) / sigma);
+//     sigma == 0 is an error.
+//   * quantiser: q = clamp(round_half_even(z * 2^k), -2047, 2047) with the
+//     product formed in float (exact for a power of two).
+//   * int16 form: costs saturate at CAP = 32767 - 2*2047 = 28673, which also
+//     stands for infinity: gamma = min(CAP, delta + min3(...)).
+//   * end column: 0-based index into the concatenated reference; ties go to
+//     the smallest column.
+//
+// Parity pins live in tests/ (brute-force path enumeration, exact copies,
+// closed-form special cases, bounds, algorithm equivalences).
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <thread>
+#include <vector>
+
+namespace {
+
+const int kQmax = 2047;
+const int kCap = 32767 - 2 * kQmax;  // 28673
+const size_t kZBlock = 4096;
+
+inline double dmin3(double a, double b, double c) {
+  double m = a < b ? a : b;
+  return m < c ? m : c;
+}
+inline float fmin3_(float a, float b, float c) {
+  float m = a < b ? a : b;
+  return m < c ? m : c;
+}
+inline int32_t imin3(int32_t a, int32_t b, int32_t c) {
+  int32_t m = a < b ? a : b;
+  return m < c ? m : c;
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_cap(void) { return kCap; }
+int oracle_qmax(void) { return kQmax; }
+
+// ---------------------------------------------------------------- z-score --
+// Section 4.1: (x - mean) / sigma over the whole sequence.
+int oracle_zscore(const float *x, size_t n, float *z) {
+  if (n == 0) return -1;
+  double sum = 0.0;
+  for (size_t b = 0; b < n; b += kZBlock) {
+    size_t e = b + kZBlock < n ? b + kZBlock : n;
+    double bs = 0.0;
+    for (size_t i = b; i < e; ++i) bs += (double)x[i];
+    sum += bs;
+  }
+  double mean = sum / (double)n;
+  double ss = 0.0;
+  for (size_t b = 0; b < n; b += kZBlock) {
+    size_t e = b + kZBlock < n ? b + kZBlock : n;
+    double bs = 0.0;
+    for (size_t i = b; i < e; ++i) {
+      double d = (double)x[i] - mean;
+      double d2 = d * d;
+      bs += d2;
+    }
+    ss += bs;
+  }
+  double var = ss / (double)n;
+  double sigma = std::sqrt(var);
+  if (!(sigma > 0.0)) return -1;
+  for (size_t i = 0; i < n; ++i) z[i] = (float)(((double)x[i] - mean) / sigma);
+  return 0;
+}
+
+// -------------------------------------------------------------- quantiser --
+// Sections 4.1 and 4.3: scale the normalised values by 2^k and keep 16 bits.
+void oracle_quantise(const float *z, size_t n, int scale_log2, int16_t *q) {
+  const float s = (float)(1 << scale_log2);
+  for (size_t i = 0; i < n; ++i) {
+    float p = z[i] * s;
+    float r = std::nearbyint(p);  // default rounding: half to even
+    long v = (long)r;
+    if (v > kQmax) v = kQmax;
+    if (v < -kQmax) v = -kQmax;
+    q[i] = (int16_t)v;
+  }
+}
+
+// ------------------------------------------------------- reference levels --
+// Section 2.2 (k-mer model) and Section 4.1 (forward and reverse strands):
+// out[0 .. n-k] = model[kmer(bases, j)], out[n-k+1 .. 2(n-k+1)-1] = the same
+// over the reverse complement. Bases are 0..3 = A, C, G, T; a k-mer's code
+// reads its first base as the most significant base-4 digit.
+long oracle_ref_levels(const uint8_t *bases, size_t n, const float *model, int k, float *out) {
+  if (k < 1 || n < (size_t)k) return -1;
+  size_t per = n - (size_t)k + 1;
+  for (size_t j = 0; j < per; ++j) {
+    long code = 0;
+    for (int u = 0; u < k; ++u) code = code * 4 + bases[j + u];
+    out[j] = model[code];
+  }
+  // reverse complement: rc[u] = 3 - bases[n - 1 - u]
+  for (size_t j = 0; j < per; ++j) {
+    long code = 0;
+    for (int u = 0; u < k; ++u) code = code * 4 + (3 - bases[n - 1 - (j + u)]);
+    out[per + j] = model[code];
+  }
+  return (long)(2 * per);
+}
+
+// ------------------------------------------------ Algorithm 1: full matrix --
+// C is (M+1) x (N+1) with row 0 = 0 and column 0 = +inf (rows >= 1).
+void oracle_sdtw_full_f64(const double *x, int M, const double *y, long N, double *cost, long *col) {
+  const double inf = std::numeric_limits<double>::infinity();
+  std::vector<double> C((size_t)(M + 1) * (size_t)(N + 1));
+  auto at = [&](long i, long j) -> double & { return C[(size_t)i * (size_t)(N + 1) + (size_t)j]; };
+  for (long j = 0; j <= N; ++j) at(0, j) = 0.0;
+  for (long i = 1; i <= M; ++i) at(i, 0) = inf;
+  for (long i = 1; i <= M; ++i)
+    for (long j = 1; j <= N; ++j)
+      at(i, j) = std::fabs(x[i - 1] - y[j - 1]) + dmin3(at(i - 1, j), at(i - 1, j - 1), at(i, j - 1));
+  double score = inf;
+  long pos = -1;
+  for (long j = 1; j <= N; ++j)
+    if (at(M, j) < score) {
+      score = at(M, j);
+      pos = j - 1;
+    }
+  *cost = score;
+  *col = pos;
+}
+
+void oracle_sdtw_full_i16(const int16_t *x, int M, const int16_t *y, long N, int32_t *cost, long *col) {
+  std::vector<int32_t> C((size_t)(M + 1) * (size_t)(N + 1));
+  auto at = [&](long i, long j) -> int32_t & { return C[(size_t)i * (size_t)(N + 1) + (size_t)j]; };
+  for (long j = 0; j <= N; ++j) at(0, j) = 0;
+  for (long i = 1; i <= M; ++i) at(i, 0) = kCap;
+  for (long i = 1; i <= M; ++i)
+    for (long j = 1; j <= N; ++j) {
+      int32_t d = std::abs((int32_t)x[i - 1] - (int32_t)y[j - 1]);
+      int32_t v = d + imin3(at(i - 1, j), at(i - 1, j - 1), at(i, j - 1));
+      at(i, j) = v < kCap ? v : kCap;
+    }
+  int32_t score = std::numeric_limits<int32_t>::max();
+  long pos = -1;
+  for (long j = 1; j <= N; ++j)
+    if (at(M, j) < score) {
+      score = at(M, j);
+      pos = j - 1;
+    }
+  *cost = score;
+  *col = pos;
+}
+
+// The last row of the full matrix (used by tests for bounds and runner-ups).
+void oracle_sdtw_lastrow_f64(const double *x, int M, const double *y, long N, double *last) {
+  const double inf = std::numeric_limits<double>::infinity();
+  std::vector<double> prev((size_t)N + 1, 0.0), cur((size_t)N + 1);
+  for (int i = 1; i <= M; ++i) {
+    cur[0] = inf;
+    for (long j = 1; j <= N; ++j)
+      cur[j] = std::fabs(x[i - 1] - y[j - 1]) + dmin3(prev[j], prev[j - 1], cur[j - 1]);
+    prev.swap(cur);
+  }
+  for (long j = 0; j < N; ++j) last[j] = prev[(size_t)j + 1];
+}
+
+// ---------------------------------------------- Algorithm 2: rolling array --
+// C[0..M], C[0] is the free-start row (0); C[1..M] start at +inf (column 0).
+// For each reference sample j: walk i = 1..M keeping the north-west value of
+// the previous column, then compare C[M] against the best so far (strict <).
+void oracle_sdtw_roll_f64(const double *x, int M, const double *y, long N, double *cost, long *col,
+                          double *runner_up) {
+  const double inf = std::numeric_limits<double>::infinity();
+  std::vector<double> C((size_t)M + 1, inf);
+  C[0] = 0.0;
+  double score = inf, second = inf;
+  long pos = -1;
+  for (long j = 0; j < N; ++j) {
+    double nw = C[0];  // gamma(0, j-1) = 0
+    for (int i = 1; i <= M; ++i) {
+      double w = C[i];  // gamma(i, j-1)
+      double v = std::fabs(x[i - 1] - y[j]) + dmin3(C[i - 1], nw, w);
+      nw = w;
+      C[i] = v;
+    }
+    double last = C[M];
+    if (last < score) {
+      second = score;
+      score = last;
+      pos = j;
+    } else if (last < second) {
+      second = last;
+    }
+  }
+  *cost = score;
+  *col = pos;
+  if (runner_up) *runner_up = second;
+}
+
+void oracle_sdtw_roll_f32(const float *x, int M, const float *y, long N, float *cost, long *col) {
+  const float inf = std::numeric_limits<float>::infinity();
+  std::vector<float> C((size_t)M + 1, inf);
+  C[0] = 0.0f;
+  float score = inf;
+  long pos = -1;
+  for (long j = 0; j < N; ++j) {
+    float nw = C[0];
+    for (int i = 1; i <= M; ++i) {
+      float w = C[i];
+      float d = std::fabs(x[i - 1] - y[j]);
+      float v = d + fmin3_(C[i - 1], nw, w);
+      nw = w;
+      C[i] = v;
+    }
+    if (C[M] < score) {
+      score = C[M];
+      pos = j;
+    }
+  }
+  *cost = score;
+  *col = pos;
+}
+
+void oracle_sdtw_roll_i16(const int16_t *x, int M, const int16_t *y, long N, int32_t *cost, long *col) {
+  std::vector<int32_t> C((size_t)M + 1, kCap);
+  C[0] = 0;
+  int32_t score = std::numeric_limits<int32_t>::max();
+  long pos = -1;
+  for (long j = 0; j < N; ++j) {
+    int32_t nw = C[0];
+    for (int i = 1; i <= M; ++i) {
+      int32_t w = C[i];
+      int32_t d = std::abs((int32_t)x[i - 1] - (int32_t)y[j]);
+      int32_t v = d + imin3(C[i - 1], nw, w);
+      nw = w;
+      C[i] = v < kCap ? v : kCap;
+    }
+    if (C[M] < score) {
+      score = C[M];
+      pos = j;
+    }
+  }
+  *cost = score;
+  *col = pos;
+}
+
+// ------------------------------------------------------------------ batch --
+// The whole path as the library exposes it: z-score the reference and each
+// query (when asked), quantise for the int16 form, run Algorithm 2 per query.
+// prec: 0 = FP32, 1 = int16 (saturating), 2 = FP64 (inputs are the FP32
+// z-values widened). cost is reported in z units (int16: integer / 2^k).
+// Queries are spread over `threads` worker threads (0 = hardware count).
+// Returns 0, or -1 on invalid input (first offending query in *bad).
+int oracle_batch(int prec, const float *ref, size_t N, int normalize_ref, const float *events,
+                 const uint32_t *offsets, uint32_t nq, int normalize_q, int scale_log2, int threads,
+                 double *cost, int64_t *col, double *runner_up, int32_t *icost, long *bad) {
+  if (N == 0) return -1;
+  std::vector<float> rz(N);
+  if (normalize_ref) {
+    if (oracle_zscore(ref, N, rz.data()) != 0) return -1;
+  } else {
+    std::memcpy(rz.data(), ref, N * sizeof(float));
+  }
+  std::vector<int16_t> rq;
+  std::vector<double> rd;
+  if (prec == 1) {
+    rq.resize(N);
+    oracle_quantise(rz.data(), N, scale_log2, rq.data());
+  }
+  if (prec == 2) {
+    rd.resize(N);
+    for (size_t j = 0; j < N; ++j) rd[j] = (double)rz[j];
+  }
+  for (uint32_t q = 0; q < nq; ++q) {
+    long m = (long)offsets[q + 1] - (long)offsets[q];
+    if (m < 1 || (size_t)m > N) {
+      if (bad) *bad = q;
+      return -1;
+    }
+  }
+  std::atomic<uint32_t> next(0);
+  std::atomic<int> err(0);
+  const double s = (double)(1 << scale_log2);
+  auto worker = [&]() {
+    std::vector<float> qz;
+    std::vector<int16_t> qq;
+    std::vector<double> qd;
+    for (;;) {
+      uint32_t q = next.fetch_add(1);
+      if (q >= nq) break;
+      int M = (int)(offsets[q + 1] - offsets[q]);
+      const float *ev = events + offsets[q];
+      qz.resize((size_t)M);
+      if (normalize_q) {
+        if (oracle_zscore(ev, (size_t)M, qz.data()) != 0) {
+          err.store(1);
+          if (bad) *bad = q;
+          continue;
+        }
+      } else {
+        std::memcpy(qz.data(), ev, (size_t)M * sizeof(float));
+      }
+      long c = -1;
+      if (prec == 0) {
+        float f;
+        oracle_sdtw_roll_f32(qz.data(), M, rz.data(), (long)N, &f, &c);
+        cost[q] = (double)f;
+      } else if (prec == 1) {
+        qq.resize((size_t)M);
+        oracle_quantise(qz.data(), (size_t)M, scale_log2, qq.data());
+        int32_t v;
+        oracle_sdtw_roll_i16(qq.data(), M, rq.data(), (long)N, &v, &c);
+        cost[q] = (double)v / s;
+        if (icost) icost[q] = v;
+      } else {
+        qd.resize((size_t)M);
+        for (int i = 0; i < M; ++i) qd[(size_t)i] = (double)qz[(size_t)i];
+        double v, r;
+        oracle_sdtw_roll_f64(qd.data(), M, rd.data(), (long)N, &v, &c, &r);
+        cost[q] = v;
+        if (runner_up) runner_up[q] = r;
+      }
+      col[q] = (int64_t)c;
+    }
+  };
+  int nt = threads > 0 ? threads : (int)std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if ((uint32_t)nt > nq) nt = (int)(nq > 0 ? nq : 1);
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &t : pool) t.join();
+  return err.load() ? -1 : 0;
+}
+
+}  // extern "C"
