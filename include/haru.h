@@ -1,0 +1,142 @@
+/* libharu: GB300-native subsequence DTW for signal-alignment Read Until.
+ *
+ * The method is HARU's (arXiv 2211.07340): a z-score-normalised query of
+ * nanopore events is aligned against a reference signal built from a k-mer
+ * pore model over both strands of a genome (Section 4.1); the alignment is
+ * subsequence dynamic time warping, Eq. 1 of Section 2.3:
+ *
+ *   gamma(i, j) = |x_i - y_j| + min(gamma(i-1, j), gamma(i-1, j-1), gamma(i, j-1))
+ *   gamma(i, 0) = inf for i >= 1,   gamma(0, j) = 0 for j >= 0 (free start)
+ *
+ * and the answer per query is the minimum of the last row and the first
+ * column that reaches it (Algorithm 1's final scan, Algorithm 2's
+ * per-column update; ties go to the smallest column). Columns are 0-based
+ * indices into the reference as loaded (forward strand first when built by
+ * haru_ref_build).
+ *
+ * Two arithmetic forms:
+ *   HARU_FP32  plain float: delta = |x - y| rounded once, sums rounded once.
+ *   HARU_INT16 the paper's fixed-point idea (Sections 4.1 and 4.3): samples
+ *              are quantised to q = clamp(round_half_even(z * 2^k), -2047,
+ *              2047) and costs saturate at HARU_INT16_CAP, which also stands
+ *              for infinity; the reported cost is the integer cost / 2^k.
+ *
+ * Conventions for every entry point:
+ *   - return 0 (HARU_OK) or a negative HARU_E* code; nothing aborts or traps;
+ *   - the caller owns every buffer it passes; the library copies what it
+ *     keeps (the reference) before returning and keeps no caller pointer;
+ *   - a context is used by one host thread at a time (the serving calls are
+ *     the exception: haru_stream_submit and haru_stream_poll may be called
+ *     from different threads);
+ *   - the first CUDA error seen by a context is sticky: later calls return
+ *     HARU_ECUDA until the context is destroyed.
+ */
+#ifndef HARU_H_
+#define HARU_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HARU_OK 0
+#define HARU_EINVAL (-1)    /* bad argument: empty/NaN/Inf input, M = 0, M > N, M too long, bad scale */
+#define HARU_ENOREF (-2)    /* no reference loaded */
+#define HARU_ENOMEM (-3)    /* device or host allocation failed, or admission budget exceeded */
+#define HARU_EBUSY (-4)     /* serving queue full: poll, then retry */
+#define HARU_ETIMEDOUT (-5) /* a bounded wait (device or host) gave up */
+#define HARU_ECUDA (-6)     /* a CUDA runtime error (sticky per context) */
+
+#define HARU_FP32 0
+#define HARU_INT16 1
+
+#define HARU_INT16_QMAX 2047
+#define HARU_INT16_CAP 28673 /* 32767 - 2 * HARU_INT16_QMAX */
+#define HARU_MAX_QUERY 512   /* longest query (events) one warp strip holds: 32 lanes x 16 rows */
+
+/* haru_sdtw_batch flags */
+#define HARU_ON_DEVICE 1u /* events/offsets/out_* are device pointers, ordered on `stream` */
+#define HARU_RAW 2u       /* events are raw currents: z-score each query on the device first */
+#define HARU_ASYNC 4u     /* HARU_ON_DEVICE only: return after enqueueing; read the status later
+                             with haru_last_status() once the stream has been synchronised */
+
+typedef struct haru_ctx haru_ctx;
+
+typedef struct {
+  int warps_per_cta;        /* warps (queries or query pairs) sharing one reference tile stream; 0 = auto */
+  int tile_cols;            /* reference columns per shared-memory tile, 2048..16384; 0 = auto */
+  int ctas_per_sm;          /* persistent CTAs per SM; 0 = as many as fit */
+  uint32_t wait_limit;      /* spin iterations before a device wait reports HARU_ETIMEDOUT; 0 = default */
+  /* serving */
+  float threshold;          /* accept iff cost <= threshold (z units; int16 compares floor(threshold * 2^k)) */
+  int serve_precision;      /* HARU_FP32 or HARU_INT16 */
+  size_t serve_budget_bytes;/* device memory for in-flight serving requests; 0 = 64 MiB */
+  uint32_t serve_max_batch; /* most requests launched together; 0 = 1024 */
+  uint32_t serve_prefix;    /* events per decision prefix; 0 = 250 (Section 4.1) */
+} haru_config;
+
+/* Fill *cfg with defaults. Returns HARU_OK, or HARU_EINVAL if cfg is NULL. */
+int haru_config_default(haru_config *cfg);
+
+/* Create a context on CUDA device `device` (the device is made current for
+ * every later call on this context). cfg may be NULL (defaults). */
+int haru_create(haru_ctx **out, int device, const haru_config *cfg);
+
+/* Release the context, its device memory and its serving thread. NULL is a no-op. */
+void haru_destroy(haru_ctx *ctx);
+
+/* Load a reference signal of n levels (host pointer, float32).
+ * normalize = 1: levels are raw currents; they are z-scored on the device
+ *   (Section 4.1; population sigma, double-precision sums).
+ * normalize = 0: levels are already z-scores.
+ * scale_log2 = k in [1, 7]: int16 quantisation scale 2^k (Section 4.3 uses 2^5).
+ * Replaces any previous reference. Errors: HARU_EINVAL (n = 0, non-finite
+ * value, zero spread, bad k), HARU_ENOMEM, HARU_ECUDA. */
+int haru_ref_load(haru_ctx *ctx, const float *levels, size_t n, int normalize, int scale_log2);
+
+/* Build the reference on the device from a genome (Sections 2.2 and 4.1):
+ * bases[0..n_bases) in {0,1,2,3} = A,C,G,T; kmer_levels[4^k] the pore model
+ * indexed by the base-4 k-mer code (first base most significant). The signal
+ * is the forward strand's k-mer levels followed by the reverse complement's,
+ * 2 * (n_bases - k + 1) values, then z-scored and quantised as in
+ * haru_ref_load. Host pointers. Errors: HARU_EINVAL (k not in 1..12, genome
+ * shorter than k, base > 3), HARU_ENOMEM, HARU_ECUDA. */
+int haru_ref_build(haru_ctx *ctx, const uint8_t *bases, size_t n_bases, const float *kmer_levels, int k,
+                   int scale_log2);
+
+/* Length of the loaded reference (0 if none). */
+size_t haru_ref_length(const haru_ctx *ctx);
+
+/* Copy the loaded reference back: z-scores (float, n values) and/or the
+ * int16 codes (n values). Either pointer may be NULL. Host pointers. */
+int haru_ref_read(haru_ctx *ctx, float *z, int16_t *q, size_t n);
+
+/* Align a batch of queries against the loaded reference (the hot path).
+ * events[offsets[q] .. offsets[q+1]) are query q's events, float32;
+ * offsets has nq + 1 entries, offsets[0] = 0, non-decreasing.
+ * precision: HARU_FP32 or HARU_INT16.
+ * out_cost[q]: the minimum last-row cost (float; int16: integer cost / 2^k,
+ *   exact). out_col[q]: its first (smallest) 0-based reference column.
+ * flags: HARU_ON_DEVICE (device pointers, work ordered on `stream`, a
+ *   cudaStream_t cast to uintptr_t, 0 = the context's stream), HARU_RAW (z-score
+ *   each query on the device, Section 4.1), HARU_ASYNC.
+ * Without HARU_ASYNC the call returns after the results are in out_*.
+ * Every query needs 1 <= M <= min(N, HARU_MAX_QUERY). nq = 0 is a no-op.
+ * Errors: HARU_EINVAL, HARU_ENOREF, HARU_ENOMEM, HARU_ETIMEDOUT, HARU_ECUDA. */
+int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
+                    float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);
+
+/* Status of the last HARU_ASYNC batch on this context (after the caller has
+ * synchronised its stream): HARU_OK or the first error the device reported. */
+int haru_last_status(haru_ctx *ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char *haru_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HARU_H_ */

@@ -1,0 +1,212 @@
+"""Python binding of libharu (include/haru.h): argument marshalling only.
+
+Every step of the sDTW path (reference synthesis, z-score, quantisation,
+planning, the wavefront kernels) runs in the CUDA library; this module loads
+it with ctypes and passes pointers. There is no CPU fallback: if the library
+is missing the import of `lib()` raises.
+
+Device buffers may be torch tensors (their data_ptr() is passed with
+HARU_ON_DEVICE); host buffers are numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libharu.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "haru.h")
+
+HARU_OK = 0
+HARU_EINVAL = -1
+HARU_ENOREF = -2
+HARU_ENOMEM = -3
+HARU_EBUSY = -4
+HARU_ETIMEDOUT = -5
+HARU_ECUDA = -6
+HARU_FP32 = 0
+HARU_INT16 = 1
+HARU_ON_DEVICE = 1
+HARU_RAW = 2
+HARU_ASYNC = 4
+HARU_INT16_QMAX = 2047
+HARU_INT16_CAP = 28673
+HARU_MAX_QUERY = 512
+
+
+class HaruError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        name = lib().haru_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {name} ({code})" if what else f"{name} ({code})")
+
+
+class haru_config(ctypes.Structure):
+    _fields_ = [
+        ("warps_per_cta", ctypes.c_int),
+        ("tile_cols", ctypes.c_int),
+        ("ctas_per_sm", ctypes.c_int),
+        ("wait_limit", ctypes.c_uint32),
+        ("threshold", ctypes.c_float),
+        ("serve_precision", ctypes.c_int),
+        ("serve_budget_bytes", ctypes.c_size_t),
+        ("serve_max_batch", ctypes.c_uint32),
+        ("serve_prefix", ctypes.c_uint32),
+    ]
+
+
+_lib = None
+
+_SIGS = {
+    "haru_config_default": (ctypes.c_int, [ctypes.POINTER(haru_config)]),
+    "haru_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(haru_config)]),
+    "haru_destroy": (None, [ctypes.c_void_p]),
+    "haru_ref_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
+    "haru_ref_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                      ctypes.c_int, ctypes.c_int]),
+    "haru_ref_length": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "haru_ref_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "haru_sdtw_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_uint32]),
+    "haru_last_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "haru_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def build_library(force: bool = False) -> str:
+    """Compile libharu.so in-tree (nvcc, sm_103a)."""
+    import importlib
+    return importlib.import_module(__name__ + ".build").build(force=force)
+
+
+def lib():
+    """Load libharu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libharu.so not built ({LIB_PATH}); run paper_2211_07340_gb300.build_library()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/haru.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(haru_[a-z_0-9]+)\s*\(", txt, re.M)))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def check(code: int, what: str = ""):
+    if code != HARU_OK:
+        raise HaruError(code, what)
+    return code
+
+
+def default_config(**kw) -> haru_config:
+    cfg = haru_config()
+    check(lib().haru_config_default(ctypes.byref(cfg)))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+class Context:
+    """One libharu context on one CUDA device."""
+
+    def __init__(self, device: int = 0, config: haru_config | None = None, **kw):
+        self._h = ctypes.c_void_p()
+        cfg = config if config is not None else default_config(**kw)
+        check(lib().haru_create(ctypes.byref(self._h), int(device), ctypes.byref(cfg)), "haru_create")
+        self.config = cfg
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().haru_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # reference -----------------------------------------------------------
+    def ref_load(self, levels, normalize: bool = True, scale_log2: int = 6):
+        levels = np.ascontiguousarray(levels, dtype=np.float32)
+        return check(lib().haru_ref_load(self._h, _ptr(levels), levels.shape[0], int(normalize), int(scale_log2)),
+                     "haru_ref_load")
+
+    def ref_build(self, bases, kmer_levels, k: int = 6, scale_log2: int = 6):
+        bases = np.ascontiguousarray(bases, dtype=np.uint8)
+        kmer_levels = np.ascontiguousarray(kmer_levels, dtype=np.float32)
+        return check(lib().haru_ref_build(self._h, _ptr(bases), bases.shape[0], _ptr(kmer_levels), int(k),
+                                          int(scale_log2)), "haru_ref_build")
+
+    @property
+    def ref_length(self) -> int:
+        return int(lib().haru_ref_length(self._h))
+
+    def ref_read(self):
+        n = self.ref_length
+        z = np.empty(n, dtype=np.float32)
+        q = np.empty(n, dtype=np.int16)
+        check(lib().haru_ref_read(self._h, _ptr(z), _ptr(q), n), "haru_ref_read")
+        return z, q
+
+    # batch ----------------------------------------------------------------
+    def sdtw_batch_raw(self, precision: int, events, offsets, nq: int, out_cost, out_col, stream: int = 0,
+                       flags: int = 0) -> int:
+        """Direct call of haru_sdtw_batch with caller-provided buffers; returns the status code."""
+        return int(lib().haru_sdtw_batch(self._h, int(precision), _ptr(events), _ptr(offsets), int(nq),
+                                         _ptr(out_cost), _ptr(out_col), int(stream), int(flags)))
+
+    def sdtw_batch(self, precision: int, events, offsets, raw: bool = True):
+        """Host arrays in, host arrays out: (cost float32[nq], col int64[nq])."""
+        events = np.ascontiguousarray(events, dtype=np.float32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+        nq = offsets.shape[0] - 1
+        cost = np.empty(max(nq, 1), dtype=np.float32)
+        col = np.empty(max(nq, 1), dtype=np.int64)
+        ev = events if events.shape[0] else np.zeros(1, np.float32)
+        check(self.sdtw_batch_raw(precision, ev, offsets, nq, cost, col, 0, HARU_RAW if raw else 0),
+              "haru_sdtw_batch")
+        return cost[:nq], col[:nq]
+
+    def sdtw_batch_device(self, precision: int, events, offsets, out_cost, out_col, stream: int = 0,
+                          raw: bool = True, asynchronous: bool = False):
+        """Device tensors in and out (torch), ordered on `stream` (a cudaStream_t as int)."""
+        nq = int(offsets.shape[0]) - 1
+        flags = HARU_ON_DEVICE | (HARU_RAW if raw else 0) | (HARU_ASYNC if asynchronous else 0)
+        return check(self.sdtw_batch_raw(precision, events, offsets, nq, out_cost, out_col, stream, flags),
+                     "haru_sdtw_batch")
+
+    def last_status(self) -> int:
+        return int(lib().haru_last_status(self._h))

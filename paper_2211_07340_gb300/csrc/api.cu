@@ -1,0 +1,424 @@
+// The C ABI of libharu (declared in include/haru.h): contexts, the reference
+// store, and the batch entry point of the sDTW hot path.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "haru_internal.h"
+
+using haru::Group;
+using haru::Item;
+
+struct haru_ctx {
+  int device = 0;
+  haru_config cfg{};
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int sticky = HARU_OK;
+  int last_status = HARU_OK;
+  std::mutex mu;
+
+  // reference store
+  size_t N = 0;
+  int scale_log2 = 6;
+  float *ref_z = nullptr;       // N
+  uint32_t *img16 = nullptr;    // N + kRefPad, packed (q, q)
+  float *img32 = nullptr;       // N + kRefPad
+  double *stats = nullptr;      // mean, sigma
+  double *partials = nullptr;
+  size_t partials_cap = 0;
+
+  // batch workspace
+  int *d_status = nullptr;      // [0] status, [1] n_groups, [2] n_items, [3] queue
+  Item *items = nullptr;
+  Group *groups = nullptr;
+  uint32_t *img = nullptr;
+  size_t cap_items = 0;
+  float *d_events = nullptr;
+  size_t cap_events = 0;
+  uint32_t *d_offsets = nullptr;
+  float *d_cost = nullptr;
+  int64_t *d_col = nullptr;
+  size_t cap_q = 0;
+};
+
+namespace {
+
+int cuda_fail(haru_ctx *c, cudaError_t e) {
+  if (e == cudaSuccess) return HARU_OK;
+  if (c->sticky == HARU_OK) c->sticky = HARU_ECUDA;
+  return HARU_ECUDA;
+}
+
+#define HARU_CUDA(call)                                \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_);  \
+  } while (0)
+
+template <class T>
+cudaError_t grow(T **p, size_t *cap, size_t need) {
+  if (*cap >= need && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  size_t n = std::max<size_t>(need, 1);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+int pick_warps(const haru_config &cfg) {
+  int w = cfg.warps_per_cta;
+  if (w != 2 && w != 4 && w != 8) w = 8;
+  return w;
+}
+
+int pick_tile(const haru_config &cfg) {
+  int t = cfg.tile_cols;
+  if (t < 2048 || t > haru::kMaxTile) t = 4096;
+  return t;
+}
+
+unsigned long long wait_ns(const haru_config &cfg) {
+  return cfg.wait_limit ? static_cast<unsigned long long>(cfg.wait_limit) * 1000ull : 2000000000ull;
+}
+
+}  // namespace
+
+extern "C" {
+
+int haru_config_default(haru_config *cfg) {
+  if (!cfg) return HARU_EINVAL;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->warps_per_cta = 8;
+  cfg->tile_cols = 4096;
+  cfg->ctas_per_sm = 0;
+  cfg->wait_limit = 0;
+  cfg->threshold = 0.0f;
+  cfg->serve_precision = HARU_INT16;
+  cfg->serve_budget_bytes = 64u << 20;
+  cfg->serve_max_batch = 1024;
+  cfg->serve_prefix = 250;
+  return HARU_OK;
+}
+
+const char *haru_strerror(int code) {
+  switch (code) {
+    case HARU_OK: return "ok";
+    case HARU_EINVAL: return "invalid argument";
+    case HARU_ENOREF: return "no reference loaded";
+    case HARU_ENOMEM: return "out of memory or admission budget";
+    case HARU_EBUSY: return "serving queue full";
+    case HARU_ETIMEDOUT: return "bounded wait timed out";
+    case HARU_ECUDA: return "CUDA error";
+    default: return "unknown error";
+  }
+}
+
+int haru_create(haru_ctx **out, int device, const haru_config *cfg) {
+  if (!out) return HARU_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HARU_EINVAL;
+  haru_ctx *ctx = new (std::nothrow) haru_ctx();
+  if (!ctx) return HARU_ENOMEM;
+  ctx->device = device;
+  if (cfg)
+    ctx->cfg = *cfg;
+  else
+    haru_config_default(&ctx->cfg);
+  int rc = HARU_OK;
+  do {
+    if (cudaSetDevice(device) != cudaSuccess) { rc = HARU_ECUDA; break; }
+    if (cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      rc = HARU_ECUDA;
+      break;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = HARU_ECUDA; break; }
+    if (cudaMalloc(&ctx->d_status, 8 * sizeof(int)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
+    if (cudaMalloc(&ctx->stats, 2 * sizeof(double)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
+  } while (0);
+  if (rc != HARU_OK) {
+    haru_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return HARU_OK;
+}
+
+void haru_destroy(haru_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  void *ptrs[] = {ctx->ref_z, ctx->img16, ctx->img32, ctx->stats, ctx->partials, ctx->d_status, ctx->items,
+                  ctx->groups, ctx->img, ctx->d_events, ctx->d_offsets, ctx->d_cost, ctx->d_col};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+size_t haru_ref_length(const haru_ctx *ctx) { return ctx ? ctx->N : 0; }
+
+// Normalise/quantise `x_dev` (n floats on the device) into the reference store.
+static int ref_install(haru_ctx *ctx, const float *x_dev, size_t n, int normalize, int scale_log2) {
+  cudaStream_t s = ctx->stream;
+  const size_t img_len = n + haru::kRefPad;
+  float *z = nullptr, *i32 = nullptr;
+  uint32_t *i16 = nullptr;
+  cudaError_t e = cudaMalloc(&z, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&i16, img_len * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&i32, img_len * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaFree(z); cudaFree(i16); cudaFree(i32);
+    cudaGetLastError();
+    return HARU_ENOMEM;
+  }
+  const size_t nb = (n + 4095) / 4096;
+  HARU_CUDA(grow(&ctx->partials, &ctx->partials_cap, nb));
+  HARU_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+  HARU_CUDA(cudaMemsetAsync(i16, 0, img_len * sizeof(uint32_t), s));
+  HARU_CUDA(cudaMemsetAsync(i32, 0, img_len * sizeof(float), s));
+  if (normalize) HARU_CUDA(haru::launch_zscore_stats(x_dev, n, ctx->partials, ctx->stats, ctx->d_status, s));
+  HARU_CUDA(haru::launch_ref_finish(x_dev, n, ctx->stats, normalize, scale_log2, z, i16, i32, img_len,
+                                    ctx->d_status, s));
+  int st = 0;
+  HARU_CUDA(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HARU_CUDA(cudaStreamSynchronize(s));
+  if (st != HARU_OK) {
+    cudaFree(z); cudaFree(i16); cudaFree(i32);
+    return st;
+  }
+  cudaFree(ctx->ref_z); cudaFree(ctx->img16); cudaFree(ctx->img32);
+  ctx->ref_z = z;
+  ctx->img16 = i16;
+  ctx->img32 = i32;
+  ctx->N = n;
+  ctx->scale_log2 = scale_log2;
+  return HARU_OK;
+}
+
+int haru_ref_load(haru_ctx *ctx, const float *levels, size_t n, int normalize, int scale_log2) {
+  if (!ctx) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  if (!levels || n == 0 || scale_log2 < 1 || scale_log2 > 7) return HARU_EINVAL;
+  if (n > (size_t)1 << 31) return HARU_EINVAL;
+  HARU_CUDA(cudaSetDevice(ctx->device));
+  float *x = nullptr;
+  if (cudaMalloc(&x, n * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return HARU_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(x, levels, n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+  int rc = e == cudaSuccess ? ref_install(ctx, x, n, normalize, scale_log2) : cuda_fail(ctx, e);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(x);
+  return rc;
+}
+
+int haru_ref_build(haru_ctx *ctx, const uint8_t *bases, size_t n_bases, const float *kmer_levels, int k,
+                   int scale_log2) {
+  if (!ctx) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  if (!bases || !kmer_levels || k < 1 || k > 12 || n_bases < (size_t)k || scale_log2 < 1 || scale_log2 > 7)
+    return HARU_EINVAL;
+  const size_t per = n_bases - k + 1;
+  const size_t n = 2 * per;
+  if (n > (size_t)1 << 31) return HARU_EINVAL;
+  HARU_CUDA(cudaSetDevice(ctx->device));
+  const size_t nmodel = (size_t)1 << (2 * k);
+  uint8_t *db = nullptr;
+  float *dm = nullptr, *x = nullptr;
+  cudaError_t e = cudaMalloc(&db, n_bases);
+  if (e == cudaSuccess) e = cudaMalloc(&dm, nmodel * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&x, n * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaFree(db); cudaFree(dm); cudaFree(x);
+    cudaGetLastError();
+    return HARU_ENOMEM;
+  }
+  int rc = HARU_OK;
+  cudaStream_t s = ctx->stream;
+  e = cudaMemcpyAsync(db, bases, n_bases, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dm, kmer_levels, nmodel * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = haru::launch_ref_levels(db, n_bases, dm, k, x, ctx->d_status, s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess)
+    rc = cuda_fail(ctx, e);
+  else if (st != HARU_OK)
+    rc = st;
+  else
+    rc = ref_install(ctx, x, n, 1, scale_log2);
+  cudaStreamSynchronize(s);
+  cudaFree(db); cudaFree(dm); cudaFree(x);
+  return rc;
+}
+
+int haru_ref_read(haru_ctx *ctx, float *z, int16_t *q, size_t n) {
+  if (!ctx) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  if (ctx->N == 0) return HARU_ENOREF;
+  if (n != ctx->N) return HARU_EINVAL;
+  HARU_CUDA(cudaSetDevice(ctx->device));
+  if (z) HARU_CUDA(cudaMemcpyAsync(z, ctx->ref_z, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  if (q) {
+    std::vector<uint32_t> w(n);
+    HARU_CUDA(cudaMemcpyAsync(w.data(), ctx->img16, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    HARU_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < n; ++i) q[i] = static_cast<int16_t>(w[i] & 0xffffu);
+  }
+  HARU_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HARU_OK;
+}
+
+int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
+                    float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags) {
+  if (!ctx) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  if (precision != HARU_FP32 && precision != HARU_INT16) return HARU_EINVAL;
+  if (ctx->N == 0) return HARU_ENOREF;
+  if (nq == 0) return HARU_OK;
+  if (!events || !offsets || !out_cost || !out_col) return HARU_EINVAL;
+  const bool on_dev = flags & HARU_ON_DEVICE;
+  const bool async = (flags & HARU_ASYNC) && on_dev;
+  const int raw = (flags & HARU_RAW) ? 1 : 0;
+  HARU_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : ctx->stream;
+
+  const uint32_t *d_off = offsets;
+  const float *d_ev = events;
+  float *d_cost = out_cost;
+  int64_t *d_col = out_col;
+  if (!on_dev) {
+    // Host inputs: validate on the host, then stage on the device.
+    const long lim = std::min<long>((long)ctx->N, HARU_MAX_QUERY);
+    if (offsets[0] != 0) return HARU_EINVAL;
+    for (uint32_t q = 0; q < nq; ++q) {
+      if (offsets[q + 1] < offsets[q]) return HARU_EINVAL;
+      long m = (long)offsets[q + 1] - (long)offsets[q];
+      if (m < 1 || m > lim) return HARU_EINVAL;
+    }
+    const size_t ne = offsets[nq];
+    HARU_CUDA(grow(&ctx->d_events, &ctx->cap_events, ne));
+    if (ctx->cap_q < (size_t)nq + 1) {
+      size_t c0 = 0, c1 = 0, c2 = 0;
+      cudaFree(ctx->d_offsets); cudaFree(ctx->d_cost); cudaFree(ctx->d_col);
+      ctx->d_offsets = nullptr; ctx->d_cost = nullptr; ctx->d_col = nullptr;
+      ctx->cap_q = 0;
+      HARU_CUDA(grow(&ctx->d_offsets, &c0, (size_t)nq + 1));
+      HARU_CUDA(grow(&ctx->d_cost, &c1, (size_t)nq + 1));
+      HARU_CUDA(grow(&ctx->d_col, &c2, (size_t)nq + 1));
+      ctx->cap_q = (size_t)nq + 1;
+    }
+    HARU_CUDA(cudaMemcpyAsync(ctx->d_events, events, ne * sizeof(float), cudaMemcpyHostToDevice, s));
+    HARU_CUDA(cudaMemcpyAsync(ctx->d_offsets, offsets, ((size_t)nq + 1) * sizeof(uint32_t),
+                              cudaMemcpyHostToDevice, s));
+    d_off = ctx->d_offsets;
+    d_ev = ctx->d_events;
+    d_cost = ctx->d_cost;
+    d_col = ctx->d_col;
+  }
+  const int warps = pick_warps(ctx->cfg);
+  const int tile = pick_tile(ctx->cfg);
+  const size_t max_items = precision == HARU_INT16 ? ((size_t)nq + 1) / 2 + haru::kMaxS : (size_t)nq;
+  if (ctx->cap_items < max_items) {
+    size_t c0 = 0, c1 = 0, c2 = 0;
+    cudaFree(ctx->items); cudaFree(ctx->groups); cudaFree(ctx->img);
+    ctx->items = nullptr; ctx->groups = nullptr; ctx->img = nullptr;
+    ctx->cap_items = 0;
+    HARU_CUDA(grow(&ctx->items, &c0, max_items));
+    HARU_CUDA(grow(&ctx->groups, &c1, max_items + haru::kMaxS));
+    HARU_CUDA(grow(&ctx->img, &c2, max_items * haru::kImgStride));
+    ctx->cap_items = max_items;
+  }
+  HARU_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4 * sizeof(int), s));
+
+  haru::PlanArgs pa;
+  pa.offsets = d_off;
+  pa.nq = nq;
+  pa.N = (long)ctx->N;
+  pa.pair = precision == HARU_INT16;
+  pa.warps = warps;
+  pa.items = ctx->items;
+  pa.groups = ctx->groups;
+  pa.n_groups = ctx->d_status + 1;
+  pa.n_items = ctx->d_status + 2;
+  pa.queue = ctx->d_status + 3;
+  pa.status = ctx->d_status;
+  HARU_CUDA(haru::launch_plan(pa, s));
+
+  haru::PackArgs ka;
+  ka.events = d_ev;
+  ka.offsets = d_off;
+  ka.items = ctx->items;
+  ka.n_items = ctx->d_status + 2;
+  ka.img = ctx->img;
+  ka.raw = raw;
+  ka.pair = pa.pair;
+  ka.scale_log2 = ctx->scale_log2;
+  ka.status = ctx->d_status;
+  HARU_CUDA(haru::launch_pack(ka, (uint32_t)max_items, s));
+
+  haru::SdtwArgs sa;
+  sa.ref_img = precision == HARU_INT16 ? (const void *)ctx->img16 : (const void *)ctx->img32;
+  sa.N = (long)ctx->N;
+  sa.img = ctx->img;
+  sa.items = ctx->items;
+  sa.groups = ctx->groups;
+  sa.n_groups = ctx->d_status + 1;
+  sa.queue = ctx->d_status + 3;
+  sa.out_cost = d_cost;
+  sa.out_col = d_col;
+  sa.inv_scale = 1.0f / (float)(1 << ctx->scale_log2);
+  sa.tile_cols = tile;
+  sa.warps = warps;
+  sa.wait_ns = wait_ns(ctx->cfg);
+  sa.status = ctx->d_status;
+  int per_sm = ctx->cfg.ctas_per_sm > 0 ? ctx->cfg.ctas_per_sm : haru::sdtw_max_ctas_per_sm(precision, tile, warps);
+  if (per_sm < 1) per_sm = 1;
+  const size_t groups_max = (max_items + warps - 1) / warps + haru::kMaxS;
+  int grid = (int)std::min<size_t>((size_t)ctx->sms * per_sm, groups_max);
+  HARU_CUDA(haru::launch_sdtw(precision, sa, grid, s));
+
+  if (async) {
+    ctx->last_status = HARU_OK;
+    return HARU_OK;
+  }
+  if (!on_dev) {
+    HARU_CUDA(cudaMemcpyAsync(out_cost, d_cost, (size_t)nq * sizeof(float), cudaMemcpyDeviceToHost, s));
+    HARU_CUDA(cudaMemcpyAsync(out_col, d_col, (size_t)nq * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  }
+  int st = 0;
+  HARU_CUDA(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HARU_CUDA(cudaStreamSynchronize(s));
+  ctx->last_status = st;
+  return st;
+}
+
+int haru_last_status(haru_ctx *ctx) {
+  if (!ctx) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  int st = 0;
+  HARU_CUDA(cudaSetDevice(ctx->device));
+  HARU_CUDA(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  ctx->last_status = st;
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,334 @@
+// Device-side preparation: reference synthesis and normalisation (Section
+// 4.1), the batch planner, and per-query normalisation, quantisation and
+// packing into the warp-strip register images the sweep kernels load.
+//
+// z-score reading (the paper does not say how mean and sigma are formed):
+// population sigma; sums in double, in blocks of 4096 consecutive samples
+// added in index order, block sums added in index order; every double
+// operation is an explicitly rounded intrinsic so no contraction occurs;
+// z = (float)((x - mean) / sigma). Quantiser: clamp(rint(z * 2^k), +-2047).
+
+#include <cuda_runtime.h>
+
+#include "haru_internal.h"
+
+namespace haru {
+namespace {
+
+constexpr int kZBlock = 4096;
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+__device__ __forceinline__ int quantise(float z, float s) {
+  int v = __float2int_rn(__fmul_rn(z, s));
+  return v > kQmax ? kQmax : (v < -kQmax ? -kQmax : v);
+}
+
+// ------------------------------------------------------------ reference --
+__global__ void ref_levels_kernel(const uint8_t *bases, size_t n, const float *model, int k, float *out,
+                                  int *status) {
+  const size_t per = n - static_cast<size_t>(k) + 1;
+  for (size_t j = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; j < 2 * per;
+       j += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    long code = 0;
+    bool bad = false;
+    if (j < per) {
+      for (int u = 0; u < k; ++u) {
+        uint8_t b = bases[j + u];
+        bad |= b > 3;
+        code = code * 4 + (b & 3);
+      }
+    } else {
+      const size_t jj = j - per;  // k-mer jj of the reverse complement
+      for (int u = 0; u < k; ++u) {
+        uint8_t b = bases[n - 1 - (jj + u)];
+        bad |= b > 3;
+        code = code * 4 + (3 - (b & 3));
+      }
+    }
+    if (bad) report(status, HARU_EINVAL);
+    out[j] = model[code];
+  }
+}
+
+// One thread per block of kZBlock samples: the block's sum (pass 0) or sum
+// of squared deviations from stats[0] (pass 1), in index order.
+__global__ void block_sums_kernel(const float *x, size_t n, const double *stats, int pass, double *partials) {
+  const size_t b = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  const size_t lo = b * kZBlock;
+  if (lo >= n) return;
+  const size_t hi = lo + kZBlock < n ? lo + kZBlock : n;
+  double acc = 0.0;
+  if (pass == 0) {
+    for (size_t i = lo; i < hi; ++i) acc = __dadd_rn(acc, static_cast<double>(x[i]));
+  } else {
+    const double mean = stats[0];
+    for (size_t i = lo; i < hi; ++i) {
+      const double d = __dsub_rn(static_cast<double>(x[i]), mean);
+      acc = __dadd_rn(acc, __dmul_rn(d, d));
+    }
+  }
+  partials[b] = acc;
+}
+
+// Single thread: add the block sums in order; pass 0 -> mean, pass 1 -> sigma.
+__global__ void finish_sums_kernel(const double *partials, size_t nblocks, size_t n, int pass, double *stats,
+                                   int *status) {
+  double acc = 0.0;
+  for (size_t b = 0; b < nblocks; ++b) acc = __dadd_rn(acc, partials[b]);
+  if (pass == 0) {
+    stats[0] = __ddiv_rn(acc, static_cast<double>(n));
+    if (!finite_d(stats[0])) report(status, HARU_EINVAL);
+  } else {
+    const double sigma = __dsqrt_rn(__ddiv_rn(acc, static_cast<double>(n)));
+    stats[1] = sigma;
+    if (!(sigma > 0.0) || !finite_d(sigma)) report(status, HARU_EINVAL);
+  }
+}
+
+__global__ void ref_finish_kernel(const float *x, size_t n, const double *stats, int normalize, float s,
+                                  float *z, uint32_t *img16, float *img32, int *status) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    float v = x[i];
+    if (normalize) {
+      const double mean = stats[0], sigma = stats[1];
+      v = __double2float_rn(__ddiv_rn(__dsub_rn(static_cast<double>(v), mean), sigma));
+    }
+    if (!isfinite(v)) report(status, HARU_EINVAL);
+    const int q = quantise(v, s);
+    z[i] = v;
+    img16[i] = (static_cast<uint32_t>(q) & 0xffffu) | (static_cast<uint32_t>(q) << 16);
+    img32[i] = v;
+  }
+}
+
+// --------------------------------------------------------------- planner --
+__device__ __forceinline__ int strip_rows(const uint32_t *off, uint32_t q, long N, int *status) {
+  const uint32_t m = off[q + 1] - off[q];
+  const long lim = N < HARU_MAX_QUERY ? N : HARU_MAX_QUERY;
+  if (m < 1 || static_cast<long>(m) > lim) {
+    report(status, HARU_EINVAL);
+    return 0;
+  }
+  return static_cast<int>((m + 31) / 32);
+}
+
+// One CTA of 1024 threads. Buckets queries by strip height S (descending,
+// the longest-processing-time-first order of the work queue), keeps the
+// input order inside a bucket, pairs neighbours for the int16 form, and cuts
+// each bucket into groups of `warps` items.
+__global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
+  __shared__ int cnt[kMaxS + 1], run[kMaxS + 1], ibase[kMaxS + 1], icount[kMaxS + 1];
+  __shared__ int wpre[32], wtot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid <= kMaxS) { cnt[tid] = 0; run[tid] = 0; }
+  __syncthreads();
+  for (uint32_t q = tid; q < a.nq; q += blockDim.x) {
+    const int S = strip_rows(a.offsets, q, a.N, a.status);
+    if (S) atomicAdd(&cnt[S], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int base = 0;
+    for (int S = kMaxS; S >= 1; --S) {
+      icount[S] = a.pair ? (cnt[S] + 1) / 2 : cnt[S];
+      ibase[S] = base;
+      base += icount[S];
+    }
+    *a.n_items = base;
+    int g = 0;
+    for (int S = kMaxS; S >= 1; --S)
+      for (int f = 0; f < icount[S]; f += a.warps) {
+        Group gr;
+        gr.S = S;
+        gr.first = ibase[S] + f;
+        gr.count = icount[S] - f < a.warps ? icount[S] - f : a.warps;
+        gr.pad = 0;
+        a.groups[g++] = gr;
+      }
+    *a.n_groups = g;
+    *a.queue = 0;
+  }
+  __syncthreads();
+  const int n_items = *a.n_items;
+  for (int i = tid; i < n_items; i += blockDim.x) {
+    Item it;
+    it.qa = -1; it.qb = -1; it.S = 0; it.pad = 0;
+    a.items[i] = it;
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  for (uint32_t r0 = 0; r0 < a.nq; r0 += blockDim.x) {
+    const uint32_t q = r0 + tid;
+    int S = 0;
+    if (q < a.nq) {
+      const uint32_t m = a.offsets[q + 1] - a.offsets[q];
+      const long lim = a.N < HARU_MAX_QUERY ? a.N : HARU_MAX_QUERY;
+      if (m >= 1 && static_cast<long>(m) <= lim) S = static_cast<int>((m + 31) / 32);
+    }
+    for (int b = kMaxS; b >= 1; --b) {
+      const bool pred = (S == b);
+      const unsigned mask = __ballot_sync(0xffffffffu, pred);
+      if (lane == 0) wpre[warp] = __popc(mask);
+      __syncthreads();
+      if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int v = lane < nw ? wpre[lane] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (lane < nw) wpre[lane] = incl - v;
+        if (lane == 31) wtot = incl;
+      }
+      __syncthreads();
+      if (pred) {
+        const int pos = run[b] + wpre[warp] + __popc(mask & lt);
+        if (a.pair) {
+          Item *it = &a.items[ibase[b] + pos / 2];
+          if (pos % 2 == 0) { it->qa = static_cast<int>(q); it->S = b; }
+          else it->qb = static_cast<int>(q);
+        } else {
+          Item it;
+          it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.pad = 0;
+          a.items[ibase[b] + pos] = it;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) run[b] += wtot;
+      __syncthreads();
+    }
+  }
+}
+
+// ----------------------------------------------------------------- pack --
+// Mean and sigma of one query, sequentially (a query is shorter than one
+// z-score block, so this is the blocked rule's order).
+__device__ void query_stats(const float *x, int m, double &mean, double &sigma) {
+  double acc = 0.0;
+  for (int i = 0; i < m; ++i) acc = __dadd_rn(acc, static_cast<double>(x[i]));
+  mean = __ddiv_rn(acc, static_cast<double>(m));
+  double ss = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double d = __dsub_rn(static_cast<double>(x[i]), mean);
+    ss = __dadd_rn(ss, __dmul_rn(d, d));
+  }
+  sigma = __dsqrt_rn(__ddiv_rn(ss, static_cast<double>(m)));
+}
+
+// One warp per item: lane l writes rows l*S .. l*S+S-1 of both halves.
+__global__ void pack_kernel(PackArgs a) {
+  const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (item >= *a.n_items) return;
+  const Item it = a.items[item];
+  const int S = it.S;
+  const int qs[2] = {it.qa, it.qb};
+  int m[2] = {0, 0};
+  uint32_t base[2] = {0, 0};
+  double mean[2] = {0.0, 0.0}, sigma[2] = {1.0, 1.0};
+  const int halves = a.pair ? 2 : 1;
+  for (int h = 0; h < halves; ++h) {
+    if (qs[h] >= 0) {
+      base[h] = a.offsets[qs[h]];
+      m[h] = static_cast<int>(a.offsets[qs[h] + 1] - base[h]);
+    }
+  }
+  if (a.raw) {
+    double mu = 0.0, sg = 1.0;
+    const int mh = lane == 0 ? m[0] : m[1];
+    const uint32_t bh = lane == 0 ? base[0] : base[1];
+    if (lane < halves && mh > 0) {
+      query_stats(a.events + bh, mh, mu, sg);
+      if (!(sg > 0.0) || !isfinite(sg) || !isfinite(mu)) report(a.status, HARU_EINVAL);
+    }
+    for (int h = 0; h < halves; ++h) {
+      mean[h] = __shfl_sync(0xffffffffu, mu, h);
+      sigma[h] = __shfl_sync(0xffffffffu, sg, h);
+    }
+  }
+  const float s = static_cast<float>(1 << a.scale_log2);
+  uint32_t *img = a.img + static_cast<size_t>(item) * kImgStride;
+  for (int k = 0; k < S; ++k) {
+    const int row = lane * S + k;
+    uint32_t w0 = 0, w1 = 0;
+    for (int h = 0; h < halves; ++h) {
+      const int P = 32 * S - m[h];
+      const bool real = m[h] > 0 && row >= P;
+      float z = 0.0f;
+      if (real) {
+        const float x = a.events[base[h] + (row - P)];
+        if (a.raw)
+          z = __double2float_rn(__ddiv_rn(__dsub_rn(static_cast<double>(x), mean[h]), sigma[h]));
+        else
+          z = x;
+        if (!isfinite(z) || fabsf(z) > 1.0e20f) report(a.status, HARU_EINVAL);
+      }
+      if (a.pair) {
+        const int qv = real ? quantise(z, s) : 0;
+        const uint32_t cap = real ? static_cast<uint32_t>(kCap) : 0u;
+        w0 |= (static_cast<uint32_t>(qv) & 0xffffu) << (16 * h);
+        w1 |= cap << (16 * h);
+      } else {
+        w0 = __float_as_uint(z);
+        w1 = __float_as_uint(real ? 1.0f : 0.0f);
+      }
+    }
+    img[k * 32 + lane] = w0;
+    img[(S + k) * 32 + lane] = w1;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_plan(const PlanArgs &a, cudaStream_t s) {
+  plan_kernel<<<1, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s) {
+  if (max_items == 0) return cudaSuccess;
+  const int warps = 8;
+  pack_kernel<<<(max_items + warps - 1) / warps, warps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ref_levels(const uint8_t *bases, size_t n, const float *model, int k, float *out, int *status,
+                              cudaStream_t s) {
+  const size_t total = 2 * (n - k + 1);
+  const int th = 256;
+  size_t blocks = (total + th - 1) / th;
+  if (blocks > 65535) blocks = 65535;
+  ref_levels_kernel<<<static_cast<unsigned>(blocks), th, 0, s>>>(bases, n, model, k, out, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zscore_stats(const float *x, size_t n, double *partials, double *stats, int *status,
+                                cudaStream_t s) {
+  const size_t nb = (n + kZBlock - 1) / kZBlock;
+  const int th = 128;
+  const unsigned blocks = static_cast<unsigned>((nb + th - 1) / th);
+  block_sums_kernel<<<blocks, th, 0, s>>>(x, n, stats, 0, partials);
+  finish_sums_kernel<<<1, 1, 0, s>>>(partials, nb, n, 0, stats, status);
+  block_sums_kernel<<<blocks, th, 0, s>>>(x, n, stats, 1, partials);
+  finish_sums_kernel<<<1, 1, 0, s>>>(partials, nb, n, 1, stats, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ref_finish(const float *x, size_t n, const double *stats, int normalize, int scale_log2,
+                              float *z, uint32_t *img16, float *img32, size_t img_len, int *status,
+                              cudaStream_t s) {
+  (void)img_len;
+  const int th = 256;
+  size_t blocks = (n + th - 1) / th;
+  if (blocks > 65535) blocks = 65535;
+  ref_finish_kernel<<<static_cast<unsigned>(blocks), th, 0, s>>>(x, n, stats, normalize,
+                                                                 static_cast<float>(1 << scale_log2), z, img16,
+                                                                 img32, status);
+  return cudaGetLastError();
+}
+
+}  // namespace haru

@@ -1,0 +1,204 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+int16: bit-exact cost and end column. FP32: bitwise equal to the FP32
+oracle (sub, abs, add and min round identically), within 1e-5 relative of
+FP64, same column as FP64 unless the FP64 runner-up ties within 1e-5.
+Sizes span several reference tiles and ragged tails; the full-size batch is
+checked on a sample of queries the oracle recomputes one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import compare_fp32, compare_int16
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def haru():
+    import paper_2211_07340_gb300 as h
+    h.build_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return h
+
+
+@pytest.fixture(scope="module")
+def sars():
+    w = synth.workload("sars_32x250")
+    ref = oracle.ref_levels(w.genome, w.model, w.k)
+    return w, ref
+
+
+def offsets_of(lengths):
+    off = np.zeros(len(lengths) + 1, dtype=np.uint32)
+    off[1:] = np.cumsum(lengths)
+    return off
+
+
+def test_reference_build_and_normalisation(haru, sars):
+    w, ref = sars
+    with haru.Context() as ctx:
+        ctx.ref_build(w.genome, w.model, 6, scale_log2=6)
+        assert ctx.ref_length == 59_796
+        z, q = ctx.ref_read()
+        np.testing.assert_array_equal(z, oracle.zscore(ref))
+        np.testing.assert_array_equal(q, oracle.quantise(oracle.zscore(ref), 6))
+        ctx.ref_load(ref, normalize=True, scale_log2=5)
+        z2, q2 = ctx.ref_read()
+        np.testing.assert_array_equal(z2, z)
+        np.testing.assert_array_equal(q2, oracle.quantise(z, 5))
+
+
+def test_sars_32x250_both_forms(haru, sars):
+    w, ref = sars
+    qs = w.queries
+    with haru.Context() as ctx:
+        ctx.ref_load(ref)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
+        compare_int16(c16, j16, ref, qs.events, qs.offsets)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, qs.events, qs.offsets)
+        compare_fp32(c32, j32, ref, qs.events, qs.offsets)
+    # on-target queries end near where they were planted
+    on = qs.on_target
+    assert (np.abs(j32[on] - qs.truth_end[on]) <= 8).mean() >= 0.9
+
+
+@pytest.mark.parametrize("tile,warps", [(2048, 8), (4096, 4), (16384, 2)])
+def test_ragged_sizes_span_tiles(haru, tile, warps):
+    rng = np.random.default_rng(tile + warps)
+    N = 9_001  # several tiles plus a ragged tail
+    ref = synth.random_signal(N, seed=5)
+    lengths = [1, 2, 31, 32, 33, 63, 64, 65, 100, 127, 128, 129, 250, 255, 256, 257, 300, 383, 384, 385,
+               448, 480, 500, 511, 512] + list(rng.integers(1, 513, size=14))
+    off = offsets_of(lengths)
+    # queries given as z-values (a 1-event query has no z-score of its own)
+    ev = synth.random_signal(int(off[-1]), seed=6, scale=1.0, loc=0.0)
+    with haru.Context(tile_cols=tile, warps_per_cta=warps) as ctx:
+        ctx.ref_load(ref)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off, raw=False)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev, off, raw=False)
+    compare_int16(c16, j16, ref, ev, off, normalize_q=False)
+    compare_fp32(c32, j32, ref, ev, off, normalize_q=False)
+    # and the same lengths as raw currents (z-scored on the device), 2+ events
+    lengths = [m for m in lengths if m >= 2]
+    off = offsets_of(lengths)
+    ev = synth.random_signal(int(off[-1]), seed=7)
+    with haru.Context(tile_cols=tile, warps_per_cta=warps) as ctx:
+        ctx.ref_load(ref)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev, off)
+    compare_int16(c16, j16, ref, ev, off)
+    compare_fp32(c32, j32, ref, ev, off)
+
+
+def test_planted_copies_end_at_planted_column(haru):
+    N = 5000
+    ref = synth.random_signal(N, seed=8, scale=1.0, loc=0.0)  # z-values: within the int16 range at 2^6
+    starts = [0, 1, 777, 2500, N - 300]
+    lens = [300, 250, 129, 32, 300]
+    ev = np.concatenate([ref[s:s + m] for s, m in zip(starts, lens)]).astype(np.float32)
+    off = offsets_of(lens)
+    with haru.Context() as ctx:
+        ctx.ref_load(ref, normalize=False)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev, off, raw=False)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off, raw=False)
+    np.testing.assert_array_equal(c32, 0.0)
+    np.testing.assert_array_equal(j32, [s + m - 1 for s, m in zip(starts, lens)])
+    np.testing.assert_array_equal(c16, 0.0)
+    np.testing.assert_array_equal(j16, [s + m - 1 for s, m in zip(starts, lens)])
+
+
+def test_single_event_and_full_length_queries(haru):
+    ref = synth.random_signal(600, seed=9)
+    lens = [1, 512, 1, 300, 600 - 88]
+    off = offsets_of(lens)
+    ev = synth.random_signal(int(off[-1]), seed=10, scale=1.0, loc=0.0)
+    with haru.Context() as ctx:
+        ctx.ref_load(ref)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev, off, raw=False)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off, raw=False)
+    compare_fp32(c32, j32, ref, ev, off, normalize_q=False)
+    compare_int16(c16, j16, ref, ev, off, normalize_q=False)
+    # M == N: a query as long as the reference
+    ref2 = synth.random_signal(300, seed=11)
+    ev2 = synth.random_signal(300, seed=12)
+    off2 = offsets_of([300])
+    with haru.Context() as ctx:
+        ctx.ref_load(ref2)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev2, off2)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev2, off2)
+    compare_fp32(c32, j32, ref2, ev2, off2)
+    compare_int16(c16, j16, ref2, ev2, off2)
+
+
+def test_errors_and_empty(haru, sars):
+    w, ref = sars
+    ev = synth.random_signal(100, seed=1)
+    with haru.Context() as ctx:
+        cost = np.zeros(2, np.float32)
+        col = np.zeros(2, np.int64)
+        assert ctx.sdtw_batch_raw(0, ev, offsets_of([50, 50]), 2, cost, col) == haru.HARU_ENOREF
+        ctx.ref_load(ref[:400])
+        assert ctx.sdtw_batch_raw(0, ev, offsets_of([50, 50]), 0, cost, col) == haru.HARU_OK
+        assert ctx.sdtw_batch_raw(0, ev, np.array([0, 0, 100], np.uint32), 2, cost, col) == haru.HARU_EINVAL
+        big = synth.random_signal(600, seed=2)
+        assert ctx.sdtw_batch_raw(0, big, offsets_of([600]), 1, cost, col) == haru.HARU_EINVAL  # M > N
+        assert ctx.sdtw_batch_raw(7, ev, offsets_of([50, 50]), 2, cost, col) == haru.HARU_EINVAL
+        flat = np.full(50, 3.0, np.float32)  # zero spread: z-score undefined
+        assert ctx.sdtw_batch_raw(0, flat, offsets_of([50]), 1, cost, col, 0, haru.HARU_RAW) == haru.HARU_EINVAL
+        # the context still works after rejected calls
+        c, j = ctx.sdtw_batch(haru.HARU_FP32, ev, offsets_of([50, 50]))
+        assert np.isfinite(c).all()
+        with pytest.raises(haru.HaruError):
+            ctx.ref_load(np.full(10, 1.0, np.float32))  # zero spread
+
+
+def test_device_pointers_match_host_path(haru, sars):
+    w, ref = sars
+    qs = w.queries
+    dev = torch.device("cuda:0")
+    ev = torch.from_numpy(qs.events).to(dev)
+    off = torch.from_numpy(qs.offsets.astype(np.int32)).to(dev)
+    with haru.Context() as ctx:
+        ctx.ref_load(ref)
+        for prec in (haru.HARU_INT16, haru.HARU_FP32):
+            hc, hj = ctx.sdtw_batch(prec, qs.events, qs.offsets)
+            dc = torch.empty(qs.nq, dtype=torch.float32, device=dev)
+            dj = torch.empty(qs.nq, dtype=torch.int64, device=dev)
+            s = torch.cuda.current_stream().cuda_stream
+            ctx.sdtw_batch_device(prec, ev, off, dc, dj, stream=s)
+            np.testing.assert_array_equal(dc.cpu().numpy(), hc)
+            np.testing.assert_array_equal(dj.cpu().numpy(), hj)
+            ctx.sdtw_batch_device(prec, ev, off, dc, dj, stream=s, asynchronous=True)
+            torch.cuda.synchronize()
+            assert ctx.last_status() == haru.HARU_OK
+            np.testing.assert_array_equal(dj.cpu().numpy(), hj)
+
+
+def test_uneven_8192_full_size_sampled(haru, sars):
+    """The full 8,192-query uneven batch in one launch; 40 queries re-checked
+    one by one against the oracle (both forms), covering every strip height."""
+    _, ref = sars
+    w = synth.workload("sars_uneven_8192")
+    qs = w.queries
+    with haru.Context() as ctx:
+        ctx.ref_load(ref)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, qs.events, qs.offsets)
+    lens = qs.lengths
+    rng = np.random.default_rng(0)
+    idx = []
+    for S in range(4, 17):
+        cand = np.nonzero((lens + 31) // 32 == S)[0]
+        idx += list(rng.choice(cand, size=min(3, cand.shape[0]), replace=False))
+    idx = np.array(sorted(set(idx)))[:40]
+    compare_int16(c16, j16, ref, qs.events, qs.offsets, idx=idx)
+    compare_fp32(c32, j32, ref, qs.events, qs.offsets, idx=idx)
+    # every query got a result
+    assert (j16 >= 0).all() and (j32 >= 0).all()
+    assert np.isfinite(c32).all()
