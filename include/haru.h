@@ -61,6 +61,8 @@ extern "C" {
 #define HARU_RAW 2u       /* events are raw currents: z-score each query on the device first */
 #define HARU_ASYNC 4u     /* HARU_ON_DEVICE only: return after enqueueing; read the status later
                              with haru_last_status() once the stream has been synchronised */
+#define HARU_PROFILE 8u   /* record CUDA events around the preparation kernels and the sweep kernel of
+                             this batch (also inside a captured CUDA graph); read with haru_last_timing() */
 
 typedef struct haru_ctx haru_ctx;
 
@@ -68,7 +70,7 @@ typedef struct {
   int warps_per_cta;        /* warps (queries or query pairs) sharing one reference tile stream; 0 = auto */
   int tile_cols;            /* reference columns per shared-memory tile, 2048..16384; 0 = auto */
   int ctas_per_sm;          /* persistent CTAs per SM; 0 = as many as fit */
-  uint32_t wait_limit;      /* spin iterations before a device wait reports HARU_ETIMEDOUT; 0 = default */
+  uint32_t wait_limit;      /* longest single device wait, microseconds, before HARU_ETIMEDOUT; 0 = 2 s */
   /* serving */
   float threshold;          /* accept iff cost <= threshold (z units; int16 compares floor(threshold * 2^k)) */
   int serve_precision;      /* HARU_FP32 or HARU_INT16 */
@@ -131,6 +133,12 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
 /* Status of the last HARU_ASYNC batch on this context (after the caller has
  * synchronised its stream): HARU_OK or the first error the device reported. */
 int haru_last_status(haru_ctx *ctx);
+
+/* Durations of the last HARU_PROFILE batch (after its stream has been
+ * synchronised; for a captured graph, of its latest replay): ms_prep = the
+ * planner and packing kernels, ms_sweep = the sweep kernel. Either pointer
+ * may be NULL. Errors: HARU_EINVAL (no profiled batch yet), HARU_ECUDA. */
+int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep);
 
 /* Human-readable name of a status code (static storage). */
 const char *haru_strerror(int code);

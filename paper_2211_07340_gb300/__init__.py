@@ -32,6 +32,7 @@ HARU_INT16 = 1
 HARU_ON_DEVICE = 1
 HARU_RAW = 2
 HARU_ASYNC = 4
+HARU_PROFILE = 8
 HARU_INT16_QMAX = 2047
 HARU_INT16_CAP = 28673
 HARU_MAX_QUERY = 512
@@ -73,6 +74,8 @@ _SIGS = {
                                        ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.c_uint32]),
     "haru_last_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "haru_last_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "haru_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -201,12 +204,19 @@ class Context:
         return cost[:nq], col[:nq]
 
     def sdtw_batch_device(self, precision: int, events, offsets, out_cost, out_col, stream: int = 0,
-                          raw: bool = True, asynchronous: bool = False):
+                          raw: bool = True, asynchronous: bool = False, profile: bool = False):
         """Device tensors in and out (torch), ordered on `stream` (a cudaStream_t as int)."""
         nq = int(offsets.shape[0]) - 1
-        flags = HARU_ON_DEVICE | (HARU_RAW if raw else 0) | (HARU_ASYNC if asynchronous else 0)
+        flags = (HARU_ON_DEVICE | (HARU_RAW if raw else 0) | (HARU_ASYNC if asynchronous else 0)
+                 | (HARU_PROFILE if profile else 0))
         return check(self.sdtw_batch_raw(precision, events, offsets, nq, out_cost, out_col, stream, flags),
                      "haru_sdtw_batch")
 
     def last_status(self) -> int:
         return int(lib().haru_last_status(self._h))
+
+    def last_timing(self):
+        """(ms_prep, ms_sweep) of the last HARU_PROFILE batch."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        check(lib().haru_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)), "haru_last_timing")
+        return a.value, b.value

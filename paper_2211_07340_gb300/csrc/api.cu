@@ -47,6 +47,10 @@ struct haru_ctx {
   float *d_cost = nullptr;
   int64_t *d_col = nullptr;
   size_t cap_q = 0;
+
+  // profiling events (HARU_PROFILE)
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool profiled = false;
 };
 
 namespace {
@@ -89,6 +93,16 @@ int pick_tile(const haru_config &cfg) {
 
 unsigned long long wait_ns(const haru_config &cfg) {
   return cfg.wait_limit ? static_cast<unsigned long long>(cfg.wait_limit) * 1000ull : 2000000000ull;
+}
+
+// Record `e` on `s`; inside a stream capture, as an external event node so
+// the timing of every replay can be read back.
+cudaError_t record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t r = cudaStreamIsCapturing(s, &cs);
+  if (r != cudaSuccess) return r;
+  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  return cudaEventRecord(e, s);
 }
 
 }  // namespace
@@ -145,6 +159,9 @@ int haru_create(haru_ctx **out, int device, const haru_config *cfg) {
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = HARU_ECUDA; break; }
     if (cudaMalloc(&ctx->d_status, 8 * sizeof(int)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
     if (cudaMalloc(&ctx->stats, 2 * sizeof(double)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
+    bool ev_ok = true;
+    for (auto &e : ctx->ev) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!ev_ok) { rc = HARU_ECUDA; break; }
   } while (0);
   if (rc != HARU_OK) {
     haru_destroy(ctx);
@@ -162,6 +179,8 @@ void haru_destroy(haru_ctx *ctx) {
                   ctx->groups, ctx->img, ctx->d_events, ctx->d_offsets, ctx->d_cost, ctx->d_col};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  for (auto e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -346,7 +365,9 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
     HARU_CUDA(grow(&ctx->img, &c2, max_items * haru::kImgStride));
     ctx->cap_items = max_items;
   }
+  const bool prof = flags & HARU_PROFILE;
   HARU_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4 * sizeof(int), s));
+  if (prof) HARU_CUDA(record(ctx->ev[0], s));
 
   haru::PlanArgs pa;
   pa.offsets = d_off;
@@ -393,7 +414,12 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   if (per_sm < 1) per_sm = 1;
   const size_t groups_max = (max_items + warps - 1) / warps + haru::kMaxS;
   int grid = (int)std::min<size_t>((size_t)ctx->sms * per_sm, groups_max);
+  if (prof) HARU_CUDA(record(ctx->ev[1], s));
   HARU_CUDA(haru::launch_sdtw(precision, sa, grid, s));
+  if (prof) {
+    HARU_CUDA(record(ctx->ev[2], s));
+    ctx->profiled = true;
+  }
 
   if (async) {
     ctx->last_status = HARU_OK;
@@ -408,6 +434,21 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   HARU_CUDA(cudaStreamSynchronize(s));
   ctx->last_status = st;
   return st;
+}
+
+int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep) {
+  if (!ctx) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  if (!ctx->profiled) return HARU_EINVAL;
+  HARU_CUDA(cudaSetDevice(ctx->device));
+  HARU_CUDA(cudaEventSynchronize(ctx->ev[2]));
+  float a = 0.0f, b = 0.0f;
+  HARU_CUDA(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
+  HARU_CUDA(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+  if (ms_prep) *ms_prep = a;
+  if (ms_sweep) *ms_sweep = b;
+  return HARU_OK;
 }
 
 int haru_last_status(haru_ctx *ctx) {
