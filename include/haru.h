@@ -140,6 +140,37 @@ int haru_last_status(haru_ctx *ctx);
  * may be NULL. Errors: HARU_EINVAL (no profiled batch yet), HARU_ECUDA. */
 int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep);
 
+/* ---- Batch without allocation --------------------------------------------
+ * No counterpart in the paper: an interface option of this library.
+ *
+ * haru_sdtw_batch_noalloc is haru_sdtw_batch for callers that cannot let the
+ * library allocate device memory: a service that reserves its whole device
+ * budget at start-up and must not grow afterwards, a host that forbids
+ * run-time device allocation, or a latency-critical caller that cannot
+ * accept cudaMalloc's implicit synchronisation stalling its other streams.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. Its
+ * scratch memory (planner items and groups, packed query images, status and
+ * work-queue counters) is one fixed array of about 4.1 MiB compiled into
+ * the library, which every GPU that loads the library holds until the
+ * process exits.
+ *
+ * events, offsets, out_cost and out_col are DEVICE pointers owned by the
+ * caller, laid out as in haru_sdtw_batch; the reference is the context's.
+ * flags: 0 or HARU_RAW. The call is ordered on `stream` (0 = the context's)
+ * and returns after the results are written.
+ * Limits and errors: nq <= HARU_NOALLOC_MAX_QUERIES, else HARU_EINVAL (as for
+ * any other flag or bad argument); per-query rules and the other codes as
+ * for haru_sdtw_batch.
+ * The first call on a device looks up the array's device address (which may
+ * load the library's GPU code); make that first call before any stream
+ * capture. Every call on every context of the process shares the one array
+ * and it keeps the last call's contents: calls that overlap on the GPU (two
+ * streams, two threads, two contexts on one device) race and must be
+ * serialised by the caller. */
+#define HARU_NOALLOC_MAX_QUERIES 1024
+int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets,
+                            uint32_t nq, float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);
+
 /* Human-readable name of a status code (static storage). */
 const char *haru_strerror(int code);
 

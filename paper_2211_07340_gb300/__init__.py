@@ -36,6 +36,7 @@ HARU_PROFILE = 8
 HARU_INT16_QMAX = 2047
 HARU_INT16_CAP = 28673
 HARU_MAX_QUERY = 512
+HARU_NOALLOC_MAX_QUERIES = 1024
 
 
 class HaruError(RuntimeError):
@@ -77,6 +78,9 @@ _SIGS = {
     "haru_last_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "haru_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "haru_sdtw_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                               ctypes.c_uint32]),
 }
 
 

@@ -107,6 +107,31 @@ cudaError_t record(cudaEvent_t e, cudaStream_t s) {
 
 }  // namespace
 
+namespace haru {
+
+// Reference and launch settings of a context, for haru_sdtw_batch_noalloc
+// (noalloc.cu). Reads state only; allocates nothing.
+int ctx_reference(haru_ctx *ctx, int precision, const void **img, long *N, int *scale_log2, int *device,
+                  cudaStream_t *stream, int *warps, int *tile, unsigned long long *wait, int *per_sm, int *sms) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  if (ctx->N == 0) return HARU_ENOREF;
+  *img = precision == HARU_INT16 ? static_cast<const void *>(ctx->img16) : static_cast<const void *>(ctx->img32);
+  *N = static_cast<long>(ctx->N);
+  *scale_log2 = ctx->scale_log2;
+  *device = ctx->device;
+  *stream = ctx->stream;
+  *warps = pick_warps(ctx->cfg);
+  *tile = pick_tile(ctx->cfg);
+  *wait = wait_ns(ctx->cfg);
+  *sms = ctx->sms;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return HARU_ECUDA;
+  *per_sm = ctx->cfg.ctas_per_sm > 0 ? ctx->cfg.ctas_per_sm : sdtw_max_ctas_per_sm(precision, *tile, *warps);
+  return HARU_OK;
+}
+
+}  // namespace haru
+
 extern "C" {
 
 int haru_config_default(haru_config *cfg) {

@@ -1,0 +1,142 @@
+// haru_sdtw_batch_noalloc: the batch path with its scratch memory in a
+// fixed, file-scope device array instead of buffers the library allocates.
+//
+// Who needs this: callers that cannot let the library call cudaMalloc. A
+// service that reserves its whole device-memory budget at start-up and must
+// not grow afterwards; a host that forbids run-time device allocation; a
+// latency-critical caller that cannot accept cudaMalloc's implicit
+// synchronisation, which can stall work queued on its other streams. Such a
+// caller owns every input and output buffer (device pointers) and this entry
+// point allocates nothing: the planner's items and groups, the packed query
+// images and the status and work-queue counters all live in `scratch` below,
+// which every GPU that loads the library holds until the process exits.
+//
+// The paper has no counterpart; it is an interface option of this library.
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "haru_internal.h"
+
+namespace haru {
+namespace {
+
+// Layout of the scratch array (bytes): 4 ints of status and counters, then
+// items, groups and the per-item register images for up to
+// HARU_NOALLOC_MAX_QUERIES queries (the FP32 form needs one item per query,
+// the int16 form one per pair).
+constexpr size_t kNaItems = HARU_NOALLOC_MAX_QUERIES + kMaxS;
+constexpr size_t kNaHead = 256;
+constexpr size_t kNaItemsOff = kNaHead;
+constexpr size_t kNaGroupsOff = kNaItemsOff + ((kNaItems * sizeof(Item) + 255) / 256) * 256;
+constexpr size_t kNaImgOff = kNaGroupsOff + ((kNaItems * sizeof(Group) + 255) / 256) * 256;
+constexpr size_t kNaBytes = kNaImgOff + kNaItems * kImgStride * sizeof(uint32_t);
+
+static __device__ __align__(256) unsigned char scratch[kNaBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_ptr[kMaxDevices] = {nullptr};
+
+// Device address of `scratch` on `device` (current). Looked up once per
+// device; the first lookup may load the module.
+int scratch_on(int device, unsigned char **out) {
+  if (device < 0 || device >= kMaxDevices) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_ptr[device]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, scratch) != cudaSuccess || !p) return HARU_ECUDA;
+    g_ptr[device] = p;
+  }
+  *out = static_cast<unsigned char *>(g_ptr[device]);
+  return HARU_OK;
+}
+
+}  // namespace
+
+// Reference access for the no-allocation path (defined in api.cu).
+int ctx_reference(haru_ctx *ctx, int precision, const void **img, long *N, int *scale_log2, int *device,
+                  cudaStream_t *stream, int *warps, int *tile, unsigned long long *wait, int *per_sm, int *sms);
+
+}  // namespace haru
+
+extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets,
+                                       uint32_t nq, float *out_cost, int64_t *out_col, uintptr_t stream,
+                                       uint32_t flags) {
+  using namespace haru;
+  if (!ctx) return HARU_EINVAL;
+  if (precision != HARU_FP32 && precision != HARU_INT16) return HARU_EINVAL;
+  if (nq > HARU_NOALLOC_MAX_QUERIES) return HARU_EINVAL;
+  if (flags & ~static_cast<uint32_t>(HARU_RAW)) return HARU_EINVAL;
+  if (nq == 0) return HARU_OK;
+  if (!events || !offsets || !out_cost || !out_col) return HARU_EINVAL;
+  const void *img = nullptr;
+  long N = 0;
+  int scale = 0, device = 0, warps = 0, tile = 0, per_sm = 0, sms = 0;
+  unsigned long long wait = 0;
+  cudaStream_t own = nullptr;
+  int rc = ctx_reference(ctx, precision, &img, &N, &scale, &device, &own, &warps, &tile, &wait, &per_sm, &sms);
+  if (rc != HARU_OK) return rc;
+  if (cudaSetDevice(device) != cudaSuccess) return HARU_ECUDA;
+  unsigned char *base = nullptr;
+  rc = scratch_on(device, &base);
+  if (rc != HARU_OK) return rc;
+  cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : own;
+  int *status = reinterpret_cast<int *>(base);
+  Item *items = reinterpret_cast<Item *>(base + kNaItemsOff);
+  Group *groups = reinterpret_cast<Group *>(base + kNaGroupsOff);
+  uint32_t *imgs = reinterpret_cast<uint32_t *>(base + kNaImgOff);
+  const size_t max_items = precision == HARU_INT16 ? (static_cast<size_t>(nq) + 1) / 2 + kMaxS : nq;
+
+  // The array keeps the previous call's contents: the status word and the
+  // counters must start at zero; items, groups and images are rewritten.
+  if (cudaMemsetAsync(status, 0, 4 * sizeof(int), s) != cudaSuccess) return HARU_ECUDA;
+  PlanArgs pa;
+  pa.offsets = offsets;
+  pa.nq = nq;
+  pa.N = N;
+  pa.pair = precision == HARU_INT16;
+  pa.warps = warps;
+  pa.items = items;
+  pa.groups = groups;
+  pa.n_groups = status + 1;
+  pa.n_items = status + 2;
+  pa.queue = status + 3;
+  pa.status = status;
+  if (launch_plan(pa, s) != cudaSuccess) return HARU_ECUDA;
+  PackArgs ka;
+  ka.events = events;
+  ka.offsets = offsets;
+  ka.items = items;
+  ka.n_items = status + 2;
+  ka.img = imgs;
+  ka.raw = (flags & HARU_RAW) ? 1 : 0;
+  ka.pair = pa.pair;
+  ka.scale_log2 = scale;
+  ka.status = status;
+  if (launch_pack(ka, static_cast<uint32_t>(max_items), s) != cudaSuccess) return HARU_ECUDA;
+  SdtwArgs sa;
+  sa.ref_img = img;
+  sa.N = N;
+  sa.img = imgs;
+  sa.items = items;
+  sa.groups = groups;
+  sa.n_groups = status + 1;
+  sa.queue = status + 3;
+  sa.out_cost = out_cost;
+  sa.out_col = out_col;
+  sa.inv_scale = 1.0f / static_cast<float>(1 << scale);
+  sa.tile_cols = tile;
+  sa.warps = warps;
+  sa.wait_ns = wait;
+  sa.status = status;
+  const size_t groups_max = (max_items + warps - 1) / warps + kMaxS;
+  size_t grid = static_cast<size_t>(sms) * (per_sm > 0 ? per_sm : 1);
+  if (grid > groups_max) grid = groups_max;
+  if (launch_sdtw(precision, sa, static_cast<int>(grid), s) != cudaSuccess) return HARU_ECUDA;
+  int st = 0;
+  if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HARU_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HARU_ECUDA;
+  return st;
+}
