@@ -78,7 +78,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -147,12 +147,13 @@ def run_reference(args, rank: int):
     q = w.queries
     threads = os.cpu_count() or 1
     N = ref.shape[0]
-    # size each step to ~8 s of CPU work
+    # size each step so that the whole run takes about two minutes of CPU work
+    per_step_s = max(0.5, min(8.0, 120.0 / max(1, args.steps + args.warmup)))
     probe = q.subset(np.arange(min(q.nq, max(threads, 16))))
     t = time.perf_counter()
     oracle.batch(oracle.PREC_I16, ref, probe.events, probe.offsets, threads=threads)
     rate = probe.lengths.sum() * N / max(time.perf_counter() - t, 1e-6)
-    n = int(np.searchsorted(np.cumsum(q.lengths), 8.0 * rate / N)) + 1
+    n = int(np.searchsorted(np.cumsum(q.lengths), per_step_s * rate / N)) + 1
     n = max(threads, min(q.nq, n))
     times, cells_per_step = [], 0.0
     for step in range(args.warmup + args.steps):
@@ -178,13 +179,17 @@ def run_reference(args, rank: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="haru", choices=["haru", "reference"])
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--nq", type=int, default=0, help="first nq queries only (profiling runs)")
+    ap.add_argument("--units", type=int, default=0, help="work units target (0 = library default)")
+    ap.add_argument("--forms", default="int16,fp32", help="forms to time (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,12 +210,14 @@ def main():
 
     # Weak scaling: every rank aligns its own batch (independent seeds).
     w = synth.workload(WORKLOAD, seed=101 + 1000 * rank)
-    q = w.queries
+    q = w.queries if not args.nq else w.queries.subset(np.arange(min(args.nq, w.queries.nq)))
     cfg = haru.default_config()
     if args.tile:
         cfg.tile_cols = args.tile
     if args.warps:
         cfg.warps_per_cta = args.warps
+    if args.units:
+        cfg.units_target = args.units
     ctx = haru.Context(local, config=cfg)
     ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
     N = ctx.ref_length
@@ -275,8 +282,15 @@ def main():
             raise haru.HaruError(st, "batch")
         return float(np.mean(step_ms)), float(np.mean(sweep_ms)), clk.summary(), graph is not None
 
-    ms16, sweep16, clocks, graphed = run_form(haru.HARU_INT16)
-    ms32, sweep32, clocks32, _ = run_form(haru.HARU_FP32)
+    forms = args.forms.split(",")
+    nan = float("nan")
+    ms16 = sweep16 = ms32 = sweep32 = nan
+    clocks = clocks32 = {}
+    graphed = False
+    if "int16" in forms:
+        ms16, sweep16, clocks, graphed = run_form(haru.HARU_INT16)
+    if "fp32" in forms:
+        ms32, sweep32, clocks32, _ = run_form(haru.HARU_FP32)
 
     # End to end through the C ABI with host buffers: H2D of raw events and
     # offsets, the batch, D2H of costs and columns, every step.
@@ -295,10 +309,12 @@ def main():
         haru.check(rc, "e2e batch")
         return time.perf_counter() - t
 
-    for _ in range(args.warmup):
-        e2e_step()
-    e2e_s = [e2e_step() for _ in range(args.steps)]
-    e2e_ms = 1e3 * float(np.mean(e2e_s))
+    e2e_ms = nan
+    if not args.no_e2e:
+        for _ in range(args.warmup):
+            e2e_step()
+        e2e_s = [e2e_step() for _ in range(args.steps)]
+        e2e_ms = 1e3 * float(np.mean(e2e_s))
 
     if dist:
         t = torch.tensor([ms16, e2e_ms, ms32], dtype=torch.float64, device=dev)
@@ -324,7 +340,7 @@ def main():
                    "cells_per_step": total_cells, "form": "int16 (two queries per 32-bit lane)",
                    "cuda_graph": graphed, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"dp{world} (independent batches per GPU)", "tile_cols": cfg.tile_cols,
-                   "warps_per_cta": cfg.warps_per_cta},
+                   "warps_per_cta": cfg.warps_per_cta, "units_target": cfg.units_target},
         "roofline": {"bound": "alu", "kernel": "sdtw_kernel<INT16>", "achieved": ach16, "peak": peak,
                      "unit": "GCUPS", "frac": ach16 / peak, "traffic": None,
                      "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (half-rate DPX pipe, 1.5 ops/cell) x "
@@ -336,13 +352,13 @@ def main():
                               "unit": "GCUPS", "frac": ach32 / peak,
                               "peak_basis": "3 issue slots per cell (sub, 3-input min, fma) at 4 warp-instr/clk/SM"},
                  "clocks": clocks32},
-        "int16_over_fp32": value / value32,
+        "int16_over_fp32": value / value32 if value32 == value32 else None,
         "prep_ms_per_step": ms16 - sweep16,
         "e2e": {"value": e2e_value, "unit": "GCUPS", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(q.events.nbytes + q.offsets.nbytes),
                 "d2h_bytes_per_step": int(q.nq * (4 + 8))},
         "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches_per_step * args.steps * len(forms),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle

@@ -77,6 +77,8 @@ typedef struct {
   size_t serve_budget_bytes;/* device memory for in-flight serving requests; 0 = 64 MiB */
   uint32_t serve_max_batch; /* most requests launched together; 0 = 1024 */
   uint32_t serve_prefix;    /* events per decision prefix; 0 = 250 (Section 4.1) */
+  int units_target;         /* work units (query x reference segment) a batch is cut into, at least;
+                               0 = 4 x SMs x warps_per_cta; 1 = never split the reference */
 } haru_config;
 
 /* Fill *cfg with defaults. Returns HARU_OK, or HARU_EINVAL if cfg is NULL. */
@@ -129,6 +131,19 @@ int haru_ref_read(haru_ctx *ctx, float *z, int16_t *q, size_t n);
  * Errors: HARU_EINVAL, HARU_ENOREF, HARU_ENOMEM, HARU_ETIMEDOUT, HARU_ECUDA. */
 int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
                     float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);
+
+/* Work accounting of the last batch on this context (read after its stream
+ * has been synchronised): items = warps of work (queries, or query pairs in
+ * the int16 form), groups = CTA work units, segments = reference segments
+ * per item (largest), fixups = segments recomputed because their
+ * speculative start did not converge to the exact state. */
+typedef struct {
+  uint32_t items;
+  uint32_t groups;
+  uint32_t fixups;
+  uint32_t max_segments;
+} haru_batch_stats;
+int haru_last_stats(haru_ctx *ctx, haru_batch_stats *out);
 
 /* Status of the last HARU_ASYNC batch on this context (after the caller has
  * synchronised its stream): HARU_OK or the first error the device reported. */

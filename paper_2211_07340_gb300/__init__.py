@@ -57,7 +57,13 @@ class haru_config(ctypes.Structure):
         ("serve_budget_bytes", ctypes.c_size_t),
         ("serve_max_batch", ctypes.c_uint32),
         ("serve_prefix", ctypes.c_uint32),
+        ("units_target", ctypes.c_int),
     ]
+
+
+class haru_batch_stats(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_uint32), ("groups", ctypes.c_uint32), ("fixups", ctypes.c_uint32),
+                ("max_segments", ctypes.c_uint32)]
 
 
 _lib = None
@@ -75,6 +81,7 @@ _SIGS = {
                                        ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.c_uint32]),
     "haru_last_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "haru_last_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_batch_stats)]),
     "haru_last_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "haru_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -218,6 +225,11 @@ class Context:
 
     def last_status(self) -> int:
         return int(lib().haru_last_status(self._h))
+
+    def last_stats(self) -> dict:
+        st = haru_batch_stats()
+        check(lib().haru_last_stats(self._h, ctypes.byref(st)), "haru_last_stats")
+        return {"items": st.items, "groups": st.groups, "fixups": st.fixups, "max_segments": st.max_segments}
 
     def last_timing(self):
         """(ms_prep, ms_sweep) of the last HARU_PROFILE batch."""

@@ -47,10 +47,22 @@ struct haru_ctx {
   float *d_cost = nullptr;
   int64_t *d_col = nullptr;
   size_t cap_q = 0;
+  uint32_t *states = nullptr;   // saved segment states
+  size_t cap_states = 0;
+  haru::Best *bests = nullptr;  // per-unit last-row minima
+  size_t cap_bests = 0;
 
   // profiling events (HARU_PROFILE)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool profiled = false;
+
+  // one stream per strip-height class; the class kernels of a batch run
+  // concurrently (fork/join through events, also inside a captured graph)
+  cudaStream_t aux[haru::kClasses] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[haru::kClasses] = {nullptr, nullptr, nullptr, nullptr};
+  const int *last_fixups_ptr = nullptr;
+  int last_nseg_cap = 1;
 };
 
 namespace {
@@ -126,7 +138,7 @@ int ctx_reference(haru_ctx *ctx, int precision, const void **img, long *N, int *
   *wait = wait_ns(ctx->cfg);
   *sms = ctx->sms;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return HARU_ECUDA;
-  *per_sm = ctx->cfg.ctas_per_sm > 0 ? ctx->cfg.ctas_per_sm : sdtw_max_ctas_per_sm(precision, *tile, *warps);
+  *per_sm = ctx->cfg.ctas_per_sm;
   return HARU_OK;
 }
 
@@ -182,10 +194,15 @@ int haru_create(haru_ctx **out, int device, const haru_config *cfg) {
       break;
     }
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = HARU_ECUDA; break; }
-    if (cudaMalloc(&ctx->d_status, 8 * sizeof(int)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
+    if (cudaMalloc(&ctx->d_status, haru::kIntWords * sizeof(int)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
     if (cudaMalloc(&ctx->stats, 2 * sizeof(double)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
     bool ev_ok = true;
     for (auto &e : ctx->ev) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
+    ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; c < haru::kClasses; ++c) {
+      ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming) == cudaSuccess;
+      ev_ok = ev_ok && cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking) == cudaSuccess;
+    }
     if (!ev_ok) { rc = HARU_ECUDA; break; }
   } while (0);
   if (rc != HARU_OK) {
@@ -200,12 +217,18 @@ void haru_destroy(haru_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void *ptrs[] = {ctx->ref_z, ctx->img16, ctx->img32, ctx->stats, ctx->partials, ctx->d_status, ctx->items,
-                  ctx->groups, ctx->img, ctx->d_events, ctx->d_offsets, ctx->d_cost, ctx->d_col};
+  void *ptrs[] = {ctx->ref_z, ctx->img16, ctx->img32, ctx->stats,  ctx->partials, ctx->d_status,
+                  ctx->items, ctx->groups, ctx->img,   ctx->d_events, ctx->d_offsets, ctx->d_cost,
+                  ctx->d_col, ctx->states, ctx->bests};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  for (int c = 0; c < haru::kClasses; ++c) {
+    if (ctx->join[c]) cudaEventDestroy(ctx->join[c]);
+    if (ctx->aux[c]) cudaStreamDestroy(ctx->aux[c]);
+  }
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -380,18 +403,28 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   const int warps = pick_warps(ctx->cfg);
   const int tile = pick_tile(ctx->cfg);
   const size_t max_items = precision == HARU_INT16 ? ((size_t)nq + 1) / 2 + haru::kMaxS : (size_t)nq;
+  // Work units: enough (query x reference segment) units to keep every SM
+  // busy to the end; nseg_cap bounds the segments per item for storage.
+  const int units_target = ctx->cfg.units_target > 0 ? ctx->cfg.units_target : 4 * ctx->sms * warps;
+  const size_t items_min = precision == HARU_INT16 ? ((size_t)nq + 1) / 2 : (size_t)nq;
+  int nseg_cap = (int)std::min<size_t>(haru::kMaxSeg, ((size_t)units_target + items_min - 1) / items_min);
+  if (nseg_cap < 1) nseg_cap = 1;
   if (ctx->cap_items < max_items) {
     size_t c0 = 0, c1 = 0, c2 = 0;
     cudaFree(ctx->items); cudaFree(ctx->groups); cudaFree(ctx->img);
     ctx->items = nullptr; ctx->groups = nullptr; ctx->img = nullptr;
     ctx->cap_items = 0;
     HARU_CUDA(grow(&ctx->items, &c0, max_items));
-    HARU_CUDA(grow(&ctx->groups, &c1, max_items + haru::kMaxS));
+    HARU_CUDA(grow(&ctx->groups, &c1, max_items * haru::kMaxSeg + haru::kMaxS * haru::kMaxSeg));
     HARU_CUDA(grow(&ctx->img, &c2, max_items * haru::kImgStride));
     ctx->cap_items = max_items;
   }
+  const size_t units = max_items * (size_t)nseg_cap;
+  HARU_CUDA(grow(&ctx->bests, &ctx->cap_bests, units));
+  if (nseg_cap > 1) HARU_CUDA(grow(&ctx->states, &ctx->cap_states, units * 2 * haru::kStateStride));
   const bool prof = flags & HARU_PROFILE;
-  HARU_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4 * sizeof(int), s));
+  int *ints = ctx->d_status;
+  HARU_CUDA(cudaMemsetAsync(ints, 0, haru::kIntWords * sizeof(int), s));
   if (prof) HARU_CUDA(record(ctx->ev[0], s));
 
   haru::PlanArgs pa;
@@ -400,24 +433,23 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   pa.N = (long)ctx->N;
   pa.pair = precision == HARU_INT16;
   pa.warps = warps;
+  pa.units_target = units_target;
+  pa.nseg_cap = nseg_cap;
   pa.items = ctx->items;
   pa.groups = ctx->groups;
-  pa.n_groups = ctx->d_status + 1;
-  pa.n_items = ctx->d_status + 2;
-  pa.queue = ctx->d_status + 3;
-  pa.status = ctx->d_status;
+  pa.ints = ints;
   HARU_CUDA(haru::launch_plan(pa, s));
 
   haru::PackArgs ka;
   ka.events = d_ev;
   ka.offsets = d_off;
   ka.items = ctx->items;
-  ka.n_items = ctx->d_status + 2;
+  ka.n_items = ints + haru::kIntItems;
   ka.img = ctx->img;
   ka.raw = raw;
   ka.pair = pa.pair;
   ka.scale_log2 = ctx->scale_log2;
-  ka.status = ctx->d_status;
+  ka.status = ints + haru::kIntStatus;
   HARU_CUDA(haru::launch_pack(ka, (uint32_t)max_items, s));
 
   haru::SdtwArgs sa;
@@ -426,25 +458,38 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   sa.img = ctx->img;
   sa.items = ctx->items;
   sa.groups = ctx->groups;
-  sa.n_groups = ctx->d_status + 1;
-  sa.queue = ctx->d_status + 3;
+  sa.ints = ints;
+  sa.states = ctx->states;
+  sa.bests = ctx->bests;
+  sa.nseg_cap = nseg_cap;
   sa.out_cost = d_cost;
   sa.out_col = d_col;
   sa.inv_scale = 1.0f / (float)(1 << ctx->scale_log2);
   sa.tile_cols = tile;
   sa.warps = warps;
   sa.wait_ns = wait_ns(ctx->cfg);
-  sa.status = ctx->d_status;
-  int per_sm = ctx->cfg.ctas_per_sm > 0 ? ctx->cfg.ctas_per_sm : haru::sdtw_max_ctas_per_sm(precision, tile, warps);
-  if (per_sm < 1) per_sm = 1;
-  const size_t groups_max = (max_items + warps - 1) / warps + haru::kMaxS;
-  int grid = (int)std::min<size_t>((size_t)ctx->sms * per_sm, groups_max);
+  const size_t groups_max = ((max_items + warps - 1) / warps + haru::kMaxS) * (size_t)nseg_cap;
   if (prof) HARU_CUDA(record(ctx->ev[1], s));
-  HARU_CUDA(haru::launch_sdtw(precision, sa, grid, s));
+  // Fork: the class kernels (tallest strips first) run side by side; each is
+  // persistent over its own part of the group list, then verifies its
+  // segments and writes its queries' results.
+  HARU_CUDA(cudaEventRecord(ctx->fork, s));
+  for (int c = 0; c < haru::kClasses; ++c) {
+    int per_sm = ctx->cfg.ctas_per_sm > 0 ? ctx->cfg.ctas_per_sm
+                                          : haru::sdtw_max_ctas_per_sm(precision, c, tile, warps);
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::min<size_t>((size_t)ctx->sms * per_sm, groups_max);
+    HARU_CUDA(cudaStreamWaitEvent(ctx->aux[c], ctx->fork, 0));
+    HARU_CUDA(haru::launch_sdtw(precision, c, sa, grid, (int)max_items, ctx->aux[c]));
+    HARU_CUDA(cudaEventRecord(ctx->join[c], ctx->aux[c]));
+    HARU_CUDA(cudaStreamWaitEvent(s, ctx->join[c], 0));
+  }
   if (prof) {
     HARU_CUDA(record(ctx->ev[2], s));
     ctx->profiled = true;
   }
+  ctx->last_fixups_ptr = ints + haru::kIntFixups;
+  ctx->last_nseg_cap = nseg_cap;
 
   if (async) {
     ctx->last_status = HARU_OK;
@@ -473,6 +518,20 @@ int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep) {
   HARU_CUDA(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
   if (ms_prep) *ms_prep = a;
   if (ms_sweep) *ms_sweep = b;
+  return HARU_OK;
+}
+
+int haru_last_stats(haru_ctx *ctx, haru_batch_stats *out) {
+  if (!ctx || !out) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->sticky) return ctx->sticky;
+  HARU_CUDA(cudaSetDevice(ctx->device));
+  int w[haru::kIntWords];
+  HARU_CUDA(cudaMemcpy(w, ctx->d_status, sizeof(w), cudaMemcpyDeviceToHost));
+  out->items = (uint32_t)w[haru::kIntItems];
+  out->groups = (uint32_t)w[haru::kIntGroups];
+  out->fixups = (uint32_t)w[haru::kIntFixups];
+  out->max_segments = (uint32_t)ctx->last_nseg_cap;
   return HARU_OK;
 }
 

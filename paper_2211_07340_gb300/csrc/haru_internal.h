@@ -12,26 +12,41 @@ namespace haru {
 
 // One warp's work: a query (FP32) or a pair of queries packed into the two
 // 16-bit halves of every register (INT16). qb < 0 when the pair is short.
+// Its steps are cut into nseg segments (work units).
 struct Item {
   int qa;
   int qb;
-  int S;  // rows per lane of the warp strip: 32 * S >= longest query of the item
-  int pad;
+  int S;     // rows per lane of the warp strip: 32 * S >= longest query of the item
+  int nseg;  // segments of its sweep
 };
 
-// Consecutive items with the same S, swept together by one CTA over one
-// shared stream of reference tiles.
+// Consecutive items with the same S swept over the same segment by one CTA,
+// sharing one stream of reference tiles.
 struct Group {
   int S;
   int first;
   int count;
+  int seg;
+  int nseg;
+  int pad[3];
+};
+
+// Last-row minimum of one unit (item, segment): int16 halves a and b, or fp32.
+struct Best {
+  int ia, ib;
+  float f;
   int pad;
+  int64_t ca, cb;
 };
 
 // Per-item register image: [2][S][32] 32-bit words (INT16: packed query
-// samples, packed caps; FP32: query samples, row weights).
+// codes q and their negations -q, both -4095 on pad rows; FP32: query
+// samples and row weights, 1 on real rows and 0 on pad rows).
 constexpr int kImgStride = 2 * 16 * 32;
+// A saved strip state: the last two oblique columns, [2][S][32] words.
+constexpr int kStateStride = 2 * 16 * 32;
 constexpr int kMaxS = 16;
+constexpr int kMaxSeg = 64;
 constexpr int kQmax = HARU_INT16_QMAX;
 constexpr int kCap = HARU_INT16_CAP;
 // Extra reference columns past N that the tile stream may read: the lane
@@ -39,21 +54,63 @@ constexpr int kCap = HARU_INT16_CAP;
 constexpr int kMaxTile = 16384;
 constexpr long kRefPad = 32 * kMaxS + kMaxTile + 64;
 
+// Strip-height classes, tallest first: S in 13..16, 9..12, 5..8, 1..4.
+constexpr int kClasses = 4;
+
+// Layout of the small integer block every batch uses (status and counters).
+constexpr int kIntStatus = 0, kIntGroups = 1, kIntItems = 2, kIntFixups = 3, kIntQueues = 4, kIntClassFirst = 8,
+              kIntClassCount = 12, kIntClassItemFirst = 16, kIntClassItemCount = 20, kIntWords = 24;
+
+__host__ __device__ inline int steps_per_chunk(int S) { return (S % 2 == 0) ? S : 2 * S; }
+
+// Tile width (columns) for strip height S: a multiple of lcm(U, 4) not above T.
+__host__ __device__ inline int tile_width(int S, int T) {
+  const int U = steps_per_chunk(S);
+  const int g = U % 4 == 0 ? 4 : (U % 2 == 0 ? 2 : 1);
+  const int L = U / g * 4;
+  const int w = (T / L) * L;
+  return w > 0 ? w : L;
+}
+
+// Warm-up steps of a speculative segment: four strip heights of rows.
+__host__ __device__ inline long warmup_steps(int S) {
+  const int U = steps_per_chunk(S);
+  return (4L * 32 * S + U - 1) / U * U;
+}
+
+// Whole-chunk step count of one sweep of strip height S over N columns.
+__host__ __device__ inline long sweep_steps(int S, long N) {
+  const int U = steps_per_chunk(S);
+  return (N + 32L * S - 1 + U - 1) / U * U;
+}
+
+// Steps of segment `seg` of `nseg`: own steps [t_own, t_end), warm-up from t_start.
+__host__ __device__ inline void seg_bounds(int S, int nseg, int seg, long N, long *t_start, long *t_own,
+                                           long *t_end) {
+  const int U = steps_per_chunk(S);
+  const long chunks = sweep_steps(S, N) / U;
+  *t_own = chunks * seg / nseg * U;
+  *t_end = chunks * (seg + 1) / nseg * U;
+  const long w = *t_own - warmup_steps(S);
+  *t_start = seg == 0 ? 0 : (w > 0 ? w : 0);
+}
+
 struct SdtwArgs {
   const void *ref_img;     // INT16: uint32 (r | r << 16); FP32: float. >= N + kRefPad words
   long N;                  // reference length (columns)
   const uint32_t *img;     // item images, kImgStride words each
   const Item *items;
   const Group *groups;
-  const int *n_groups;
-  int *queue;              // work counter, zero before launch
+  int *ints;               // kIntWords status and counter words
+  uint32_t *states;        // [item][nseg_cap][2] saved states (start, final), kStateStride words each
+  Best *bests;             // [item][nseg_cap]
+  int nseg_cap;
   float *out_cost;
   int64_t *out_col;
   float inv_scale;         // INT16: 2^-k
   int tile_cols;           // requested tile width T (columns)
   int warps;               // warps per CTA = items per group
   unsigned long long wait_ns;
-  int *status;             // first error code (0 = none)
 };
 
 // Planner / prep arguments.
@@ -63,12 +120,11 @@ struct PlanArgs {
   long N;
   int pair;                 // 1: INT16 (two queries per item)
   int warps;                // items per group
+  int units_target;         // wanted work units (item x segment) in the batch
+  int nseg_cap;             // most segments per item (state storage is sized for it)
   Item *items;
   Group *groups;
-  int *n_groups;
-  int *n_items;
-  int *queue;
-  int *status;
+  int *ints;                // kIntWords counters (status, counts, queues, class ranges)
 };
 
 struct PackArgs {
@@ -86,9 +142,10 @@ struct PackArgs {
 // Kernel launchers (stream-ordered, no synchronisation).
 cudaError_t launch_plan(const PlanArgs &a, cudaStream_t s);
 cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s);
-cudaError_t launch_sdtw(int precision, const SdtwArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s);
 size_t sdtw_smem_bytes(int tile_cols, int warps);
-int sdtw_max_ctas_per_sm(int precision, int tile_cols, int warps);
+int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps);
+int sdtw_class_of(int S);
 
 // Reference preparation.
 cudaError_t launch_ref_levels(const uint8_t *bases, size_t n, const float *model, int k, float *out,

@@ -22,15 +22,17 @@
 namespace haru {
 namespace {
 
-// Layout of the scratch array (bytes): 4 ints of status and counters, then
-// items, groups and the per-item register images for up to
-// HARU_NOALLOC_MAX_QUERIES queries (the FP32 form needs one item per query,
-// the int16 form one per pair).
+// Layout of the scratch array (bytes): the status and counter words, then
+// items, groups, per-item last-row minima and the per-item register images
+// for up to HARU_NOALLOC_MAX_QUERIES queries (the FP32 form needs one item
+// per query, the int16 form one per pair). This path never splits the
+// reference into segments, so it needs no saved states.
 constexpr size_t kNaItems = HARU_NOALLOC_MAX_QUERIES + kMaxS;
-constexpr size_t kNaHead = 256;
+constexpr size_t kNaHead = 256;  // kIntWords status and counter words
 constexpr size_t kNaItemsOff = kNaHead;
 constexpr size_t kNaGroupsOff = kNaItemsOff + ((kNaItems * sizeof(Item) + 255) / 256) * 256;
-constexpr size_t kNaImgOff = kNaGroupsOff + ((kNaItems * sizeof(Group) + 255) / 256) * 256;
+constexpr size_t kNaBestsOff = kNaGroupsOff + ((kNaItems * sizeof(Group) + 255) / 256) * 256;
+constexpr size_t kNaImgOff = kNaBestsOff + ((kNaItems * sizeof(Best) + 255) / 256) * 256;
 constexpr size_t kNaBytes = kNaImgOff + kNaItems * kImgStride * sizeof(uint32_t);
 
 static __device__ __align__(256) unsigned char scratch[kNaBytes];
@@ -86,35 +88,35 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   int *status = reinterpret_cast<int *>(base);
   Item *items = reinterpret_cast<Item *>(base + kNaItemsOff);
   Group *groups = reinterpret_cast<Group *>(base + kNaGroupsOff);
+  Best *bests = reinterpret_cast<Best *>(base + kNaBestsOff);
   uint32_t *imgs = reinterpret_cast<uint32_t *>(base + kNaImgOff);
   const size_t max_items = precision == HARU_INT16 ? (static_cast<size_t>(nq) + 1) / 2 + kMaxS : nq;
 
   // The array keeps the previous call's contents: the status word and the
   // counters must start at zero; items, groups and images are rewritten.
-  if (cudaMemsetAsync(status, 0, 4 * sizeof(int), s) != cudaSuccess) return HARU_ECUDA;
+  if (cudaMemsetAsync(status, 0, kIntWords * sizeof(int), s) != cudaSuccess) return HARU_ECUDA;
   PlanArgs pa;
   pa.offsets = offsets;
   pa.nq = nq;
   pa.N = N;
   pa.pair = precision == HARU_INT16;
   pa.warps = warps;
+  pa.units_target = 1;
+  pa.nseg_cap = 1;
   pa.items = items;
   pa.groups = groups;
-  pa.n_groups = status + 1;
-  pa.n_items = status + 2;
-  pa.queue = status + 3;
-  pa.status = status;
+  pa.ints = status;
   if (launch_plan(pa, s) != cudaSuccess) return HARU_ECUDA;
   PackArgs ka;
   ka.events = events;
   ka.offsets = offsets;
   ka.items = items;
-  ka.n_items = status + 2;
+  ka.n_items = status + kIntItems;
   ka.img = imgs;
   ka.raw = (flags & HARU_RAW) ? 1 : 0;
   ka.pair = pa.pair;
   ka.scale_log2 = scale;
-  ka.status = status;
+  ka.status = status + kIntStatus;
   if (launch_pack(ka, static_cast<uint32_t>(max_items), s) != cudaSuccess) return HARU_ECUDA;
   SdtwArgs sa;
   sa.ref_img = img;
@@ -122,19 +124,24 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   sa.img = imgs;
   sa.items = items;
   sa.groups = groups;
-  sa.n_groups = status + 1;
-  sa.queue = status + 3;
+  sa.ints = status;
+  sa.states = nullptr;
+  sa.bests = bests;
+  sa.nseg_cap = 1;
   sa.out_cost = out_cost;
   sa.out_col = out_col;
   sa.inv_scale = 1.0f / static_cast<float>(1 << scale);
   sa.tile_cols = tile;
   sa.warps = warps;
   sa.wait_ns = wait;
-  sa.status = status;
   const size_t groups_max = (max_items + warps - 1) / warps + kMaxS;
-  size_t grid = static_cast<size_t>(sms) * (per_sm > 0 ? per_sm : 1);
-  if (grid > groups_max) grid = groups_max;
-  if (launch_sdtw(precision, sa, static_cast<int>(grid), s) != cudaSuccess) return HARU_ECUDA;
+  for (int c = 0; c < kClasses; ++c) {
+    int cps = per_sm > 0 ? per_sm : sdtw_max_ctas_per_sm(precision, c, tile, warps);
+    size_t grid = static_cast<size_t>(sms) * (cps > 0 ? cps : 1);
+    if (grid > groups_max) grid = groups_max;
+    if (launch_sdtw(precision, c, sa, static_cast<int>(grid), static_cast<int>(max_items), s) != cudaSuccess)
+      return HARU_ECUDA;
+  }
   int st = 0;
   if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HARU_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return HARU_ECUDA;

@@ -104,6 +104,8 @@ __global__ void ref_finish_kernel(const float *x, size_t n, const double *stats,
 }
 
 // --------------------------------------------------------------- planner --
+__device__ __forceinline__ int sdtw_class_dev(int S) { return S >= 13 ? 0 : (S >= 9 ? 1 : (S >= 5 ? 2 : 3)); }
+
 __device__ __forceinline__ int strip_rows(const uint32_t *off, uint32_t q, long N, int *status) {
   const uint32_t m = off[q + 1] - off[q];
   const long lim = N < HARU_MAX_QUERY ? N : HARU_MAX_QUERY;
@@ -119,13 +121,14 @@ __device__ __forceinline__ int strip_rows(const uint32_t *off, uint32_t q, long 
 // input order inside a bucket, pairs neighbours for the int16 form, and cuts
 // each bucket into groups of `warps` items.
 __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
-  __shared__ int cnt[kMaxS + 1], run[kMaxS + 1], ibase[kMaxS + 1], icount[kMaxS + 1];
+  __shared__ int cnt[kMaxS + 1], run[kMaxS + 1], ibase[kMaxS + 1], icount[kMaxS + 1], nseg_of[kMaxS + 1];
   __shared__ int wpre[32], wtot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int *status = a.ints + kIntStatus;
   if (tid <= kMaxS) { cnt[tid] = 0; run[tid] = 0; }
   __syncthreads();
   for (uint32_t q = tid; q < a.nq; q += blockDim.x) {
-    const int S = strip_rows(a.offsets, q, a.N, a.status);
+    const int S = strip_rows(a.offsets, q, a.N, status);
     if (S) atomicAdd(&cnt[S], 1);
   }
   __syncthreads();
@@ -136,25 +139,48 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
       ibase[S] = base;
       base += icount[S];
     }
-    *a.n_items = base;
+    a.ints[kIntItems] = base;
+    // Segments per item: enough work units for the machine, each segment
+    // at least four warm-ups (and 2048 steps) long.
+    int want = base > 0 ? (a.units_target + base - 1) / base : 1;
+    if (want < 1) want = 1;
+    if (want > a.nseg_cap) want = a.nseg_cap;
     int g = 0;
-    for (int S = kMaxS; S >= 1; --S)
-      for (int f = 0; f < icount[S]; f += a.warps) {
-        Group gr;
-        gr.S = S;
-        gr.first = ibase[S] + f;
-        gr.count = icount[S] - f < a.warps ? icount[S] - f : a.warps;
-        gr.pad = 0;
-        a.groups[g++] = gr;
+    for (int c = 0; c < kClasses; ++c) {
+      a.ints[kIntClassFirst + c] = g;
+      a.ints[kIntQueues + c] = 0;
+      int ifirst = -1, icnt = 0;
+      for (int S = kMaxS; S >= 1; --S) {
+        if (sdtw_class_dev(S) != c) continue;
+        if (icount[S] > 0 && ifirst < 0) ifirst = ibase[S];
+        icnt += icount[S];
+        const long minlen = 4 * warmup_steps(S) > 2048 ? 4 * warmup_steps(S) : 2048;
+        long lim = sweep_steps(S, a.N) / minlen;
+        if (lim < 1) lim = 1;
+        nseg_of[S] = want < lim ? want : static_cast<int>(lim);
+        for (int seg = 0; seg < nseg_of[S]; ++seg)
+          for (int f = 0; f < icount[S]; f += a.warps) {
+            Group gr;
+            gr.S = S;
+            gr.first = ibase[S] + f;
+            gr.count = icount[S] - f < a.warps ? icount[S] - f : a.warps;
+            gr.seg = seg;
+            gr.nseg = nseg_of[S];
+            gr.pad[0] = gr.pad[1] = gr.pad[2] = 0;
+            a.groups[g++] = gr;
+          }
       }
-    *a.n_groups = g;
-    *a.queue = 0;
+      a.ints[kIntClassCount + c] = g - a.ints[kIntClassFirst + c];
+      a.ints[kIntClassItemFirst + c] = ifirst < 0 ? 0 : ifirst;
+      a.ints[kIntClassItemCount + c] = icnt;
+    }
+    a.ints[kIntGroups] = g;
   }
   __syncthreads();
-  const int n_items = *a.n_items;
+  const int n_items = a.ints[kIntItems];
   for (int i = tid; i < n_items; i += blockDim.x) {
     Item it;
-    it.qa = -1; it.qb = -1; it.S = 0; it.pad = 0;
+    it.qa = -1; it.qb = -1; it.S = 0; it.nseg = 1;
     a.items[i] = it;
   }
   __syncthreads();
@@ -189,11 +215,11 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         const int pos = run[b] + wpre[warp] + __popc(mask & lt);
         if (a.pair) {
           Item *it = &a.items[ibase[b] + pos / 2];
-          if (pos % 2 == 0) { it->qa = static_cast<int>(q); it->S = b; }
+          if (pos % 2 == 0) { it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b]; }
           else it->qb = static_cast<int>(q);
         } else {
           Item it;
-          it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.pad = 0;
+          it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b];
           a.items[ibase[b] + pos] = it;
         }
       }
@@ -268,10 +294,11 @@ __global__ void pack_kernel(PackArgs a) {
         if (!isfinite(z) || fabsf(z) > 1.0e20f) report(a.status, HARU_EINVAL);
       }
       if (a.pair) {
-        const int qv = real ? quantise(z, s) : 0;
-        const uint32_t cap = real ? static_cast<uint32_t>(kCap) : 0u;
+        // real row: (q, -q); pad row: (-4095, -4095), read by the sweep as distance 0
+        const int qv = real ? quantise(z, s) : -4095;
+        const int nv = real ? -qv : -4095;
         w0 |= (static_cast<uint32_t>(qv) & 0xffffu) << (16 * h);
-        w1 |= cap << (16 * h);
+        w1 |= (static_cast<uint32_t>(nv) & 0xffffu) << (16 * h);
       } else {
         w0 = __float_as_uint(z);
         w1 = __float_as_uint(real ? 1.0f : 0.0f);

@@ -20,16 +20,27 @@
 // CAP, pad rows have cap 0. FP32 form: one query per warp, 3-input min.f32,
 // pad rows have weight 0 in gamma = fma(|q - r|, w, min3).
 //
+// Segments. The steps of one query are cut into segments that run as
+// independent work units. Segment s > 0 starts V steps early from a fresh
+// state (as if the reference began there) and records its state (the last
+// two oblique columns) when it reaches its own first step B_s; segment s-1
+// records its exact state at the same step. The fix-up kernel compares the
+// two: equal states give identical computations from B_s on (the DP is a
+// deterministic function of that state and the reference), so the segment's
+// results stand; otherwise it recomputes the segment from the exact state.
+// The result is always the plain DP's.
+//
 // The reference streams through shared memory: every CTA sweeps a group of
-// warps (same S) over the same columns; tiles of T_S columns are fetched by
-// cp.async.bulk (TMA) into a two-slot ring guarded by mbarriers. The warp
-// that releases a slot last issues the copy of the tile two ahead.
+// warps (same S, same segment) over the same columns; tiles of T_S columns
+// are fetched by cp.async.bulk (TMA) into a two-slot ring guarded by
+// mbarriers. The warp that releases a slot last issues the copy of the tile
+// two ahead.
 //
 // The last-row minimum and its first column (Algorithm 1's final scan,
 // Algorithm 2's per-column compare) are tracked through a small per-warp
 // shared ring: lane 31 stores its bottom-row cost every step, and every
-// <= 32 steps each lane scans one stored value; a warp reduction at the end
-// keeps the smallest cost, then the smallest column.
+// <= 32 steps each lane scans one stored value; a warp reduction keeps the
+// smallest cost, then the smallest column.
 //
 // Every wait is bounded by a global-timer deadline; on expiry the kernel
 // records HARU_ETIMEDOUT, waits (bounded) for its own copies in flight and
@@ -90,25 +101,266 @@ __device__ __forceinline__ float fmin3f(float a, float b, float c) {
   return d;
 }
 
-constexpr int cx_gcd(int a, int b) { return b == 0 ? a : cx_gcd(b, a % b); }
-constexpr int cx_lcm(int a, int b) { return a / cx_gcd(a, b) * b; }
+// d = a * b + c on the integer multiply-add unit (keeps lane-0 fix-ups off
+// the half-rate pipe that the DPX min/max instructions use).
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Reference sample of step u of a chunk, read 4 (or 2) at a time: `ref` is
+// 16-byte (8-byte) aligned whenever U is a multiple of 4 (2).
+template <int U>
+struct RefWindow {
+  uint4 v4;
+  uint2 v2;
+  __device__ __forceinline__ uint32_t get(const uint32_t *ref, int u) {
+    if constexpr (U % 4 == 0) {
+      if (u % 4 == 0) v4 = reinterpret_cast<const uint4 *>(ref)[u / 4];
+      const int c = u % 4;
+      return c == 0 ? v4.x : (c == 1 ? v4.y : (c == 2 ? v4.z : v4.w));
+    } else if constexpr (U % 2 == 0) {
+      if (u % 2 == 0) v2 = reinterpret_cast<const uint2 *>(ref)[u / 2];
+      return (u % 2 == 0) ? v2.x : v2.y;
+    } else {
+      return ref[u];
+    }
+  }
+};
 
 template <int S>
 struct Geo {
-  static constexpr int U = (S % 2 == 0) ? S : 2 * S;  // steps per unrolled chunk (register renaming period)
+  static constexpr int U = (S % 2 == 0) ? S : 2 * S;    // steps per unrolled chunk (register renaming period)
   static constexpr int F = (32 / U) > 0 ? (32 / U) : 1; // chunks per tracking flush
-  static constexpr int E = F * U;                      // tracked steps per flush (<= 32)
-  static constexpr int L = cx_lcm(U, 4);               // tile widths are multiples of L
 };
 
-__host__ __device__ inline int tile_width(int S, int T) {
-  int U = (S % 2 == 0) ? S : 2 * S;
-  int g = U % 4 == 0 ? 4 : (U % 2 == 0 ? 2 : 1);
-  int L = U / g * 4;  // lcm(U, 4)
-  int w = (T / L) * L;
-  return w > 0 ? w : L;
-}
+// ---------------------------------------------------------------- INT16 --
+// Pad rows carry the code -4095 in both Q and NQ: |q - r| is then taken as
+// relu(max(r + NQ, Q - r)) = relu(negative) = 0, so a pad row stays 0 (the
+// free-start row) without a per-row cap, and real rows (|q|, |r| <= 2047)
+// get max(r - q, q - r) unchanged.
+constexpr uint32_t kPadQ2 = 0xf001f001u;  // -4095 in both halves
+constexpr uint32_t kCap2 = (static_cast<uint32_t>(kCap) << 16) | static_cast<uint32_t>(kCap);
 
+template <int S>
+struct StripI16 {
+  uint32_t Q[S], NQ[S], G[2][S], Rr[S];
+  uint32_t gprev;
+
+  __device__ __forceinline__ void load(const uint32_t *img, int lane) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      Q[k] = img[k * 32 + lane];
+      NQ[k] = img[(S + k) * 32 + lane];
+    }
+  }
+  // Initial value of row k of this lane: CAP (infinity) for a real row, 0 for a pad row.
+  __device__ __forceinline__ uint32_t init(int k) const { return ~__vcmpeq2(Q[k], kPadQ2) & kCap2; }
+  // As if the reference began at the current step: every row at its initial
+  // value; the masked chunks hold rows that have not reached their first
+  // column at that value.
+  __device__ __forceinline__ void fresh() {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[0][k] = init(k);
+      G[1][k] = G[0][k];
+      Rr[k] = 0u;
+    }
+    gprev = 0u;
+  }
+  // Exact state before step t: G[1] = step t-1, G[0] = step t-2, and the
+  // reference samples the cells used at step t-1 (from the global image).
+  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[1][k] = st[k * 32 + lane];
+      G[0][k] = st[(S + k) * 32 + lane];
+      Rr[(1 + k) % S] = gref[t - 1 - static_cast<long>(lane) * S - k];
+    }
+    const uint32_t g = __shfl_up_sync(kFull, G[0][S - 1], 1);
+    gprev = lane ? g : 0u;
+  }
+  __device__ __forceinline__ void save(uint32_t *st, int lane) const {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      st[k * 32 + lane] = G[1][k];
+      st[(S + k) * 32 + lane] = G[0][k];
+    }
+  }
+
+  template <bool MASK>
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t nl,
+                                        uint32_t l0) {
+    constexpr int U = Geo<S>::U;
+    RefWindow<U> win;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = (S - (u % S)) % S;
+      const int a = (u + 1) & 1;
+      const int b = u & 1;
+      uint32_t gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
+      uint32_t rin = __shfl_up_sync(kFull, Rr[p], 1);
+      const uint32_t rv = win.get(ref, u);
+      gup = imad(gup, nl, 0u);               // lane 0: the free-start row, 0
+      rin = imad(rin, nl, imad(rv, l0, 0u));  // lane 0: reference sample t
+      Rr[p] = rin;
+#pragma unroll
+      for (int k = S - 1; k >= 0; --k) {
+        const uint32_t r = Rr[(p + k) % S];
+        const uint32_t d = __viaddmax_s16x2_relu(r, NQ[k], __vsub2(Q[k], r));  // |q - r| per half
+        const uint32_t up = k ? G[a][k - 1] : gup;
+        const uint32_t dg = k ? G[b][k - 1] : gprev;
+        const uint32_t m = __vimin3_s16x2(up, dg, G[a][k]);
+        uint32_t v = __viaddmin_s16x2(d, m, kCap2);
+        if (MASK) v = (trel + u - lane * S >= k) ? v : init(k);
+        G[b][k] = v;
+      }
+      gprev = gup;
+      if (lane == 31) ring[e0 + u] = G[b][S - 1];
+    }
+  }
+};
+
+struct TrackI16 {
+  int ba = 0x7fffffff, bb = 0x7fffffff;
+  long ca = -1, cb = -1;
+  __device__ __forceinline__ void add(uint32_t v, long c) {
+    const int va = static_cast<int>(v & 0xffffu);
+    const int vb = static_cast<int>(v >> 16);
+    if (va < ba) { ba = va; ca = c; }
+    if (vb < bb) { bb = vb; cb = c; }
+  }
+  __device__ __forceinline__ void reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      int oa = __shfl_xor_sync(kFull, ba, o), ob = __shfl_xor_sync(kFull, bb, o);
+      long pa = __shfl_xor_sync(kFull, ca, o), pb = __shfl_xor_sync(kFull, cb, o);
+      if (oa < ba || (oa == ba && static_cast<unsigned long>(pa) < static_cast<unsigned long>(ca))) { ba = oa; ca = pa; }
+      if (ob < bb || (ob == bb && static_cast<unsigned long>(pb) < static_cast<unsigned long>(cb))) { bb = ob; cb = pb; }
+    }
+  }
+  __device__ __forceinline__ void store(Best *b) const {
+    b->ia = ba; b->ib = bb; b->f = 0.0f; b->pad = 0; b->ca = ca; b->cb = cb;
+  }
+};
+
+// ----------------------------------------------------------------- FP32 --
+template <int S>
+struct StripF32 {
+  float Q[S], W[S], G[2][S], Rr[S];
+  float gprev;
+
+  __device__ __forceinline__ void load(const uint32_t *img, int lane) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      Q[k] = __uint_as_float(img[k * 32 + lane]);
+      W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
+    }
+  }
+  __device__ __forceinline__ void fresh() {
+    const float kBig = 1.0e30f;  // stands for +inf; sums of these stay finite
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[0][k] = W[k] != 0.0f ? kBig : 0.0f;
+      G[1][k] = G[0][k];
+      Rr[k] = kBig;  // columns before the start: distance ~1e30 for real rows, weight 0 for pad rows
+    }
+    gprev = 0.0f;
+  }
+  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[1][k] = __uint_as_float(st[k * 32 + lane]);
+      G[0][k] = __uint_as_float(st[(S + k) * 32 + lane]);
+      Rr[(1 + k) % S] = __uint_as_float(gref[t - 1 - static_cast<long>(lane) * S - k]);
+    }
+    const float g = __shfl_up_sync(kFull, G[0][S - 1], 1);
+    gprev = lane ? g : 0.0f;
+  }
+  __device__ __forceinline__ void save(uint32_t *st, int lane) const {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      st[k * 32 + lane] = __float_as_uint(G[1][k]);
+      st[(S + k) * 32 + lane] = __float_as_uint(G[0][k]);
+    }
+  }
+
+  template <bool MASK>
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t nl,
+                                        uint32_t l0) {
+    (void)trel;
+    (void)nl;
+    (void)l0;
+    constexpr int U = Geo<S>::U;
+    RefWindow<U> win;
+    float *fring = reinterpret_cast<float *>(ring);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = (S - (u % S)) % S;
+      const int a = (u + 1) & 1;
+      const int b = u & 1;
+      float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
+      float rin = __shfl_up_sync(kFull, Rr[p], 1);
+      const float rv = __uint_as_float(win.get(ref, u));
+      gup = lane ? gup : 0.0f;
+      rin = lane ? rin : rv;
+      Rr[p] = rin;
+#pragma unroll
+      for (int k = S - 1; k >= 0; --k) {
+        const float r = Rr[(p + k) % S];
+        const float d = __fsub_rn(Q[k], r);
+        const float up = k ? G[a][k - 1] : gup;
+        const float dg = k ? G[b][k - 1] : gprev;
+        const float m = fmin3f(up, dg, G[a][k]);
+        G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
+      }
+      gprev = gup;
+      if (lane == 31) fring[e0 + u] = G[b][S - 1];
+    }
+  }
+};
+
+struct TrackF32 {
+  float best;
+  long col;
+  __device__ TrackF32() : best(__builtin_huge_valf()), col(-1) {}
+  __device__ __forceinline__ void add(uint32_t v, long c) {
+    const float f = __uint_as_float(v);
+    if (f < best) { best = f; col = c; }
+  }
+  __device__ __forceinline__ void reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float ob = __shfl_xor_sync(kFull, best, o);
+      long oc = __shfl_xor_sync(kFull, col, o);
+      if (ob < best || (ob == best && static_cast<unsigned long>(oc) < static_cast<unsigned long>(col))) {
+        best = ob;
+        col = oc;
+      }
+    }
+  }
+  __device__ __forceinline__ void store(Best *b) const {
+    b->ia = 0; b->ib = 0; b->f = best; b->pad = 0; b->ca = col; b->cb = -1;
+  }
+};
+
+template <int PREC, int S>
+struct FormOf;
+template <int S>
+struct FormOf<HARU_INT16, S> {
+  using Strip = StripI16<S>;
+  using Track = TrackI16;
+  static constexpr bool kMasked = true;
+};
+template <int S>
+struct FormOf<HARU_FP32, S> {
+  using Strip = StripF32<S>;
+  using Track = TrackF32;
+  static constexpr bool kMasked = false;
+};
+
+// ----------------------------------------------------------- tile sources --
 // Shared state of one CTA.
 struct Shared {
   uint64_t full[2];
@@ -120,40 +372,43 @@ struct Shared {
   int pad;
 };
 
+// Reference tiles streamed into shared memory by TMA (the sweep kernel).
 struct TileStream {
   Shared *sh;
-  char *slots;                 // 2 slots of slot_bytes
+  char *slots;                 // two slots of tile_cols words
   const char *src;             // reference image
   int tile_cols;               // T_S
+  int k_first;                 // first global tile of this group's steps
   int K;                       // tiles in this group's sweep
   int n_active;                // warps consuming this stream
   unsigned long long wait_ns;  // longest single wait
+  int *status;
 
   __device__ void issue(int k) {  // one thread
-    int gk = sh->tile_base + k;
-    int slot = gk & 1;
-    unsigned bytes = static_cast<unsigned>(tile_cols) * 4u;
+    const int gk = sh->tile_base + k;
+    const int slot = gk & 1;
+    const unsigned bytes = static_cast<unsigned>(tile_cols) * 4u;
     fence_proxy_async();
     mbar_expect_tx(&sh->full[slot], bytes);
-    tma_load_1d(slots + static_cast<size_t>(slot) * tile_cols * 4, src + static_cast<size_t>(k) * tile_cols * 4,
-                bytes, &sh->full[slot]);
+    tma_load_1d(slots + static_cast<size_t>(slot) * tile_cols * 4,
+                src + static_cast<size_t>(k_first + k) * tile_cols * 4, bytes, &sh->full[slot]);
     sh->uses[slot] += 1;
   }
-  __device__ const char *acquire(int k, int *status) {  // whole warp
-    int gk = sh->tile_base + k;
-    int slot = gk & 1;
+  __device__ const uint32_t *acquire(int k) {  // whole warp
+    const int gk = sh->tile_base + k;
+    const int slot = gk & 1;
     if (!mbar_wait_bounded(&sh->full[slot], (gk >> 1) & 1, now_ns() + wait_ns)) {
       report(status, HARU_ETIMEDOUT);
       sh->abort = 1;
       return nullptr;
     }
-    return slots + static_cast<size_t>(slot) * tile_cols * 4;
+    return reinterpret_cast<const uint32_t *>(slots + static_cast<size_t>(slot) * tile_cols * 4);
   }
   __device__ void release(int k) {  // lane 0 of a warp
-    int gk = sh->tile_base + k;
-    int slot = gk & 1;
+    const int gk = sh->tile_base + k;
+    const int slot = gk & 1;
     __threadfence_block();
-    int old = atomicAdd(&sh->cnt[slot], 1);
+    const int old = atomicAdd(&sh->cnt[slot], 1);
     if (old == n_active - 1) {
       sh->cnt[slot] = 0;
       __threadfence_block();
@@ -162,189 +417,55 @@ struct TileStream {
   }
 };
 
-// ---------------------------------------------------------------- INT16 --
-template <int S, bool MASK>
-__device__ __forceinline__ void chunk_i16(const uint32_t (&Q)[S], const uint32_t (&NQ)[S], const uint32_t (&C)[S],
-                                          uint32_t (&G)[2][S], uint32_t (&Rr)[S], uint32_t &gprev,
-                                          const uint32_t *ref, int t0, int lane, uint32_t *ring, int e0) {
-  constexpr int U = Geo<S>::U;
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int p = (S - (u % S)) % S;
-    const int a = (u + 1) & 1;
-    const int b = u & 1;
-    uint32_t gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
-    uint32_t rin = __shfl_up_sync(kFull, Rr[p], 1);
-    const uint32_t rv = ref[u];
-    gup = lane ? gup : 0u;
-    rin = lane ? rin : rv;
-    Rr[p] = rin;
-#pragma unroll
-    for (int k = S - 1; k >= 0; --k) {
-      const uint32_t r = Rr[(p + k) % S];
-      const uint32_t d = __viaddmax_s16x2(r, NQ[k], __vsub2(Q[k], r));  // |q - r| per half
-      const uint32_t up = k ? G[a][k - 1] : gup;
-      const uint32_t dg = k ? G[b][k - 1] : gprev;
-      const uint32_t m = __vimin3_s16x2(up, dg, G[a][k]);
-      uint32_t v = __viaddmin_s16x2(d, m, C[k]);
-      if (MASK) v = (t0 + u - lane * S >= k) ? v : C[k];
-      G[b][k] = v;
-    }
-    gprev = gup;
-    if (lane == 31) ring[e0 + u] = G[b][S - 1];
+// The reference read straight from global memory (the fix-up kernel).
+struct GlobalTiles {
+  const uint32_t *img;
+  int tile_cols;
+  long k_first;
+  __device__ __forceinline__ const uint32_t *acquire(int k) {
+    return img + static_cast<size_t>(k_first + k) * tile_cols;
   }
-}
+  __device__ __forceinline__ void release(int) {}
+};
 
-__device__ __forceinline__ void track_i16(uint32_t v, long c, long N, int &ba, int &bb, long &ca, long &cb) {
-  if (c >= 0 && c < N) {
-    const int va = static_cast<int>(v & 0xffffu);
-    const int vb = static_cast<int>(v >> 16);
-    if (va < ba) { ba = va; ca = c; }
-    if (vb < bb) { bb = vb; cb = c; }
-  }
-}
-
-template <int S>
-__device__ void sweep_i16(const SdtwArgs &A, TileStream &ts, int item, uint32_t *ring, int lane) {
-  constexpr int U = Geo<S>::U, F = Geo<S>::F, E = Geo<S>::E;
-  const Item it = A.items[item];
-  const uint32_t *img = A.img + static_cast<size_t>(item) * kImgStride;
-  uint32_t Q[S], NQ[S], C[S], G[2][S], Rr[S];
-#pragma unroll
-  for (int k = 0; k < S; ++k) {
-    Q[k] = img[k * 32 + lane];
-    C[k] = img[(S + k) * 32 + lane];
-    NQ[k] = __vsub2(0u, Q[k]);
-    G[0][k] = C[k];
-    G[1][k] = C[k];
-    Rr[k] = 0u;
-  }
-  uint32_t gprev = 0u;
-  int ba = 0x7fffffff, bb = 0x7fffffff;
-  long ca = -1, cb = -1;
-  const long N = A.N;
-  const long total = N + 32L * S - 1;           // steps of the sweep
-  const long tstop = (total + U - 1) / U * U;   // whole chunks
-  const int TS = ts.tile_cols;                  // multiple of U
-  const int K = ts.K;
-  const int prologue = 32 * S;                  // masked steps (multiple of U)
-  int fl = 0, buf = 0;
-  long tflush = 0;
-  bool ok = true;
-  for (int k = 0; k < K && ok; ++k) {
-    const char *tile = ts.acquire(k, A.status);
-    if (!tile) { ok = false; break; }
-    const uint32_t *tref = reinterpret_cast<const uint32_t *>(tile);
-    const long tk0 = static_cast<long>(k) * TS;
-    const long tend = tk0 + TS < tstop ? tk0 + TS : tstop;
-    for (long t0 = tk0; t0 < tend; t0 += U) {
-      const uint32_t *ref = tref + (t0 - tk0);
-      uint32_t *rg = ring + buf * 32;
-      if (t0 < prologue)
-        chunk_i16<S, true>(Q, NQ, C, G, Rr, gprev, ref, static_cast<int>(t0), lane, rg, fl * U);
-      else
-        chunk_i16<S, false>(Q, NQ, C, G, Rr, gprev, ref, 0, lane, rg, fl * U);
-      if (++fl == F || t0 + U >= total) {
-        __syncwarp();
-        if (lane < fl * U) track_i16(rg[lane], tflush + lane - (32L * S - 1), N, ba, bb, ca, cb);
-        tflush += static_cast<long>(fl) * U;
-        fl = 0;
-        buf ^= 1;
-      }
-    }
-    __syncwarp();
-    if (lane == 0) ts.release(k);
-  }
-  (void)E;
-  // warp reduction: smallest cost, then smallest column
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    int oa = __shfl_xor_sync(kFull, ba, o), ob = __shfl_xor_sync(kFull, bb, o);
-    long pa = __shfl_xor_sync(kFull, ca, o), pb = __shfl_xor_sync(kFull, cb, o);
-    if (oa < ba || (oa == ba && static_cast<unsigned long>(pa) < static_cast<unsigned long>(ca))) { ba = oa; ca = pa; }
-    if (ob < bb || (ob == bb && static_cast<unsigned long>(pb) < static_cast<unsigned long>(cb))) { bb = ob; cb = pb; }
-  }
-  if (lane == 0 && ok) {
-    A.out_cost[it.qa] = static_cast<float>(ba) * A.inv_scale;
-    A.out_col[it.qa] = ca;
-    if (it.qb >= 0) {
-      A.out_cost[it.qb] = static_cast<float>(bb) * A.inv_scale;
-      A.out_col[it.qb] = cb;
-    }
-  }
-}
-
-// ----------------------------------------------------------------- FP32 --
-template <int S>
-__device__ __forceinline__ void chunk_f32(const float (&Q)[S], const float (&W)[S], float (&G)[2][S], float (&Rr)[S],
-                                          float &gprev, const float *ref, int lane, float *ring, int e0) {
-  constexpr int U = Geo<S>::U;
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int p = (S - (u % S)) % S;
-    const int a = (u + 1) & 1;
-    const int b = u & 1;
-    float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
-    float rin = __shfl_up_sync(kFull, Rr[p], 1);
-    const float rv = ref[u];
-    gup = lane ? gup : 0.0f;
-    rin = lane ? rin : rv;
-    Rr[p] = rin;
-#pragma unroll
-    for (int k = S - 1; k >= 0; --k) {
-      const float r = Rr[(p + k) % S];
-      const float d = __fsub_rn(Q[k], r);
-      const float up = k ? G[a][k - 1] : gup;
-      const float dg = k ? G[b][k - 1] : gprev;
-      const float m = fmin3f(up, dg, G[a][k]);
-      G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
-    }
-    gprev = gup;
-    if (lane == 31) ring[e0 + u] = G[b][S - 1];
-  }
-}
-
-template <int S>
-__device__ void sweep_f32(const SdtwArgs &A, TileStream &ts, int item, float *ring, int lane) {
+// ------------------------------------------------------------ one unit --
+// Runs steps [t_start, t_end) of one strip (a query or a pair) and tracks
+// the last row over own steps [t_own, t_end). fresh: the strip starts from
+// the fresh state at t_start (masked prologue for the int16 form).
+// save_start / save_final: where to store the state before step t_own and
+// before step t_end (nullptr: not stored). Returns false on abort.
+template <int PREC, int S, class Src>
+__device__ bool run_steps(typename FormOf<PREC, S>::Strip &st, typename FormOf<PREC, S>::Track &tr, Src &src,
+                          int TS, long t_start, long t_own, long t_end, bool fresh, long N, uint32_t *save_start,
+                          uint32_t *save_final, uint32_t *ring, int lane) {
   constexpr int U = Geo<S>::U, F = Geo<S>::F;
-  const Item it = A.items[item];
-  const uint32_t *img = A.img + static_cast<size_t>(item) * kImgStride;
-  float Q[S], W[S], G[2][S], Rr[S];
-  const float kBig = 1.0e30f;  // stands for +inf; sums of these stay finite
-#pragma unroll
-  for (int k = 0; k < S; ++k) {
-    Q[k] = __uint_as_float(img[k * 32 + lane]);
-    W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
-    G[0][k] = W[k] != 0.0f ? kBig : 0.0f;
-    G[1][k] = G[0][k];
-    Rr[k] = kBig;  // columns before the reference start: distance ~1e30 for real rows
-  }
-  float gprev = 0.0f;
-  float best = __int_as_float(0x7f800000);
-  long col = -1;
-  const long N = A.N;
-  const long total = N + 32L * S - 1;
-  const long tstop = (total + U - 1) / U * U;
-  const int TS = ts.tile_cols;
-  const int K = ts.K;
+  constexpr bool kMasked = FormOf<PREC, S>::kMasked;
+  const uint32_t nl = lane != 0 ? 1u : 0u, l0 = 1u - nl;
+  const long mask_end = fresh ? t_start + 32L * S : t_start;
+  const long k_first = t_start / TS;
+  const int K = static_cast<int>((t_end + TS - 1) / TS - k_first);
   int fl = 0, buf = 0;
-  long tflush = 0;
-  bool ok = true;
-  for (int k = 0; k < K && ok; ++k) {
-    const char *tile = ts.acquire(k, A.status);
-    if (!tile) { ok = false; break; }
-    const float *tref = reinterpret_cast<const float *>(tile);
-    const long tk0 = static_cast<long>(k) * TS;
-    const long tend = tk0 + TS < tstop ? tk0 + TS : tstop;
-    for (long t0 = tk0; t0 < tend; t0 += U) {
-      float *rg = ring + buf * 32;
-      chunk_f32<S>(Q, W, G, Rr, gprev, tref + (t0 - tk0), lane, rg, fl * U);
-      if (++fl == F || t0 + U >= total) {
+  long tflush = t_start;
+  for (int k = 0; k < K; ++k) {
+    const uint32_t *tile = src.acquire(k);
+    if (!tile) return false;
+    const long tk0 = (k_first + k) * TS;
+    const long lo = tk0 > t_start ? tk0 : t_start;
+    const long hi = tk0 + TS < t_end ? tk0 + TS : t_end;
+    for (long t0 = lo; t0 < hi; t0 += U) {
+      if (save_start && t0 == t_own) st.save(save_start, lane);
+      uint32_t *rg = ring + buf * 32;
+      const uint32_t *ref = tile + (t0 - tk0);
+      if (kMasked && t0 < mask_end)
+        st.template chunk<true>(ref, static_cast<int>(t0 - t_start), lane, rg, fl * U, nl, l0);
+      else
+        st.template chunk<false>(ref, 0, lane, rg, fl * U, nl, l0);
+      if (++fl == F || t0 + U >= t_end) {
         __syncwarp();
         if (lane < fl * U) {
-          const long c = tflush + lane - (32L * S - 1);
-          const float v = rg[lane];
-          if (c >= 0 && c < N && v < best) { best = v; col = c; }
+          const long t = tflush + lane;
+          const long c = t - (32L * S - 1);
+          if (t >= t_own && c >= 0 && c < N) tr.add(rg[lane], c);
         }
         tflush += static_cast<long>(fl) * U;
         fl = 0;
@@ -352,43 +473,55 @@ __device__ void sweep_f32(const SdtwArgs &A, TileStream &ts, int item, float *ri
       }
     }
     __syncwarp();
-    if (lane == 0) ts.release(k);
+    if (lane == 0) src.release(k);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    float ob = __shfl_xor_sync(kFull, best, o);
-    long oc = __shfl_xor_sync(kFull, col, o);
-    if (ob < best || (ob == best && static_cast<unsigned long>(oc) < static_cast<unsigned long>(col))) {
-      best = ob;
-      col = oc;
-    }
-  }
-  if (lane == 0 && ok) {
-    A.out_cost[it.qa] = best;
-    A.out_col[it.qa] = col;
+  if (save_final) st.save(save_final, lane);
+  return true;
+}
+
+// Speculative sweep of one unit (item, segment) in the sweep kernel.
+template <int PREC, int S>
+__device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, int item, uint32_t *ring,
+                           int lane) {
+  typename FormOf<PREC, S>::Strip st;
+  typename FormOf<PREC, S>::Track tr;
+  st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
+  st.fresh();
+  long t_start, t_own, t_end;
+  seg_bounds(S, g.nseg, g.seg, A.N, &t_start, &t_own, &t_end);
+  uint32_t *ss = nullptr, *sf = nullptr;
+  const size_t unit = static_cast<size_t>(item) * A.nseg_cap + g.seg;
+  if (g.seg > 0) ss = A.states + (unit * 2 + 0) * kStateStride;
+  if (g.seg + 1 < g.nseg) sf = A.states + (unit * 2 + 1) * kStateStride;
+  const bool ok = run_steps<PREC, S>(st, tr, ts, ts.tile_cols, t_start, t_own, t_end, true, A.N, ss, sf, ring, lane);
+  tr.reduce();
+  if (ok && lane == 0) tr.store(A.bests + unit);
+}
+
+// Strip heights of one kernel class: registers are allocated for the
+// tallest strip a kernel can meet, so short strips get their own kernels.
+template <int CLS>
+struct Cls;
+template <> struct Cls<0> { static constexpr int lo = 13, hi = 16; };
+template <> struct Cls<1> { static constexpr int lo = 9, hi = 12; };
+template <> struct Cls<2> { static constexpr int lo = 5, hi = 8; };
+template <> struct Cls<3> { static constexpr int lo = 1, hi = 4; };
+
+template <int PREC, int CLS, int S = Cls<CLS>::lo>
+__device__ __forceinline__ void dispatch_sweep(int s, const SdtwArgs &A, TileStream &ts, const Group &g, int item,
+                                               uint32_t *ring, int lane) {
+  if constexpr (S <= Cls<CLS>::hi) {
+    if (s == S)
+      sweep_unit<PREC, S>(A, ts, g, item, ring, lane);
+    else
+      dispatch_sweep<PREC, CLS, S + 1>(s, A, ts, g, item, ring, lane);
   }
 }
 
-template <int PREC>
-__device__ void dispatch(int S, const SdtwArgs &A, TileStream &ts, int item, uint32_t *ring, int lane) {
-#define HARU_CASE(s)                                                             \
-  case s:                                                                        \
-    if (PREC == HARU_INT16)                                                      \
-      sweep_i16<s>(A, ts, item, ring, lane);                                     \
-    else                                                                         \
-      sweep_f32<s>(A, ts, item, reinterpret_cast<float *>(ring), lane);          \
-    break;
-  switch (S) {
-    HARU_CASE(1) HARU_CASE(2) HARU_CASE(3) HARU_CASE(4) HARU_CASE(5) HARU_CASE(6) HARU_CASE(7) HARU_CASE(8)
-    HARU_CASE(9) HARU_CASE(10) HARU_CASE(11) HARU_CASE(12) HARU_CASE(13) HARU_CASE(14) HARU_CASE(15)
-    HARU_CASE(16)
-    default: break;
-  }
-#undef HARU_CASE
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(256, 1) sdtw_kernel(SdtwArgs A) {
+// Two CTAs (16 warps) per SM for strips up to 12 rows per lane; the tallest
+// class needs more registers than that allows without spilling.
+template <int PREC, int CLS>
+__global__ void __launch_bounds__(256, CLS == 0 ? 1 : 2) sdtw_kernel(SdtwArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared *sh = reinterpret_cast<Shared *>(smem);
   uint32_t *rings = reinterpret_cast<uint32_t *>(smem + 128);
@@ -404,40 +537,149 @@ __global__ void __launch_bounds__(256, 1) sdtw_kernel(SdtwArgs A) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int n_groups = *A.n_groups;
+  const int first = A.ints[kIntClassFirst + CLS];
+  const int count = A.ints[kIntClassCount + CLS];
+  int *queue = A.ints + kIntQueues + CLS;
   for (;;) {
-    if (threadIdx.x == 0) sh->group = atomicAdd(A.queue, 1);
+    if (threadIdx.x == 0) sh->group = atomicAdd(queue, 1);
     __syncthreads();
-    const int g = sh->group;
-    if (g >= n_groups || sh->abort) break;
-    const Group grp = A.groups[g];
+    const int gi = sh->group;
+    if (gi >= count || sh->abort) break;
+    const Group grp = A.groups[first + gi];
     const int S = grp.S;
     const int TS = tile_width(S, A.tile_cols);
-    const long total = A.N + 32L * S - 1;
+    long t_start, t_own, t_end;
+    seg_bounds(S, grp.nseg, grp.seg, A.N, &t_start, &t_own, &t_end);
     TileStream ts;
     ts.sh = sh;
     ts.slots = slots;
     ts.src = reinterpret_cast<const char *>(A.ref_img);
     ts.tile_cols = TS;
-    ts.K = static_cast<int>((total + TS - 1) / TS);
+    ts.k_first = static_cast<int>(t_start / TS);
+    ts.K = static_cast<int>((t_end + TS - 1) / TS - t_start / TS);
     ts.n_active = grp.count;
     ts.wait_ns = A.wait_ns;
+    ts.status = A.ints + kIntStatus;
     if (threadIdx.x == 0) {
       ts.issue(0);
       if (ts.K > 1) ts.issue(1);
     }
     __syncthreads();
-    if (warp < grp.count) dispatch<PREC>(S, A, ts, grp.first + warp, rings + warp * 64, lane);
+    if (warp < grp.count) dispatch_sweep<PREC, CLS>(S, A, ts, grp, grp.first + warp, rings + warp * 64, lane);
     __syncthreads();
     if (threadIdx.x == 0) sh->tile_base += ts.K;
   }
   // On abort, wait (bounded) for this CTA's copies still in flight before exit.
   __syncthreads();
   if (threadIdx.x == 0 && sh->abort) {
-    unsigned long long dl = now_ns() + A.wait_ns;
+    const unsigned long long dl = now_ns() + A.wait_ns;
     for (int s = 0; s < 2; ++s)
       if (sh->uses[s] > 0) mbar_wait_bounded(&sh->full[s], (sh->uses[s] - 1) & 1, dl);
   }
+}
+
+// --------------------------------------------------------------- fix-up --
+// One warp per item: verify every segment boundary, recompute segments whose
+// speculative start state differs from the exact one, combine the segments'
+// last-row minima (smallest cost, then smallest column) and write the
+// outputs.
+template <int PREC, int S>
+__device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane) {
+  const Item it = A.items[item];
+  const int nseg = it.nseg;
+  const size_t base = static_cast<size_t>(item) * A.nseg_cap;
+  Best b = A.bests[base];
+  if (nseg > 1) {
+    typename FormOf<PREC, S>::Strip st;
+    st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
+    const int TS = tile_width(S, A.tile_cols);
+    for (int s = 1; s < nseg; ++s) {
+      const uint32_t *exact = A.states + ((base + s - 1) * 2 + 1) * kStateStride;
+      const uint32_t *spec = A.states + ((base + s) * 2 + 0) * kStateStride;
+      bool eq = true;
+      for (int k = 0; k < 2 * S; ++k) eq = eq && exact[k * 32 + lane] == spec[k * 32 + lane];
+      if (!__all_sync(kFull, eq)) {
+        long t_start, t_own, t_end;
+        seg_bounds(S, nseg, s, A.N, &t_start, &t_own, &t_end);
+        st.restore(exact, reinterpret_cast<const uint32_t *>(A.ref_img), t_own, lane);
+        typename FormOf<PREC, S>::Track tr;
+        GlobalTiles src{reinterpret_cast<const uint32_t *>(A.ref_img), TS, t_own / TS};
+        uint32_t *sf = s + 1 < nseg ? A.states + ((base + s) * 2 + 1) * kStateStride : nullptr;
+        run_steps<PREC, S>(st, tr, src, TS, t_own, t_own, t_end, false, A.N, nullptr, sf, ring, lane);
+        tr.reduce();
+        if (lane == 0) {
+          tr.store(A.bests + base + s);
+          atomicAdd(A.ints + kIntFixups, 1);
+        }
+        __syncwarp();
+      }
+      const Best o = A.bests[base + s];
+      if (PREC == HARU_INT16) {
+        if (o.ia < b.ia) { b.ia = o.ia; b.ca = o.ca; }
+        if (o.ib < b.ib) { b.ib = o.ib; b.cb = o.cb; }
+      } else {
+        if (o.f < b.f) { b.f = o.f; b.ca = o.ca; }
+      }
+    }
+  }
+  if (lane == 0) {
+    if (PREC == HARU_INT16) {
+      A.out_cost[it.qa] = static_cast<float>(b.ia) * A.inv_scale;
+      A.out_col[it.qa] = b.ca;
+      if (it.qb >= 0) {
+        A.out_cost[it.qb] = static_cast<float>(b.ib) * A.inv_scale;
+        A.out_col[it.qb] = b.cb;
+      }
+    } else {
+      A.out_cost[it.qa] = b.f;
+      A.out_col[it.qa] = b.ca;
+    }
+  }
+}
+
+template <int PREC, int CLS, int S = Cls<CLS>::lo>
+__device__ __forceinline__ void dispatch_fixup(int s, const SdtwArgs &A, int item, uint32_t *ring, int lane) {
+  if constexpr (S <= Cls<CLS>::hi) {
+    if (s == S)
+      fixup_item<PREC, S>(A, item, ring, lane);
+    else
+      dispatch_fixup<PREC, CLS, S + 1>(s, A, item, ring, lane);
+  }
+}
+
+constexpr int kFixWarps = 4;
+
+template <int PREC, int CLS>
+__global__ void __launch_bounds__(kFixWarps * 32) fixup_kernel(SdtwArgs A) {
+  __shared__ uint32_t rings[kFixWarps * 64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int first = A.ints[kIntClassItemFirst + CLS];
+  const int count = A.ints[kIntClassItemCount + CLS];
+  const int i = blockIdx.x * kFixWarps + warp;
+  if (i >= count) return;
+  const int item = first + i;
+  dispatch_fixup<PREC, CLS>(A.items[item].S, A, item, rings + warp * 64, lane);
+}
+
+template <int PREC, int CLS>
+cudaError_t launch_cls(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
+  const size_t sm = sdtw_smem_bytes(a.tile_cols, a.warps);
+  cudaError_t e = cudaFuncSetAttribute(sdtw_kernel<PREC, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  sdtw_kernel<PREC, CLS><<<grid, a.warps * 32, sm, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || fix_items <= 0) return e;
+  fixup_kernel<PREC, CLS><<<(fix_items + kFixWarps - 1) / kFixWarps, kFixWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC, int CLS>
+int occupancy_cls(int tile_cols, int warps) {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sdtw_kernel<PREC, CLS>, warps * 32,
+                                                sdtw_smem_bytes(tile_cols, warps));
+  return n;
 }
 
 }  // namespace
@@ -446,31 +688,38 @@ size_t sdtw_smem_bytes(int tile_cols, int warps) {
   return 128 + static_cast<size_t>(warps) * 64 * 4 + 2 * static_cast<size_t>(tile_cols) * 4;
 }
 
-int sdtw_max_ctas_per_sm(int precision, int tile_cols, int warps) {
-  int n = 0;
-  size_t sm = sdtw_smem_bytes(tile_cols, warps);
-  if (precision == HARU_INT16)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sdtw_kernel<HARU_INT16>, warps * 32, sm);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sdtw_kernel<HARU_FP32>, warps * 32, sm);
-  return n;
+int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
+  if (precision == HARU_INT16) {
+    switch (cls) {
+      case 0: return occupancy_cls<HARU_INT16, 0>(tile_cols, warps);
+      case 1: return occupancy_cls<HARU_INT16, 1>(tile_cols, warps);
+      case 2: return occupancy_cls<HARU_INT16, 2>(tile_cols, warps);
+      default: return occupancy_cls<HARU_INT16, 3>(tile_cols, warps);
+    }
+  }
+  switch (cls) {
+    case 0: return occupancy_cls<HARU_FP32, 0>(tile_cols, warps);
+    case 1: return occupancy_cls<HARU_FP32, 1>(tile_cols, warps);
+    case 2: return occupancy_cls<HARU_FP32, 2>(tile_cols, warps);
+    default: return occupancy_cls<HARU_FP32, 3>(tile_cols, warps);
+  }
 }
 
-cudaError_t launch_sdtw(int precision, const SdtwArgs &a, int grid, cudaStream_t s) {
-  size_t sm = sdtw_smem_bytes(a.tile_cols, a.warps);
-  cudaError_t e;
+cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   if (precision == HARU_INT16) {
-    e = cudaFuncSetAttribute(sdtw_kernel<HARU_INT16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sm));
-    if (e != cudaSuccess) return e;
-    sdtw_kernel<HARU_INT16><<<grid, a.warps * 32, sm, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(sdtw_kernel<HARU_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sm));
-    if (e != cudaSuccess) return e;
-    sdtw_kernel<HARU_FP32><<<grid, a.warps * 32, sm, s>>>(a);
+    switch (cls) {
+      case 0: return launch_cls<HARU_INT16, 0>(a, grid, fix_items, s);
+      case 1: return launch_cls<HARU_INT16, 1>(a, grid, fix_items, s);
+      case 2: return launch_cls<HARU_INT16, 2>(a, grid, fix_items, s);
+      default: return launch_cls<HARU_INT16, 3>(a, grid, fix_items, s);
+    }
   }
-  return cudaGetLastError();
+  switch (cls) {
+    case 0: return launch_cls<HARU_FP32, 0>(a, grid, fix_items, s);
+    case 1: return launch_cls<HARU_FP32, 1>(a, grid, fix_items, s);
+    case 2: return launch_cls<HARU_FP32, 2>(a, grid, fix_items, s);
+    default: return launch_cls<HARU_FP32, 3>(a, grid, fix_items, s);
+  }
 }
 
 }  // namespace haru

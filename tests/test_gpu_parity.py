@@ -202,3 +202,32 @@ def test_uneven_8192_full_size_sampled(haru, sars):
     # every query got a result
     assert (j16 >= 0).all() and (j32 >= 0).all()
     assert np.isfinite(c32).all()
+
+
+@pytest.mark.parametrize("units", [1, 4096, 100_000])
+def test_reference_segments_are_exact(haru, sars, units):
+    """Splitting every sweep into speculative reference segments (verified
+    and, where needed, recomputed) gives the unsplit results bit for bit."""
+    _, ref = sars
+    w = synth.workload("sars_uneven_8192", nq=300)
+    qs = w.queries
+    with haru.Context(units_target=1) as ctx:
+        ctx.ref_load(ref)
+        base16 = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
+        base32 = ctx.sdtw_batch(haru.HARU_FP32, qs.events, qs.offsets)
+        assert ctx.last_stats()["max_segments"] == 1
+    with haru.Context(units_target=units) as ctx:
+        ctx.ref_load(ref)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
+        st16 = ctx.last_stats()
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, qs.events, qs.offsets)
+        st32 = ctx.last_stats()
+    np.testing.assert_array_equal(c16, base16[0])
+    np.testing.assert_array_equal(j16, base16[1])
+    np.testing.assert_array_equal(c32, base32[0])
+    np.testing.assert_array_equal(j32, base32[1])
+    if units > 1:
+        assert st16["max_segments"] > 1 and st32["max_segments"] > 1
+    idx = np.arange(0, 300, 37)
+    compare_int16(c16, j16, ref, qs.events, qs.offsets, idx=idx)
+    compare_fp32(c32, j32, ref, qs.events, qs.offsets, idx=idx)
