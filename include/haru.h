@@ -132,6 +132,56 @@ int haru_ref_read(haru_ctx *ctx, float *z, int16_t *q, size_t n);
 int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
                     float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);
 
+/* ---- Serving: continuous batching of Read Until decisions -----------------
+ * A persistent request loop inside the context (a worker thread) takes the
+ * event chunks of reads as a flow cell delivers them, keeps each admitted
+ * read's events in a device slot, and once a read's decision prefix is
+ * complete (serve_prefix events, Section 4.1 uses 250) batches it with the
+ * other complete reads into the sDTW path. Batches launch while earlier ones
+ * are still on the GPU (several in flight on separate streams). Reads are
+ * admitted to device slots as the memory budget (serve_budget_bytes) allows;
+ * the rest wait on the host in arrival order. Each result carries the
+ * decision: accept (keep sequencing) iff cost <= threshold, else eject. */
+typedef struct {
+  uint64_t read_id;
+  uint32_t channel;
+  int32_t decision;       /* 1 accept, 0 eject */
+  float cost;             /* z units (int16: integer cost / 2^k) */
+  int32_t status;         /* HARU_OK, or why no alignment was made (HARU_EINVAL: prefix too short/flat) */
+  int64_t end_col;        /* 0-based reference column of the alignment end */
+  uint32_t events;        /* prefix length used */
+  uint32_t pad;
+  uint64_t t_arrival_ns;  /* as submitted with the chunk that completed the prefix */
+  uint64_t t_done_ns;     /* when the decision was ready (CLOCK_MONOTONIC ns) */
+} haru_result;
+
+/* Append a chunk of raw event currents (host pointer, n floats) to read
+ * read_id on channel. t_arrival_ns is the caller's CLOCK_MONOTONIC time of
+ * delivery (it starts the decision-latency clock when this chunk completes
+ * the prefix). last_chunk = 1 ends the read: a shorter prefix is decided as
+ * is. Chunks after the prefix is complete are ignored. The first call starts
+ * the serving thread. Errors: HARU_EINVAL, HARU_ENOREF, HARU_EBUSY (too many
+ * events waiting on the host: poll, then retry), HARU_ECUDA. */
+int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const float *events, uint32_t n,
+                       uint64_t t_arrival_ns, int last_chunk);
+
+/* Collect up to max finished decisions into out (host array), waiting up to
+ * timeout_us microseconds for the first. *n_out = how many were written
+ * (0 on timeout, which returns HARU_OK). */
+int haru_stream_poll(haru_ctx *ctx, haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us);
+
+typedef struct {
+  uint64_t reads_submitted;   /* reads seen */
+  uint64_t reads_decided;     /* results produced */
+  uint64_t reads_waiting;     /* complete or partial reads not yet admitted to a device slot */
+  uint64_t reads_in_flight;   /* admitted, not yet decided */
+  uint64_t batches;           /* batches launched */
+  uint64_t max_batch;         /* largest batch launched */
+  uint64_t max_concurrent;    /* most batches on the GPU at once */
+  uint64_t slots;             /* device slots the budget allows */
+} haru_stream_stats;
+int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
+
 /* Work accounting of the last batch on this context (read after its stream
  * has been synchronised): items = warps of work (queries, or query pairs in
  * the int16 form), groups = CTA work units, segments = reference segments

@@ -66,6 +66,19 @@ class haru_batch_stats(ctypes.Structure):
                 ("max_segments", ctypes.c_uint32)]
 
 
+class haru_result(ctypes.Structure):
+    _fields_ = [("read_id", ctypes.c_uint64), ("channel", ctypes.c_uint32), ("decision", ctypes.c_int32),
+                ("cost", ctypes.c_float), ("status", ctypes.c_int32), ("end_col", ctypes.c_int64),
+                ("events", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("t_arrival_ns", ctypes.c_uint64),
+                ("t_done_ns", ctypes.c_uint64)]
+
+
+class haru_stream_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("reads_submitted", "reads_decided", "reads_waiting",
+                                               "reads_in_flight", "batches", "max_batch", "max_concurrent",
+                                               "slots")]
+
+
 _lib = None
 
 _SIGS = {
@@ -82,6 +95,11 @@ _SIGS = {
                                        ctypes.c_uint32]),
     "haru_last_status": (ctypes.c_int, [ctypes.c_void_p]),
     "haru_last_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_batch_stats)]),
+    "haru_stream_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int]),
+    "haru_stream_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]),
+    "haru_stream_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_stream_stats)]),
     "haru_last_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "haru_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -230,6 +248,25 @@ class Context:
         st = haru_batch_stats()
         check(lib().haru_last_stats(self._h, ctypes.byref(st)), "haru_last_stats")
         return {"items": st.items, "groups": st.groups, "fixups": st.fixups, "max_segments": st.max_segments}
+
+    # serving -------------------------------------------------------------
+    def stream_submit(self, read_id: int, channel: int, events, t_arrival_ns: int, last_chunk: bool = False) -> int:
+        """Append a chunk of raw events (numpy float32) to a read; returns the status code."""
+        ev = np.ascontiguousarray(events, dtype=np.float32)
+        return int(lib().haru_stream_submit(self._h, int(read_id), int(channel), _ptr(ev) if ev.size else None,
+                                            int(ev.shape[0]), int(t_arrival_ns), int(bool(last_chunk))))
+
+    def stream_poll(self, max_results: int = 4096, timeout_us: int = 1000):
+        """Finished decisions as a list of haru_result (possibly empty)."""
+        buf = (haru_result * max_results)()
+        n = ctypes.c_uint32()
+        check(lib().haru_stream_poll(self._h, buf, max_results, ctypes.byref(n), int(timeout_us)), "haru_stream_poll")
+        return [buf[i] for i in range(n.value)]
+
+    def stream_stats(self) -> dict:
+        st = haru_stream_stats()
+        check(lib().haru_stream_get_stats(self._h, ctypes.byref(st)), "haru_stream_get_stats")
+        return {f: int(getattr(st, f)) for f, _ in haru_stream_stats._fields_}
 
     def last_timing(self):
         """(ms_prep, ms_sweep) of the last HARU_PROFILE batch."""

@@ -11,59 +11,11 @@
 #include <new>
 #include <vector>
 
-#include "haru_internal.h"
+#include "engine.h"
 
 using haru::Group;
 using haru::Item;
-
-struct haru_ctx {
-  int device = 0;
-  haru_config cfg{};
-  cudaStream_t stream = nullptr;
-  int sms = 0;
-  int sticky = HARU_OK;
-  int last_status = HARU_OK;
-  std::mutex mu;
-
-  // reference store
-  size_t N = 0;
-  int scale_log2 = 6;
-  float *ref_z = nullptr;       // N
-  uint32_t *img16 = nullptr;    // N + kRefPad, packed (q, q)
-  float *img32 = nullptr;       // N + kRefPad
-  double *stats = nullptr;      // mean, sigma
-  double *partials = nullptr;
-  size_t partials_cap = 0;
-
-  // batch workspace
-  int *d_status = nullptr;      // [0] status, [1] n_groups, [2] n_items, [3] queue
-  Item *items = nullptr;
-  Group *groups = nullptr;
-  uint32_t *img = nullptr;
-  size_t cap_items = 0;
-  float *d_events = nullptr;
-  size_t cap_events = 0;
-  uint32_t *d_offsets = nullptr;
-  float *d_cost = nullptr;
-  int64_t *d_col = nullptr;
-  size_t cap_q = 0;
-  uint32_t *states = nullptr;   // saved segment states
-  size_t cap_states = 0;
-  haru::Best *bests = nullptr;  // per-unit last-row minima
-  size_t cap_bests = 0;
-
-  // profiling events (HARU_PROFILE)
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  bool profiled = false;
-
-  // one stream per strip-height class; the class kernels of a batch run
-  // concurrently (fork/join through events, also inside a captured graph)
-  cudaStream_t aux[haru::kClasses] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fork = nullptr;
-  cudaEvent_t join[haru::kClasses] = {nullptr, nullptr, nullptr, nullptr};
-  const int *last_fixups_ptr = nullptr;
-  int last_nseg_cap = 1;
-};
+using haru::grow;
 
 namespace {
 
@@ -78,18 +30,6 @@ int cuda_fail(haru_ctx *c, cudaError_t e) {
     cudaError_t e_ = (call);                           \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_);  \
   } while (0)
-
-template <class T>
-cudaError_t grow(T **p, size_t *cap, size_t need) {
-  if (*cap >= need && *p) return cudaSuccess;
-  if (*p) cudaFree(*p);
-  *p = nullptr;
-  *cap = 0;
-  size_t n = std::max<size_t>(need, 1);
-  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
-  if (e == cudaSuccess) *cap = n;
-  return e;
-}
 
 int pick_warps(const haru_config &cfg) {
   int w = cfg.warps_per_cta;
@@ -107,17 +47,27 @@ unsigned long long wait_ns(const haru_config &cfg) {
   return cfg.wait_limit ? static_cast<unsigned long long>(cfg.wait_limit) * 1000ull : 2000000000ull;
 }
 
-// Record `e` on `s`; inside a stream capture, as an external event node so
-// the timing of every replay can be read back.
-cudaError_t record(cudaEvent_t e, cudaStream_t s) {
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaError_t r = cudaStreamIsCapturing(s, &cs);
-  if (r != cudaSuccess) return r;
-  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
-  return cudaEventRecord(e, s);
+}  // namespace
+
+haru::LaunchCfg haru_ctx::launch_cfg() const {
+  haru::LaunchCfg lc;
+  lc.warps = pick_warps(cfg);
+  lc.tile = pick_tile(cfg);
+  lc.ctas_per_sm = cfg.ctas_per_sm;
+  lc.sms = sms;
+  lc.units_target = cfg.units_target;
+  lc.wait_ns = wait_ns(cfg);
+  return lc;
 }
 
-}  // namespace
+haru::RefView haru_ctx::ref_view() const {
+  haru::RefView r;
+  r.img16 = img16;
+  r.img32 = img32;
+  r.N = static_cast<long>(N);
+  r.scale_log2 = scale_log2;
+  return r;
+}
 
 namespace haru {
 
@@ -194,14 +144,15 @@ int haru_create(haru_ctx **out, int device, const haru_config *cfg) {
       break;
     }
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = HARU_ECUDA; break; }
-    if (cudaMalloc(&ctx->d_status, haru::kIntWords * sizeof(int)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
+    size_t ci = 0;
+    if (grow(&ctx->ws.ints, &ci, (size_t)haru::kIntWords) != cudaSuccess) { rc = HARU_ENOMEM; break; }
     if (cudaMalloc(&ctx->stats, 2 * sizeof(double)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
     bool ev_ok = true;
     for (auto &e : ctx->ev) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
-    ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) == cudaSuccess;
+    ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->fj.fork, cudaEventDisableTiming) == cudaSuccess;
     for (int c = 0; c < haru::kClasses; ++c) {
-      ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->join[c], cudaEventDisableTiming) == cudaSuccess;
-      ev_ok = ev_ok && cudaStreamCreateWithFlags(&ctx->aux[c], cudaStreamNonBlocking) == cudaSuccess;
+      ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->fj.join[c], cudaEventDisableTiming) == cudaSuccess;
+      ev_ok = ev_ok && cudaStreamCreateWithFlags(&ctx->fj.aux[c], cudaStreamNonBlocking) == cudaSuccess;
     }
     if (!ev_ok) { rc = HARU_ECUDA; break; }
   } while (0);
@@ -216,18 +167,22 @@ int haru_create(haru_ctx **out, int device, const haru_config *cfg) {
 void haru_destroy(haru_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  if (ctx->server) {
+    haru::server_destroy(ctx->server);
+    ctx->server = nullptr;
+  }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void *ptrs[] = {ctx->ref_z, ctx->img16, ctx->img32, ctx->stats,  ctx->partials, ctx->d_status,
-                  ctx->items, ctx->groups, ctx->img,   ctx->d_events, ctx->d_offsets, ctx->d_cost,
-                  ctx->d_col, ctx->states, ctx->bests};
+  void *ptrs[] = {ctx->ref_z,    ctx->img16,     ctx->img32,  ctx->stats, ctx->partials,
+                  ctx->d_events, ctx->d_offsets, ctx->d_cost, ctx->d_col};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  haru::ws_free(ctx->ws);
   for (auto e : ctx->ev)
     if (e) cudaEventDestroy(e);
-  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->fj.fork) cudaEventDestroy(ctx->fj.fork);
   for (int c = 0; c < haru::kClasses; ++c) {
-    if (ctx->join[c]) cudaEventDestroy(ctx->join[c]);
-    if (ctx->aux[c]) cudaStreamDestroy(ctx->aux[c]);
+    if (ctx->fj.join[c]) cudaEventDestroy(ctx->fj.join[c]);
+    if (ctx->fj.aux[c]) cudaStreamDestroy(ctx->fj.aux[c]);
   }
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -251,14 +206,14 @@ static int ref_install(haru_ctx *ctx, const float *x_dev, size_t n, int normaliz
   }
   const size_t nb = (n + 4095) / 4096;
   HARU_CUDA(grow(&ctx->partials, &ctx->partials_cap, nb));
-  HARU_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+  HARU_CUDA(cudaMemsetAsync(ctx->ws.ints, 0, sizeof(int), s));
   HARU_CUDA(cudaMemsetAsync(i16, 0, img_len * sizeof(uint32_t), s));
   HARU_CUDA(cudaMemsetAsync(i32, 0, img_len * sizeof(float), s));
-  if (normalize) HARU_CUDA(haru::launch_zscore_stats(x_dev, n, ctx->partials, ctx->stats, ctx->d_status, s));
+  if (normalize) HARU_CUDA(haru::launch_zscore_stats(x_dev, n, ctx->partials, ctx->stats, ctx->ws.ints, s));
   HARU_CUDA(haru::launch_ref_finish(x_dev, n, ctx->stats, normalize, scale_log2, z, i16, i32, img_len,
-                                    ctx->d_status, s));
+                                    ctx->ws.ints, s));
   int st = 0;
-  HARU_CUDA(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HARU_CUDA(cudaMemcpyAsync(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost, s));
   HARU_CUDA(cudaStreamSynchronize(s));
   if (st != HARU_OK) {
     cudaFree(z); cudaFree(i16); cudaFree(i32);
@@ -318,10 +273,10 @@ int haru_ref_build(haru_ctx *ctx, const uint8_t *bases, size_t n_bases, const fl
   cudaStream_t s = ctx->stream;
   e = cudaMemcpyAsync(db, bases, n_bases, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dm, kmer_levels, nmodel * sizeof(float), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = haru::launch_ref_levels(db, n_bases, dm, k, x, ctx->d_status, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ints, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = haru::launch_ref_levels(db, n_bases, dm, k, x, ctx->ws.ints, s);
   int st = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess)
     rc = cuda_fail(ctx, e);
@@ -400,96 +355,15 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
     d_cost = ctx->d_cost;
     d_col = ctx->d_col;
   }
-  const int warps = pick_warps(ctx->cfg);
-  const int tile = pick_tile(ctx->cfg);
-  const size_t max_items = precision == HARU_INT16 ? ((size_t)nq + 1) / 2 + haru::kMaxS : (size_t)nq;
-  // Work units: enough (query x reference segment) units to keep every SM
-  // busy to the end; nseg_cap bounds the segments per item for storage.
-  const int units_target = ctx->cfg.units_target > 0 ? ctx->cfg.units_target : 4 * ctx->sms * warps;
-  const size_t items_min = precision == HARU_INT16 ? ((size_t)nq + 1) / 2 : (size_t)nq;
-  int nseg_cap = (int)std::min<size_t>(haru::kMaxSeg, ((size_t)units_target + items_min - 1) / items_min);
-  if (nseg_cap < 1) nseg_cap = 1;
-  if (ctx->cap_items < max_items) {
-    size_t c0 = 0, c1 = 0, c2 = 0;
-    cudaFree(ctx->items); cudaFree(ctx->groups); cudaFree(ctx->img);
-    ctx->items = nullptr; ctx->groups = nullptr; ctx->img = nullptr;
-    ctx->cap_items = 0;
-    HARU_CUDA(grow(&ctx->items, &c0, max_items));
-    HARU_CUDA(grow(&ctx->groups, &c1, max_items * haru::kMaxSeg + haru::kMaxS * haru::kMaxSeg));
-    HARU_CUDA(grow(&ctx->img, &c2, max_items * haru::kImgStride));
-    ctx->cap_items = max_items;
-  }
-  const size_t units = max_items * (size_t)nseg_cap;
-  HARU_CUDA(grow(&ctx->bests, &ctx->cap_bests, units));
-  if (nseg_cap > 1) HARU_CUDA(grow(&ctx->states, &ctx->cap_states, units * 2 * haru::kStateStride));
+  const haru::LaunchCfg lc = ctx->launch_cfg();
+  HARU_CUDA(haru::ws_reserve(ctx->ws, precision, nq, lc));
   const bool prof = flags & HARU_PROFILE;
-  int *ints = ctx->d_status;
-  HARU_CUDA(cudaMemsetAsync(ints, 0, haru::kIntWords * sizeof(int), s));
-  if (prof) HARU_CUDA(record(ctx->ev[0], s));
-
-  haru::PlanArgs pa;
-  pa.offsets = d_off;
-  pa.nq = nq;
-  pa.N = (long)ctx->N;
-  pa.pair = precision == HARU_INT16;
-  pa.warps = warps;
-  pa.units_target = units_target;
-  pa.nseg_cap = nseg_cap;
-  pa.items = ctx->items;
-  pa.groups = ctx->groups;
-  pa.ints = ints;
-  HARU_CUDA(haru::launch_plan(pa, s));
-
-  haru::PackArgs ka;
-  ka.events = d_ev;
-  ka.offsets = d_off;
-  ka.items = ctx->items;
-  ka.n_items = ints + haru::kIntItems;
-  ka.img = ctx->img;
-  ka.raw = raw;
-  ka.pair = pa.pair;
-  ka.scale_log2 = ctx->scale_log2;
-  ka.status = ints + haru::kIntStatus;
-  HARU_CUDA(haru::launch_pack(ka, (uint32_t)max_items, s));
-
-  haru::SdtwArgs sa;
-  sa.ref_img = precision == HARU_INT16 ? (const void *)ctx->img16 : (const void *)ctx->img32;
-  sa.N = (long)ctx->N;
-  sa.img = ctx->img;
-  sa.items = ctx->items;
-  sa.groups = ctx->groups;
-  sa.ints = ints;
-  sa.states = ctx->states;
-  sa.bests = ctx->bests;
-  sa.nseg_cap = nseg_cap;
-  sa.out_cost = d_cost;
-  sa.out_col = d_col;
-  sa.inv_scale = 1.0f / (float)(1 << ctx->scale_log2);
-  sa.tile_cols = tile;
-  sa.warps = warps;
-  sa.wait_ns = wait_ns(ctx->cfg);
-  const size_t groups_max = ((max_items + warps - 1) / warps + haru::kMaxS) * (size_t)nseg_cap;
-  if (prof) HARU_CUDA(record(ctx->ev[1], s));
-  // Fork: the class kernels (tallest strips first) run side by side; each is
-  // persistent over its own part of the group list, then verifies its
-  // segments and writes its queries' results.
-  HARU_CUDA(cudaEventRecord(ctx->fork, s));
-  for (int c = 0; c < haru::kClasses; ++c) {
-    int per_sm = ctx->cfg.ctas_per_sm > 0 ? ctx->cfg.ctas_per_sm
-                                          : haru::sdtw_max_ctas_per_sm(precision, c, tile, warps);
-    if (per_sm < 1) per_sm = 1;
-    const int grid = (int)std::min<size_t>((size_t)ctx->sms * per_sm, groups_max);
-    HARU_CUDA(cudaStreamWaitEvent(ctx->aux[c], ctx->fork, 0));
-    HARU_CUDA(haru::launch_sdtw(precision, c, sa, grid, (int)max_items, ctx->aux[c]));
-    HARU_CUDA(cudaEventRecord(ctx->join[c], ctx->aux[c]));
-    HARU_CUDA(cudaStreamWaitEvent(s, ctx->join[c], 0));
-  }
+  HARU_CUDA(haru::ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, d_cost, d_col, lc, s,
+                             &ctx->fj, prof ? ctx->ev[0] : nullptr, prof ? ctx->ev[1] : nullptr));
   if (prof) {
-    HARU_CUDA(record(ctx->ev[2], s));
+    HARU_CUDA(haru::record_event(ctx->ev[2], s));
     ctx->profiled = true;
   }
-  ctx->last_fixups_ptr = ints + haru::kIntFixups;
-  ctx->last_nseg_cap = nseg_cap;
 
   if (async) {
     ctx->last_status = HARU_OK;
@@ -500,7 +374,7 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
     HARU_CUDA(cudaMemcpyAsync(out_col, d_col, (size_t)nq * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   }
   int st = 0;
-  HARU_CUDA(cudaMemcpyAsync(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HARU_CUDA(cudaMemcpyAsync(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost, s));
   HARU_CUDA(cudaStreamSynchronize(s));
   ctx->last_status = st;
   return st;
@@ -527,11 +401,11 @@ int haru_last_stats(haru_ctx *ctx, haru_batch_stats *out) {
   if (ctx->sticky) return ctx->sticky;
   HARU_CUDA(cudaSetDevice(ctx->device));
   int w[haru::kIntWords];
-  HARU_CUDA(cudaMemcpy(w, ctx->d_status, sizeof(w), cudaMemcpyDeviceToHost));
+  HARU_CUDA(cudaMemcpy(w, ctx->ws.ints, sizeof(w), cudaMemcpyDeviceToHost));
   out->items = (uint32_t)w[haru::kIntItems];
   out->groups = (uint32_t)w[haru::kIntGroups];
   out->fixups = (uint32_t)w[haru::kIntFixups];
-  out->max_segments = (uint32_t)ctx->last_nseg_cap;
+  out->max_segments = (uint32_t)ctx->ws.nseg_cap;
   return HARU_OK;
 }
 
@@ -541,7 +415,7 @@ int haru_last_status(haru_ctx *ctx) {
   if (ctx->sticky) return ctx->sticky;
   int st = 0;
   HARU_CUDA(cudaSetDevice(ctx->device));
-  HARU_CUDA(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  HARU_CUDA(cudaMemcpy(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost));
   ctx->last_status = st;
   return st;
 }

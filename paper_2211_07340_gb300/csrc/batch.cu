@@ -1,0 +1,135 @@
+// The batch engine: workspace sizing and the stream-ordered sequence of
+// kernels of one batch (planner, pack, class sweeps, segment fix-up).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "engine.h"
+
+namespace haru {
+
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t r = cudaStreamIsCapturing(s, &cs);
+  if (r != cudaSuccess) return r;
+  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  return cudaEventRecord(e, s);
+}
+
+void ws_free(Workspace &ws) {
+  void *p[] = {ws.ints, ws.items, ws.groups, ws.img, ws.states, ws.bests};
+  for (void *q : p)
+    if (q) cudaFree(q);
+  ws = Workspace();
+}
+
+cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCfg &lc) {
+  const size_t max_items = precision == HARU_INT16 ? (static_cast<size_t>(nq) + 1) / 2 + kMaxS : nq;
+  // Work units: enough (query x reference segment) units to keep every SM
+  // busy to the end; nseg_cap bounds the segments per item for storage.
+  const int units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * lc.warps;
+  const size_t items_min = precision == HARU_INT16 ? (static_cast<size_t>(nq) + 1) / 2 : nq;
+  int nseg_cap = static_cast<int>(
+      std::min<size_t>(kMaxSeg, (static_cast<size_t>(units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
+  if (nseg_cap < 1) nseg_cap = 1;
+  cudaError_t e = cudaSuccess;
+  size_t c = ws.ints ? static_cast<size_t>(kIntWords) : 0;
+  if ((e = grow(&ws.ints, &c, kIntWords)) != cudaSuccess) return e;
+  if (ws.cap_items < max_items) {
+    cudaFree(ws.items);
+    cudaFree(ws.groups);
+    cudaFree(ws.img);
+    ws.items = nullptr;
+    ws.groups = nullptr;
+    ws.img = nullptr;
+    ws.cap_items = 0;
+    size_t c0 = 0, c1 = 0, c2 = 0;
+    if ((e = grow(&ws.items, &c0, max_items)) != cudaSuccess) return e;
+    if ((e = grow(&ws.groups, &c1, (max_items + kMaxS) * kMaxSeg)) != cudaSuccess) return e;
+    if ((e = grow(&ws.img, &c2, max_items * kImgStride)) != cudaSuccess) return e;
+    ws.cap_items = max_items;
+  }
+  const size_t units = max_items * static_cast<size_t>(nseg_cap);
+  if ((e = grow(&ws.bests, &ws.cap_bests, units)) != cudaSuccess) return e;
+  if (nseg_cap > 1 && (e = grow(&ws.states, &ws.cap_states, units * 2 * kStateStride)) != cudaSuccess) return e;
+  ws.max_items = max_items;
+  ws.nseg_cap = nseg_cap;
+  ws.units_target = units_target;
+  return cudaSuccess;
+}
+
+cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
+                       const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
+                       const LaunchCfg &lc, cudaStream_t s, const ForkJoin *fj, cudaEvent_t ev_prep,
+                       cudaEvent_t ev_sweep) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.ints, 0, kIntWords * sizeof(int), s)) != cudaSuccess) return e;
+  if (ev_prep && (e = record_event(ev_prep, s)) != cudaSuccess) return e;
+  PlanArgs pa;
+  pa.offsets = d_offsets;
+  pa.nq = nq;
+  pa.N = ref.N;
+  pa.pair = precision == HARU_INT16;
+  pa.warps = lc.warps;
+  pa.units_target = ws.units_target;
+  pa.nseg_cap = ws.nseg_cap;
+  pa.items = ws.items;
+  pa.groups = ws.groups;
+  pa.ints = ws.ints;
+  if ((e = launch_plan(pa, s)) != cudaSuccess) return e;
+
+  PackArgs ka;
+  ka.events = d_events;
+  ka.offsets = d_offsets;
+  ka.items = ws.items;
+  ka.n_items = ws.ints + kIntItems;
+  ka.img = ws.img;
+  ka.raw = raw;
+  ka.pair = pa.pair;
+  ka.scale_log2 = ref.scale_log2;
+  ka.status = ws.ints + kIntStatus;
+  if ((e = launch_pack(ka, static_cast<uint32_t>(ws.max_items), s)) != cudaSuccess) return e;
+
+  SdtwArgs sa;
+  sa.ref_img = precision == HARU_INT16 ? static_cast<const void *>(ref.img16) : static_cast<const void *>(ref.img32);
+  sa.N = ref.N;
+  sa.img = ws.img;
+  sa.items = ws.items;
+  sa.groups = ws.groups;
+  sa.ints = ws.ints;
+  sa.states = ws.states;
+  sa.bests = ws.bests;
+  sa.nseg_cap = ws.nseg_cap;
+  sa.out_cost = d_cost;
+  sa.out_col = d_col;
+  sa.inv_scale = 1.0f / static_cast<float>(1 << ref.scale_log2);
+  sa.tile_cols = lc.tile;
+  sa.warps = lc.warps;
+  sa.wait_ns = lc.wait_ns;
+  const size_t groups_max = ((ws.max_items + lc.warps - 1) / lc.warps + kMaxS) * static_cast<size_t>(ws.nseg_cap);
+  if (ev_sweep && (e = record_event(ev_sweep, s)) != cudaSuccess) return e;
+  // The class kernels (tallest strips first) run side by side when fork/join
+  // streams are given, else one after the other on s; each is persistent
+  // over its own part of the group list, then verifies its segments and
+  // writes its queries' results.
+  if (fj && fj->ok() && (e = cudaEventRecord(fj->fork, s)) != cudaSuccess) return e;
+  for (int c = 0; c < kClasses; ++c) {
+    int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, c, lc.tile, lc.warps);
+    if (per_sm < 1) per_sm = 1;
+    const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
+    cudaStream_t cs = s;
+    if (fj && fj->ok()) {
+      cs = fj->aux[c];
+      if ((e = cudaStreamWaitEvent(cs, fj->fork, 0)) != cudaSuccess) return e;
+    }
+    if ((e = launch_sdtw(precision, c, sa, grid, static_cast<int>(ws.max_items), cs)) != cudaSuccess) return e;
+    if (fj && fj->ok()) {
+      if ((e = cudaEventRecord(fj->join[c], cs)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(s, fj->join[c], 0)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+}  // namespace haru

@@ -1,0 +1,135 @@
+// Host-side structures shared by the C ABI (api.cu), the batch engine
+// (batch.cu) and the serving loop (serve.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "haru_internal.h"
+
+namespace haru {
+
+template <class T>
+cudaError_t grow(T **p, size_t *cap, size_t need) {
+  if (*cap >= need && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  const size_t n = need > 1 ? need : 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+// Launch settings derived from a context's configuration.
+struct LaunchCfg {
+  int warps = 8;
+  int tile = 4096;
+  int ctas_per_sm = 0;
+  int sms = 1;
+  int units_target = 0;  // 0: 4 x sms x warps
+  unsigned long long wait_ns = 2000000000ull;
+};
+
+// The reference as the kernels read it.
+struct RefView {
+  const uint32_t *img16 = nullptr;
+  const float *img32 = nullptr;
+  long N = 0;
+  int scale_log2 = 6;
+};
+
+// Device scratch of one batch in flight: status/counter words, planner
+// output, packed query images, segment states and per-unit minima.
+struct Workspace {
+  int *ints = nullptr;
+  Item *items = nullptr;
+  Group *groups = nullptr;
+  uint32_t *img = nullptr;
+  size_t cap_items = 0;
+  uint32_t *states = nullptr;
+  size_t cap_states = 0;
+  Best *bests = nullptr;
+  size_t cap_bests = 0;
+  // plan of the last reservation
+  size_t max_items = 0;
+  int nseg_cap = 1;
+  int units_target = 0;
+};
+
+// Size `ws` for a batch of nq queries (allocates only when it must grow).
+cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCfg &lc);
+void ws_free(Workspace &ws);
+
+// Streams/events to run the class kernels side by side (optional).
+struct ForkJoin {
+  cudaStream_t aux[kClasses] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kClasses] = {nullptr, nullptr, nullptr, nullptr};
+  bool ok() const { return fork != nullptr; }
+};
+
+// Enqueue the whole batch path on stream s: zero the counters, plan, pack
+// (z-score and quantise when raw), sweep each strip-height class, verify
+// segments and write (cost, column) per query. ev_prep/ev_sweep (optional)
+// are recorded after the counters are zeroed and after packing.
+cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
+                       const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
+                       const LaunchCfg &lc, cudaStream_t s, const ForkJoin *fj, cudaEvent_t ev_prep,
+                       cudaEvent_t ev_sweep);
+
+// Record `e` on `s`; inside a stream capture, as an external event node so
+// its time can be read after every replay.
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s);
+
+class Server;  // serve.cu
+void server_destroy(Server *s);
+
+}  // namespace haru
+
+struct haru_ctx {
+  int device = 0;
+  haru_config cfg{};
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int sticky = HARU_OK;
+  int last_status = HARU_OK;
+  std::mutex mu;
+
+  // reference store
+  size_t N = 0;
+  int scale_log2 = 6;
+  float *ref_z = nullptr;       // N
+  uint32_t *img16 = nullptr;    // N + kRefPad, packed (q, q)
+  float *img32 = nullptr;       // N + kRefPad
+  double *stats = nullptr;      // mean, sigma
+  double *partials = nullptr;
+  size_t partials_cap = 0;
+
+  // batch path
+  haru::Workspace ws;
+  float *d_events = nullptr;
+  size_t cap_events = 0;
+  uint32_t *d_offsets = nullptr;
+  float *d_cost = nullptr;
+  int64_t *d_col = nullptr;
+  size_t cap_q = 0;
+  haru::ForkJoin fj;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // HARU_PROFILE
+  bool profiled = false;
+
+  // serving (serve.cu): created by the first haru_stream_submit
+  haru::Server *server = nullptr;
+
+  haru::LaunchCfg launch_cfg() const;
+  haru::RefView ref_view() const;
+};

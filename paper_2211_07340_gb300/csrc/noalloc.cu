@@ -17,7 +17,7 @@
 
 #include <mutex>
 
-#include "haru_internal.h"
+#include "engine.h"
 
 namespace haru {
 namespace {

@@ -1,0 +1,576 @@
+// Serving: a continuous-batching request loop for Read Until decisions.
+//
+// The paper's software layer (Section 4.1) collects reads from the
+// sequencer, waits until a read has its 250-event prefix, normalises it and
+// hands it to the sDTW accelerator, then takes the accept/eject decision
+// from the alignment. Here one worker thread per context does that for
+// many reads at once:
+//   * submitted chunks are staged in pinned memory and, every loop turn,
+//     copied to the device with one transfer and scattered by a kernel into
+//     per-read device slots (a read is admitted to a slot on its first
+//     chunk while the memory budget has room, otherwise it waits on the
+//     host in arrival order);
+//   * reads whose prefix is complete are gathered into the next batch,
+//     which runs the whole device path (z-score, quantise, plan, sweep,
+//     verify) on one of several batch contexts; a batch launches as soon as
+//     a context is free, while earlier batches are still on the GPU;
+//   * finished batches are detected by event query, decided on the host
+//     (cost <= threshold) and handed to haru_stream_poll.
+// Every wait here is bounded: the loop sleeps at most 200 us between turns
+// and polls events without blocking.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <list>
+
+#include "engine.h"
+
+namespace haru {
+namespace {
+
+uint64_t now_ns() {
+  return static_cast<uint64_t>(
+      std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+          .count());
+}
+
+// Staged chunk copy: `count` events at staging[src] go to slot `slot` at `dst`.
+struct CopyOp {
+  uint32_t slot;
+  uint32_t dst;
+  uint32_t src;
+  uint32_t count;
+};
+
+__global__ void scatter_kernel(const float *staging, const CopyOp *ops, int nops, float *slots, int slot_len) {
+  const int op = blockIdx.x;
+  if (op >= nops) return;
+  const CopyOp o = ops[op];
+  for (uint32_t i = threadIdx.x; i < o.count; i += blockDim.x)
+    slots[static_cast<size_t>(o.slot) * slot_len + o.dst + i] = staging[o.src + i];
+}
+
+// Batch events from slots: request r's first len[r] events of slot[r].
+__global__ void gather_kernel(const float *slots, int slot_len, const uint32_t *slot_of, const uint32_t *off,
+                              int nreq, float *events) {
+  const int r = blockIdx.x;
+  if (r >= nreq) return;
+  const uint32_t b = off[r], e = off[r + 1];
+  for (uint32_t i = threadIdx.x; i < e - b; i += blockDim.x)
+    events[b + i] = slots[static_cast<size_t>(slot_of[r]) * slot_len + i];
+}
+
+}  // namespace
+
+class Server {
+ public:
+  explicit Server(haru_ctx *ctx) : ctx_(ctx) {}
+  ~Server() { stop(); }
+
+  int start();
+  void stop();
+  int submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t n, uint64_t t_arrival, int last);
+  int poll(haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us);
+  void stats(haru_stream_stats *out);
+
+ private:
+  struct Read {
+    uint64_t id = 0;
+    uint32_t channel = 0;
+    std::vector<float> host;     // events not yet on the device
+    uint32_t on_device = 0;      // events already in its slot
+    uint32_t total = 0;          // events accepted (<= prefix)
+    int slot = -1;
+    bool complete = false;       // prefix complete (or read ended)
+    bool queued = false;         // handed to a batch
+    bool bad = false;            // non-finite event seen
+    float lo = 0.0f, hi = 0.0f;  // range of the accepted events (a flat prefix has no z-score)
+    uint64_t t_arrival = 0;
+  };
+  struct BatchCtx {
+    Workspace ws;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    float *d_events = nullptr;
+    uint32_t *d_off = nullptr;
+    uint32_t *d_slot = nullptr;
+    float *d_cost = nullptr;
+    int64_t *d_col = nullptr;
+    uint32_t *h_off = nullptr;   // pinned
+    uint32_t *h_slot = nullptr;  // pinned
+    float *h_cost = nullptr;     // pinned
+    int64_t *h_col = nullptr;    // pinned
+    int *h_status = nullptr;     // pinned
+    std::vector<uint64_t> reads;
+    bool busy = false;
+  };
+
+  void worker();
+  int turn_upload();
+  int turn_launch();
+  int turn_complete();
+  void fail(int code);
+
+  haru_ctx *ctx_;
+  std::thread thread_;
+  std::atomic<bool> run_{false};
+  std::mutex mu_;                       // reads_, pending chunks, admission queue
+  std::condition_variable cv_work_;
+  std::unordered_map<uint64_t, Read> reads_;
+  std::deque<uint64_t> admit_q_;        // reads waiting for a slot
+  std::deque<uint64_t> ready_q_;        // admitted reads with complete prefix, uploaded
+  std::vector<int> free_slots_;
+  size_t host_events_ = 0;              // events held on the host
+  std::mutex out_mu_;
+  std::condition_variable cv_out_;
+  std::deque<haru_result> done_q_;
+  int error_ = HARU_OK;
+
+  // device resources
+  int prefix_ = 250;
+  int slot_len_ = 256;
+  int nslots_ = 0;
+  int max_batch_ = 1024;
+  int precision_ = HARU_INT16;
+  float threshold_ = 0.0f;
+  float *d_slots_ = nullptr;
+  float *h_stage_ = nullptr;   // pinned staging for chunk uploads
+  float *d_stage_ = nullptr;
+  CopyOp *h_ops_ = nullptr;    // pinned
+  CopyOp *d_ops_ = nullptr;
+  size_t stage_cap_ = 0;       // events per upload turn
+  size_t ops_cap_ = 0;
+  cudaStream_t up_stream_ = nullptr;
+  cudaEvent_t up_done_ = nullptr;
+  std::vector<BatchCtx> batches_;
+  LaunchCfg lc_;
+  RefView ref_;
+
+  // stats
+  std::atomic<uint64_t> n_submitted_{0}, n_decided_{0}, n_batches_{0}, max_batch_seen_{0}, max_conc_{0};
+};
+
+int Server::start() {
+  const haru_config &c = ctx_->cfg;
+  prefix_ = c.serve_prefix ? static_cast<int>(c.serve_prefix) : 250;
+  if (prefix_ < 1 || prefix_ > HARU_MAX_QUERY) return HARU_EINVAL;
+  slot_len_ = (prefix_ + 31) / 32 * 32;
+  max_batch_ = c.serve_max_batch ? static_cast<int>(c.serve_max_batch) : 1024;
+  precision_ = c.serve_precision == HARU_FP32 ? HARU_FP32 : HARU_INT16;
+  threshold_ = c.threshold;
+  const size_t budget = c.serve_budget_bytes ? c.serve_budget_bytes : (64u << 20);
+  nslots_ = static_cast<int>(std::min<size_t>(budget / (static_cast<size_t>(slot_len_) * sizeof(float)), 1u << 22));
+  if (nslots_ < 1) return HARU_ENOMEM;
+  lc_ = ctx_->launch_cfg();
+  ref_ = ctx_->ref_view();
+  stage_cap_ = static_cast<size_t>(std::max(nslots_, 64)) * slot_len_;
+  if (stage_cap_ > (8u << 20) / sizeof(float)) stage_cap_ = (8u << 20) / sizeof(float);
+  ops_cap_ = 65536;
+  cudaError_t e = cudaSetDevice(ctx_->device);
+  if (e == cudaSuccess) e = cudaMalloc(&d_slots_, static_cast<size_t>(nslots_) * slot_len_ * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d_stage_, stage_cap_ * sizeof(float));
+  if (e == cudaSuccess) e = cudaMallocHost(&h_stage_, stage_cap_ * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&d_ops_, ops_cap_ * sizeof(CopyOp));
+  if (e == cudaSuccess) e = cudaMallocHost(&h_ops_, ops_cap_ * sizeof(CopyOp));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&up_stream_, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&up_done_, cudaEventDisableTiming);
+  const int nb = 3;
+  batches_.resize(nb);
+  for (auto &b : batches_) {
+    if (e != cudaSuccess) break;
+    e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_events, static_cast<size_t>(max_batch_) * slot_len_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_off, (max_batch_ + 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_slot, max_batch_ * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_cost, max_batch_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_col, max_batch_ * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_off, (max_batch_ + 1) * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_slot, max_batch_ * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_cost, max_batch_ * sizeof(float));
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_col, max_batch_ * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&b.h_status, sizeof(int));
+    // size the workspace for every batch size up to max_batch (segments per
+    // item grow as batches shrink) so the loop never allocates
+    for (uint32_t n = static_cast<uint32_t>(max_batch_); n >= 1 && e == cudaSuccess; n = n / 2)
+      e = ws_reserve(b.ws, precision_, n, lc_);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HARU_ENOMEM : HARU_ECUDA;
+  }
+  free_slots_.resize(nslots_);
+  for (int i = 0; i < nslots_; ++i) free_slots_[i] = nslots_ - 1 - i;
+  run_ = true;
+  thread_ = std::thread([this] { worker(); });
+  return HARU_OK;
+}
+
+void Server::stop() {
+  if (run_.exchange(false)) {
+    cv_work_.notify_all();
+    if (thread_.joinable()) thread_.join();
+  }
+  cudaSetDevice(ctx_->device);
+  for (auto &b : batches_) {
+    if (b.stream) cudaStreamSynchronize(b.stream);
+    ws_free(b.ws);
+    void *d[] = {b.d_events, b.d_off, b.d_slot, b.d_cost, b.d_col};
+    for (void *p : d)
+      if (p) cudaFree(p);
+    void *h[] = {b.h_off, b.h_slot, b.h_cost, b.h_col, b.h_status};
+    for (void *p : h)
+      if (p) cudaFreeHost(p);
+    if (b.done) cudaEventDestroy(b.done);
+    if (b.stream) cudaStreamDestroy(b.stream);
+  }
+  batches_.clear();
+  if (up_stream_) cudaStreamSynchronize(up_stream_);
+  if (d_slots_) cudaFree(d_slots_);
+  if (d_stage_) cudaFree(d_stage_);
+  if (h_stage_) cudaFreeHost(h_stage_);
+  if (d_ops_) cudaFree(d_ops_);
+  if (h_ops_) cudaFreeHost(h_ops_);
+  if (up_done_) cudaEventDestroy(up_done_);
+  if (up_stream_) cudaStreamDestroy(up_stream_);
+  d_slots_ = d_stage_ = h_stage_ = nullptr;
+  d_ops_ = h_ops_ = nullptr;
+  up_done_ = nullptr;
+  up_stream_ = nullptr;
+}
+
+void Server::fail(int code) {
+  std::lock_guard<std::mutex> lk(out_mu_);
+  if (error_ == HARU_OK) error_ = code;
+  cv_out_.notify_all();
+}
+
+int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t n, uint64_t t_arrival, int last) {
+  {
+    std::lock_guard<std::mutex> lk(out_mu_);
+    if (error_ != HARU_OK) return error_;
+  }
+  if (n > 0 && !ev) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(mu_);
+  if (host_events_ + n > stage_cap_ * 4) return HARU_EBUSY;
+  auto it = reads_.find(read_id);
+  if (it == reads_.end()) {
+    Read r;
+    r.id = read_id;
+    r.channel = channel;
+    it = reads_.emplace(read_id, std::move(r)).first;
+    admit_q_.push_back(read_id);
+    n_submitted_++;
+  }
+  Read &r = it->second;
+  if (r.complete) return HARU_OK;  // later chunks of a decided prefix are not needed
+  const uint32_t take = std::min<uint32_t>(n, static_cast<uint32_t>(prefix_) - r.total);
+  for (uint32_t i = 0; i < take; ++i) {
+    const float x = ev[i];
+    if (!std::isfinite(x)) r.bad = true;
+    if (r.total == 0 && i == 0) r.lo = r.hi = x;
+    r.lo = std::min(r.lo, x);
+    r.hi = std::max(r.hi, x);
+  }
+  r.host.insert(r.host.end(), ev, ev + take);
+  host_events_ += take;
+  r.total += take;
+  if (r.total >= static_cast<uint32_t>(prefix_) || last) {
+    r.complete = true;
+    r.t_arrival = t_arrival;
+    if (r.bad || r.total < 2 || !(r.hi > r.lo) || r.total > static_cast<uint32_t>(ref_.N)) {
+      // no z-score or no alignment for this prefix: decided (eject) without the GPU
+      haru_result o;
+      std::memset(&o, 0, sizeof(o));
+      o.read_id = r.id;
+      o.channel = r.channel;
+      o.status = HARU_EINVAL;
+      o.events = r.total;
+      o.end_col = -1;
+      o.t_arrival_ns = t_arrival;
+      o.t_done_ns = now_ns();
+      host_events_ -= r.host.size();
+      if (r.slot >= 0) free_slots_.push_back(r.slot);
+      auto qi = std::find(admit_q_.begin(), admit_q_.end(), r.id);
+      if (qi != admit_q_.end()) admit_q_.erase(qi);
+      reads_.erase(it);
+      {
+        std::lock_guard<std::mutex> lo(out_mu_);
+        done_q_.push_back(o);
+      }
+      n_decided_++;
+      cv_out_.notify_all();
+      return HARU_OK;
+    }
+  }
+  cv_work_.notify_one();
+  return HARU_OK;
+}
+
+int Server::poll(haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us) {
+  *n_out = 0;
+  std::unique_lock<std::mutex> lk(out_mu_);
+  if (done_q_.empty() && error_ == HARU_OK && timeout_us > 0)
+    cv_out_.wait_for(lk, std::chrono::microseconds(timeout_us),
+                     [&] { return !done_q_.empty() || error_ != HARU_OK; });
+  uint32_t k = 0;
+  while (k < max && !done_q_.empty()) {
+    out[k++] = done_q_.front();
+    done_q_.pop_front();
+  }
+  *n_out = k;
+  if (k == 0 && error_ != HARU_OK) return error_;
+  return HARU_OK;
+}
+
+void Server::stats(haru_stream_stats *out) {
+  std::memset(out, 0, sizeof(*out));
+  out->reads_submitted = n_submitted_;
+  out->reads_decided = n_decided_;
+  out->batches = n_batches_;
+  out->max_batch = max_batch_seen_;
+  out->max_concurrent = max_conc_;
+  out->slots = static_cast<uint64_t>(nslots_);
+  std::lock_guard<std::mutex> lk(mu_);
+  out->reads_waiting = admit_q_.size();
+  uint64_t inflight = 0;
+  for (auto &kv : reads_)
+    if (kv.second.slot >= 0) ++inflight;
+  out->reads_in_flight = inflight;
+}
+
+// Admit waiting reads to free slots and copy every host-held event of an
+// admitted read to its slot (one staged transfer and one scatter kernel).
+int Server::turn_upload() {
+  std::vector<CopyOp> ops;
+  size_t staged = 0;
+  std::vector<uint64_t> finished;
+  {
+    std::lock_guard<std::mutex> lk(mu_);
+    while (!admit_q_.empty() && !free_slots_.empty()) {
+      Read &r = reads_[admit_q_.front()];
+      admit_q_.pop_front();
+      r.slot = free_slots_.back();
+      free_slots_.pop_back();
+    }
+    for (auto &kv : reads_) {
+      Read &r = kv.second;
+      if (r.slot < 0 || r.host.empty()) continue;
+      const size_t cnt = r.host.size();
+      if (staged + cnt > stage_cap_ || ops.size() >= ops_cap_) break;
+      std::memcpy(h_stage_ + staged, r.host.data(), cnt * sizeof(float));
+      ops.push_back(CopyOp{static_cast<uint32_t>(r.slot), r.on_device, static_cast<uint32_t>(staged),
+                           static_cast<uint32_t>(cnt)});
+      staged += cnt;
+      r.on_device += static_cast<uint32_t>(cnt);
+      host_events_ -= cnt;
+      r.host.clear();
+      if (r.complete && !r.queued && r.on_device == r.total) finished.push_back(r.id);
+    }
+    // reads completed earlier whose events were already on the device
+    for (auto &kv : reads_) {
+      Read &r = kv.second;
+      if (r.slot >= 0 && r.complete && !r.queued && r.host.empty() && r.on_device == r.total &&
+          std::find(finished.begin(), finished.end(), r.id) == finished.end())
+        finished.push_back(r.id);
+    }
+  }
+  if (!ops.empty()) {
+    std::memcpy(h_ops_, ops.data(), ops.size() * sizeof(CopyOp));
+    cudaError_t e = cudaMemcpyAsync(d_stage_, h_stage_, staged * sizeof(float), cudaMemcpyHostToDevice, up_stream_);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_ops_, h_ops_, ops.size() * sizeof(CopyOp), cudaMemcpyHostToDevice, up_stream_);
+    if (e == cudaSuccess) {
+      scatter_kernel<<<static_cast<unsigned>(ops.size()), 64, 0, up_stream_>>>(d_stage_, d_ops_,
+                                                                               static_cast<int>(ops.size()),
+                                                                               d_slots_, slot_len_);
+      e = cudaGetLastError();
+    }
+    // the staging buffers are reused next turn: wait for this transfer
+    if (e == cudaSuccess) e = cudaEventRecord(up_done_, up_stream_);
+    if (e == cudaSuccess) e = cudaEventSynchronize(up_done_);
+    if (e != cudaSuccess) return HARU_ECUDA;
+  }
+  if (!finished.empty()) {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (uint64_t id : finished) {
+      Read &r = reads_[id];
+      if (!r.queued) {
+        r.queued = true;
+        ready_q_.push_back(id);
+      }
+    }
+  }
+  return HARU_OK;
+}
+
+// Launch a batch of ready reads on a free batch context.
+int Server::turn_launch() {
+  for (auto &b : batches_) {
+    if (b.busy) continue;
+    uint32_t n = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (ready_q_.empty()) return HARU_OK;
+      b.reads.clear();
+      b.h_off[0] = 0;
+      while (!ready_q_.empty() && n < static_cast<uint32_t>(max_batch_)) {
+        Read &r = reads_[ready_q_.front()];
+        ready_q_.pop_front();
+        b.reads.push_back(r.id);
+        b.h_slot[n] = static_cast<uint32_t>(r.slot);
+        b.h_off[n + 1] = b.h_off[n] + r.total;
+        ++n;
+      }
+    }
+    cudaStream_t s = b.stream;
+    cudaError_t e = cudaStreamWaitEvent(s, up_done_, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.d_off, b.h_off, (n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.d_slot, b.h_slot, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      gather_kernel<<<n, 128, 0, s>>>(d_slots_, slot_len_, b.d_slot, b.d_off, static_cast<int>(n), b.d_events);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = ws_reserve(b.ws, precision_, n, lc_);
+    if (e == cudaSuccess)
+      e = ws_enqueue(b.ws, precision_, ref_, b.d_events, b.d_off, n, 1, b.d_cost, b.d_col, lc_, s, nullptr,
+                     nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.h_cost, b.d_cost, n * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.h_col, b.d_col, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b.h_status, b.ws.ints + kIntStatus, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b.done, s);
+    if (e != cudaSuccess) return HARU_ECUDA;
+    b.busy = true;
+    n_batches_++;
+    if (n > max_batch_seen_) max_batch_seen_ = n;
+    uint64_t conc = 0;
+    for (auto &x : batches_) conc += x.busy ? 1 : 0;
+    if (conc > max_conc_) max_conc_ = conc;
+  }
+  return HARU_OK;
+}
+
+// Collect finished batches: decisions, latency stamps, slots freed.
+int Server::turn_complete() {
+  for (auto &b : batches_) {
+    if (!b.busy) continue;
+    cudaError_t q = cudaEventQuery(b.done);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return HARU_ECUDA;
+    const uint64_t t = now_ns();
+    const int st = *b.h_status;
+    const float s = static_cast<float>(1 << ref_.scale_log2);
+    const float thr = precision_ == HARU_INT16 ? std::floor(threshold_ * s) / s : threshold_;
+    std::vector<haru_result> res(b.reads.size());
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      for (size_t i = 0; i < b.reads.size(); ++i) {
+        auto it = reads_.find(b.reads[i]);
+        Read &r = it->second;
+        haru_result &o = res[i];
+        std::memset(&o, 0, sizeof(o));
+        o.read_id = r.id;
+        o.channel = r.channel;
+        o.cost = b.h_cost[i];
+        o.end_col = b.h_col[i];
+        o.events = r.total;
+        o.status = st;
+        o.decision = (st == HARU_OK && o.cost <= thr) ? 1 : 0;
+        o.t_arrival_ns = r.t_arrival;
+        o.t_done_ns = t;
+        free_slots_.push_back(r.slot);
+        reads_.erase(it);
+      }
+    }
+    b.busy = false;
+    {
+      std::lock_guard<std::mutex> lk(out_mu_);
+      for (auto &o : res) done_q_.push_back(o);
+    }
+    n_decided_ += res.size();
+    cv_out_.notify_all();
+  }
+  return HARU_OK;
+}
+
+void Server::worker() {
+  if (cudaSetDevice(ctx_->device) != cudaSuccess) {
+    fail(HARU_ECUDA);
+    return;
+  }
+  while (run_) {
+    int rc = turn_complete();
+    if (rc == HARU_OK) rc = turn_upload();
+    if (rc == HARU_OK) rc = turn_launch();
+    if (rc != HARU_OK) {
+      fail(rc);
+      return;
+    }
+    std::unique_lock<std::mutex> lk(mu_);
+    bool busy = false;
+    for (auto &b : batches_) busy = busy || b.busy;
+    const bool work = !ready_q_.empty() || host_events_ > 0;
+    if (!work)
+      cv_work_.wait_for(lk, std::chrono::microseconds(busy ? 50 : 200));
+  }
+}
+
+void server_destroy(Server *s) { delete s; }
+
+}  // namespace haru
+
+extern "C" {
+
+int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const float *events, uint32_t n,
+                       uint64_t t_arrival_ns, int last_chunk) {
+  if (!ctx) return HARU_EINVAL;
+  haru::Server *srv = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->sticky) return ctx->sticky;
+    if (ctx->N == 0) return HARU_ENOREF;
+    if (!ctx->server) {
+      auto *s = new (std::nothrow) haru::Server(ctx);
+      if (!s) return HARU_ENOMEM;
+      const int rc = s->start();
+      if (rc != HARU_OK) {
+        delete s;
+        return rc;
+      }
+      ctx->server = s;
+    }
+    srv = ctx->server;
+  }
+  return srv->submit(read_id, channel, events, n, t_arrival_ns, last_chunk);
+}
+
+int haru_stream_poll(haru_ctx *ctx, haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us) {
+  if (!ctx || !n_out || (max > 0 && !out)) return HARU_EINVAL;
+  *n_out = 0;
+  haru::Server *srv = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    srv = ctx->server;
+  }
+  if (!srv) return HARU_OK;
+  return srv->poll(out, max, n_out, timeout_us);
+}
+
+int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out) {
+  if (!ctx || !out) return HARU_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  haru::Server *srv = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    srv = ctx->server;
+  }
+  if (srv) srv->stats(out);
+  return HARU_OK;
+}
+
+}  // extern "C"

@@ -290,3 +290,34 @@ def flowcell_schedule(channels: int, duration_s: float, seed: int, prefix_events
     ev = np.concatenate(prefixes).astype(np.float32) if prefixes else np.zeros(0, np.float32)
     q = Queries(ev, off, np.array(on_list, dtype=bool), np.array(truth, dtype=np.int64))
     return chunks, q
+
+
+def replay(chunks, submit, speed: float = 1.0, stop=None):
+    """Deliver a flow-cell schedule in (scaled) wall-clock time.
+
+    submit(chunk, t_arrival_ns) is called for every chunk at start +
+    chunk.t / speed, with the CLOCK_MONOTONIC time of delivery; it returns a
+    status code, and a nonzero code other than busy (-4) stops the replay.
+    Busy chunks are retried after 200 microseconds. Returns the number of
+    chunks delivered late by more than 5 ms (a measure of replay fidelity).
+    """
+    import time
+    t0 = time.monotonic_ns()
+    late = 0
+    for c in chunks:
+        due = t0 + int(c.t / speed * 1e9)
+        now = time.monotonic_ns()
+        if due > now:
+            time.sleep((due - now) / 1e9)
+        elif now - due > 5_000_000:
+            late += 1
+        while True:
+            rc = submit(c, time.monotonic_ns())
+            if rc != -4:
+                break
+            time.sleep(0.0002)
+        if rc != 0:
+            raise RuntimeError(f"submit failed with {rc}")
+        if stop is not None and stop():
+            break
+    return late

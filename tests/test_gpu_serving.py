@@ -1,0 +1,106 @@
+"""The serving loop: continuous batching of Read Until decisions.
+
+Reads arrive as chunks from a simulated flow cell; every decision must equal
+the same read's prefix aligned alone in a batch of one (same kernels, same
+arithmetic), whatever batch it shared on the GPU; a sample is also checked
+against the oracle.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def haru():
+    import paper_2211_07340_gb300 as h
+    h.build_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return h
+
+
+@pytest.fixture(scope="module")
+def ref():
+    return oracle.ref_levels(synth.genome(synth.SARS_COV_2_BASES, synth.SEED_GENOME_ON), synth.pore_model(6), 6)
+
+
+def run_schedule(ctx, chunks, speed):
+    results = []
+    done = threading.Event()
+
+    def poller():
+        while not done.is_set():
+            results.extend(ctx.stream_poll(4096, 2000))
+
+    th = threading.Thread(target=poller)
+    th.start()
+
+    def submit(c, t):
+        return ctx.stream_submit(c.read_id, c.channel, c.events, t, c.last)
+
+    synth.replay(chunks, submit, speed=speed)
+    n_reads = len({c.read_id for c in chunks})
+    deadline = time.monotonic() + 30
+    while len(results) < n_reads and time.monotonic() < deadline:
+        time.sleep(0.01)
+    done.set()
+    th.join()
+    results.extend(ctx.stream_poll(4096, 0))
+    return results
+
+
+@pytest.mark.parametrize("prec,budget", [(1, 64 << 20), (0, 64 << 20), (1, 8 * 1024)])
+def test_decisions_match_alone(haru, ref, prec, budget):
+    chunks, q = synth.flowcell_schedule(48, 4.0, seed=105)
+    with haru.Context(serve_precision=prec, serve_budget_bytes=budget, threshold=60.0) as ctx:
+        ctx.ref_load(ref)
+        res = run_schedule(ctx, chunks, speed=4.0)
+        stats = ctx.stream_stats()
+        assert len(res) == q.nq, (len(res), q.nq, stats)
+        by_id = {r.read_id: r for r in res}
+        assert sorted(by_id) == list(range(q.nq))
+        assert all(r.status == 0 for r in res)
+        cost, col = ctx.sdtw_batch(prec, q.events, q.offsets)  # one batch, for reference below
+        for i in range(q.nq):
+            alone_c, alone_j = ctx.sdtw_batch(prec, q.query(i), np.array([0, 250], np.uint32))
+            r = by_id[i]
+            assert r.cost == alone_c[0] and r.end_col == alone_j[0], i
+            assert r.cost == cost[i] and r.end_col == col[i]
+            assert r.decision == int(r.cost <= (np.floor(60.0 * 64) / 64 if prec == 1 else 60.0))
+            assert r.t_done_ns >= r.t_arrival_ns
+    if budget < 64 << 20:
+        assert stats["slots"] == 8 and stats["reads_submitted"] == q.nq
+    idx = np.arange(0, q.nq, 9)
+    sub = q.subset(idx)
+    o = oracle.batch(oracle.PREC_I16 if prec == 1 else oracle.PREC_F32, ref, sub.events, sub.offsets)
+    np.testing.assert_array_equal([by_id[i].end_col for i in idx], o.col)
+    np.testing.assert_array_equal(np.array([by_id[i].cost for i in idx], np.float64),
+                                  o.cost if prec == 1 else o.cost.astype(np.float32).astype(np.float64))
+
+
+def test_flat_and_short_reads_are_rejected_alone(haru, ref):
+    with haru.Context() as ctx:
+        ctx.ref_load(ref)
+        t = time.monotonic_ns()
+        assert ctx.stream_submit(1, 0, np.full(250, 80.0, np.float32), t, True) == 0
+        assert ctx.stream_submit(2, 1, np.array([80.0], np.float32), t, True) == 0
+        good = synth.flowcell_schedule(1, 2.0, seed=7)[1].query(0)
+        assert ctx.stream_submit(3, 2, good, t, True) == 0
+        got = {}
+        deadline = time.monotonic() + 10
+        while len(got) < 3 and time.monotonic() < deadline:
+            for r in ctx.stream_poll(16, 1000):
+                got[r.read_id] = r
+        assert got[1].status == haru.HARU_EINVAL and got[1].decision == 0
+        assert got[2].status == haru.HARU_EINVAL
+        assert got[3].status == 0
+        assert ctx.stream_poll(16, 1000) == []  # nothing pending: times out empty
