@@ -137,6 +137,67 @@ def cpu_baseline(ref, queries, target_s: float = 12.0, prec=None):
                       f"{dt:.1f} s"}
 
 
+def pick_threshold(costs, on_target):
+    """Decision threshold from a labelled held-out set: the cost cut with the
+    fewest misclassified queries (accept iff cost <= T); among equally good
+    cuts the first, placed midway between the two neighbouring costs."""
+    order = np.argsort(costs, kind="stable")
+    c, y = np.asarray(costs)[order], np.asarray(on_target)[order]
+    n = c.shape[0]
+    # accept the first k: errors = off-target among them + on-target after them
+    off_before = np.concatenate([[0], np.cumsum(~y)])
+    on_after = np.concatenate([[y.sum()], y.sum() - np.cumsum(y)])
+    err = off_before + on_after
+    k = int(np.argmin(err))
+    if k == 0:
+        return float(c[0]) - 1.0
+    if k == n:
+        return float(c[-1]) + 1.0
+    return float(0.5 * (c[k - 1] + c[k]))
+
+
+def run_serving(haru, args, local, w, threshold):
+    """Serve a simulated flow cell in real time; latency from the delivery of
+    the chunk that completes a read's 250-event prefix to its decision."""
+    chunks, q = synth.flowcell_schedule(args.serve_channels, args.serve_seconds, seed=105)
+    ctx = haru.Context(local, serve_precision=haru.HARU_INT16, threshold=threshold)
+    ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
+    results = []
+    done = threading.Event()
+
+    def poller():
+        while not done.is_set():
+            results.extend(ctx.stream_poll(8192, 2000))
+
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    t_start = time.monotonic_ns()
+    late = synth.replay(chunks, lambda c, t: ctx.stream_submit(c.read_id, c.channel, c.events, t, c.last))
+    deadline = time.monotonic() + 30
+    while len(results) < q.nq and time.monotonic() < deadline:
+        time.sleep(0.01)
+    done.set()
+    th.join()
+    results.extend(ctx.stream_poll(8192, 0))
+    st = ctx.stream_stats()
+    ctx.close()
+    warm_ns = t_start + int(args.serve_warm * 1e9)
+    lat = np.array([(r.t_done_ns - r.t_arrival_ns) / 1e6 for r in results if r.t_arrival_ns >= warm_ns])
+    dec = {r.read_id: r.decision for r in results}
+    acc = float(np.mean([dec.get(i, 0) == int(q.on_target[i]) for i in range(q.nq)])) if q.nq else None
+    N = 2 * (synth.SARS_COV_2_BASES - 5)
+    span = args.serve_seconds
+    return {"channels": args.serve_channels, "seconds": span, "warmup_s": args.serve_warm, "reads": q.nq,
+            "decided": len(results), "precision": "int16", "threshold_z": threshold,
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "max_ms": float(lat.max()) if lat.size else None, "latency_samples": int(lat.size),
+            "decisions_per_s": len(results) / span, "gcups": len(results) * 250 * N / span / 1e9,
+            "accept_eject_accuracy_vs_truth": acc, "batches": st["batches"], "max_batch": st["max_batch"],
+            "max_concurrent_batches": st["max_concurrent"], "late_chunks": late,
+            "latency_clock": "chunk delivery that completes the prefix -> decision available (CLOCK_MONOTONIC)"}
+
+
 def run_reference(args, rank: int):
     """The reference arm: the oracle timed on the host cores."""
     if rank != 0:
@@ -190,6 +251,9 @@ def main():
     ap.add_argument("--units", type=int, default=0, help="work units target (0 = library default)")
     ap.add_argument("--forms", default="int16,fp32", help="forms to time (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="simulated flow-cell run (0 = skip)")
+    ap.add_argument("--serve-warm", type=float, default=2.0, help="seconds of serving excluded from latency stats")
+    ap.add_argument("--serve-channels", type=int, default=512)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -360,6 +424,11 @@ def main():
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps * len(forms),
     }
+    if args.serve_seconds > 0:
+        held = synth.workload("sars_heldout_1024", seed=103)
+        hc, _ = ctx.sdtw_batch(haru.HARU_FP32, held.queries.events, held.queries.offsets)
+        thr = pick_threshold(hc.astype(np.float64), held.queries.on_target)
+        result["serving"] = run_serving(haru, args, local, w, thr)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         ref_levels = oracle.ref_levels(w.genome, w.model, w.k)

@@ -273,3 +273,20 @@ class Context:
         a, b = ctypes.c_float(), ctypes.c_float()
         check(lib().haru_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)), "haru_last_timing")
         return a.value, b.value
+
+
+def shard_queries(offsets, world: int, rank: int):
+    """Contiguous range [lo, hi) of queries for `rank` of `world` GPUs, cut so
+    that every rank gets about the same number of events (the sweep's work
+    grows with each query's length). Queries are independent, so ranks need
+    no exchange beyond gathering their results."""
+    off = np.asarray(offsets, dtype=np.int64)
+    nq = off.shape[0] - 1
+    if world <= 1 or nq == 0:
+        return 0, nq
+    total = int(off[-1])
+    cuts = [0] + [int(np.searchsorted(off, total * r / world, side="left")) for r in range(1, world)] + [nq]
+    cuts = [min(max(c, 0), nq) for c in cuts]
+    for i in range(1, len(cuts)):
+        cuts[i] = max(cuts[i], cuts[i - 1])
+    return cuts[rank], cuts[rank + 1]
