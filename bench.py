@@ -48,6 +48,27 @@ def peaks_file():
     return {}
 
 
+def profiled_traffic(form: str):
+    """DRAM bytes (read + write) of one batch's sweep kernels from the
+    committed ncu summary, or None if the kernel source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "sdtw_sweep_sars_uneven_8192.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.startswith("    "):
+                k, v = line.strip().split(":", 1)
+                vals[k.strip()] = v.strip()
+    csrc = os.path.join(ROOT, "paper_2211_07340_gb300", "csrc")
+    src = open(os.path.join(csrc, "sdtw.cu"), "rb").read() + open(os.path.join(csrc, "haru_internal.h"), "rb").read()
+    if vals.get("kernel_source_sha1") != hashlib.sha1(src).hexdigest():
+        return None
+    v = vals.get(f"traffic_bytes_per_step_{form}")
+    return float(v) if v is not None else None
+
+
 def alu_peak_gcups(sms: int, clock_mhz: float) -> float:
     """Peak cell rate of the sweep for both forms at the given SM clock.
 
@@ -389,6 +410,8 @@ def main():
     value32 = total_cells / (ms32 / 1e3) / 1e9
     e2e_value = total_cells / (e2e_ms / 1e3) / 1e9
 
+    probe16 = ctx.probe_peak(haru.HARU_INT16) / 1e9
+    probe32 = ctx.probe_peak(haru.HARU_FP32) / 1e9
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     pk = peaks_file()
@@ -406,15 +429,20 @@ def main():
                    "parallelism": f"dp{world} (independent batches per GPU)", "tile_cols": cfg.tile_cols,
                    "warps_per_cta": cfg.warps_per_cta, "units_target": cfg.units_target},
         "roofline": {"bound": "alu", "kernel": "sdtw_kernel<INT16>", "achieved": ach16, "peak": peak,
-                     "unit": "GCUPS", "frac": ach16 / peak, "traffic": None,
+                     "unit": "GCUPS", "frac": ach16 / peak, "traffic": profiled_traffic("int16"),
+                     "traffic_unit": "bytes per batch (DRAM read+write, ncu, profiles/sdtw_sweep_sars_uneven_8192.md)",
                      "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (half-rate DPX pipe, 1.5 ops/cell) x "
                                    f"{max_mhz:.0f} MHz max SM clock",
                      "frac_at_sampled_clock": (ach16 / alu_peak_gcups(sms, clocks["sm_mhz"]))
-                     if clocks.get("sm_mhz") else None},
+                     if clocks.get("sm_mhz") else None,
+                     "peak_probe": probe16, "frac_of_probe": ach16 / probe16,
+                     "peak_probe_basis": "haru_probe_peak: the int16 cell-pair instructions on independent "
+                                         "chains, no shuffles/reference/tracking, same run"},
         "fp32": {"value": value32, "unit": "GCUPS", "ms_per_step": ms32, "dtype": "f32",
                  "roofline": {"bound": "alu", "kernel": "sdtw_kernel<FP32>", "achieved": ach32, "peak": peak,
-                              "unit": "GCUPS", "frac": ach32 / peak,
-                              "peak_basis": "3 issue slots per cell (sub, 3-input min, fma) at 4 warp-instr/clk/SM"},
+                              "unit": "GCUPS", "frac": ach32 / peak, "traffic": profiled_traffic("fp32"),
+                              "peak_basis": "3 issue slots per cell (sub, 3-input min, fma) at 4 warp-instr/clk/SM",
+                              "peak_probe": probe32, "frac_of_probe": ach32 / probe32},
                  "clocks": clocks32},
         "int16_over_fp32": value / value32 if value32 == value32 else None,
         "prep_ms_per_step": ms16 - sweep16,

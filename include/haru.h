@@ -236,6 +236,14 @@ int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep);
 int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets,
                             uint32_t nq, float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);
 
+/* Measured ceiling of the cell update: the per-cell instructions of the
+ * given form (int16: vsub2, viaddmax_relu, vimin3, viaddmin per two cells;
+ * FP32: sub, 3-input min, fma per cell) issued on independent chains over
+ * every SM, with none of the wavefront's data movement. *cells_per_s is the
+ * best of three runs at the clock the GPU ran them. Errors: HARU_EINVAL,
+ * HARU_ECUDA. */
+int haru_probe_peak(haru_ctx *ctx, int precision, double *cells_per_s);
+
 /* Human-readable name of a status code (static storage). */
 const char *haru_strerror(int code);
 

@@ -103,6 +103,7 @@ _SIGS = {
     "haru_last_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_float)]),
     "haru_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "haru_probe_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "haru_sdtw_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                ctypes.c_uint32]),
@@ -267,6 +268,12 @@ class Context:
         st = haru_stream_stats()
         check(lib().haru_stream_get_stats(self._h, ctypes.byref(st)), "haru_stream_get_stats")
         return {f: int(getattr(st, f)) for f, _ in haru_stream_stats._fields_}
+
+    def probe_peak(self, precision: int) -> float:
+        """Measured cells/s ceiling of the form's cell update (no data movement)."""
+        v = ctypes.c_double()
+        check(lib().haru_probe_peak(self._h, int(precision), ctypes.byref(v)), "haru_probe_peak")
+        return v.value
 
     def last_timing(self):
         """(ms_prep, ms_sweep) of the last HARU_PROFILE batch."""
