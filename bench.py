@@ -37,6 +37,8 @@ METRIC = "sDTW GCUPS (int16 DPX vs FP32) at 1 GB300; p50/p99 Read Until decision
 WORKLOAD = "sars_uneven_8192"
 WORKLOAD_DESC = ("8192 raw-event queries, M ~ U[100,500], 50% on-target, vs a 29,903-base genome's 6-mer "
                  "levels on both strands (N = 59,796)")
+LONG_DESC = ("512 raw-event queries x 250 events, 50% on-target, vs a 5,000,000-base genome's 6-mer levels on "
+             "both strands (N = 9,999,990)")
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
@@ -270,8 +272,10 @@ def main():
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--nq", type=int, default=0, help="first nq queries only (profiling runs)")
     ap.add_argument("--units", type=int, default=0, help="work units target (0 = library default)")
-    ap.add_argument("--forms", default="int16,fp32", help="forms to time (profiling runs)")
+    ap.add_argument("--forms", default="int16,fp32", help="forms to time: int16, int16exact, fp32")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the library defaults)")
+    ap.add_argument("--workload", default=WORKLOAD, help="sars_uneven_8192 (default) or long_512x250")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="simulated flow-cell run (0 = skip)")
     ap.add_argument("--serve-warm", type=float, default=2.0, help="seconds of serving excluded from latency stats")
     ap.add_argument("--serve-channels", type=int, default=512)
@@ -294,7 +298,7 @@ def main():
     haru.build_library()
 
     # Weak scaling: every rank aligns its own batch (independent seeds).
-    w = synth.workload(WORKLOAD, seed=101 + 1000 * rank)
+    w = synth.workload(args.workload, seed=(101 if args.workload == WORKLOAD else 104) + 1000 * rank)
     q = w.queries if not args.nq else w.queries.subset(np.arange(min(args.nq, w.queries.nq)))
     cfg = haru.default_config()
     if args.tile:
@@ -315,8 +319,14 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     launches_per_step = 3  # planner, pack, sweep
 
-    def run_form(prec):
+    tuned = {}
+
+    def run_form(prec, exact_share=0):
         sh = stream.cuda_stream
+        ctx.configure(int16_exact_share=exact_share)
+        if not args.no_tune:
+            key = "int16_exact_share" if exact_share else ("int16" if prec == haru.HARU_INT16 else "fp32")
+            tuned[key] = ctx.autotune(prec, ev_d, off_d, raw=True, on_device=True)
         with torch.cuda.stream(stream):
             for _ in range(2):  # allocate the context workspace outside capture
                 ctx.sdtw_batch_device(prec, ev_d, off_d, cost_d, col_d, stream=sh, asynchronous=True,
@@ -372,10 +382,16 @@ def main():
     ms16 = sweep16 = ms32 = sweep32 = nan
     clocks = clocks32 = {}
     graphed = False
+    msdpx = sweepdpx = nan
     if "int16" in forms:
         ms16, sweep16, clocks, graphed = run_form(haru.HARU_INT16)
+    if "int16exact" in forms:
+        msdpx, sweepdpx, _, _ = run_form(haru.HARU_INT16, exact_share=1)
     if "fp32" in forms:
         ms32, sweep32, clocks32, _ = run_form(haru.HARU_FP32)
+    ctx.configure(int16_exact_share=0)
+    if "int16" in tuned:
+        ctx.configure(**tuned["int16"])
 
     # End to end through the C ABI with host buffers: H2D of raw events and
     # offsets, the batch, D2H of costs and columns, every step.
@@ -423,14 +439,17 @@ def main():
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms16, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i16", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "global_batch": q.nq * world, "reference_len": N,
-                   "cells_per_step": total_cells, "form": "int16 (two queries per 32-bit lane)",
+        "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD else LONG_DESC,
+                   "global_batch": q.nq * world, "reference_len": N,
+                   "cells_per_step": total_cells,
+                   "form": "int16 (two queries per 32-bit lane, DPX min-plus)",
                    "cuda_graph": graphed, "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": f"dp{world} (independent batches per GPU)", "tile_cols": cfg.tile_cols,
-                   "warps_per_cta": cfg.warps_per_cta, "units_target": cfg.units_target},
+                   "parallelism": f"dp{world} (independent batches per GPU)",
+                   "autotuned": tuned},
         "roofline": {"bound": "alu", "kernel": "sdtw_kernel<INT16>", "achieved": ach16, "peak": peak,
                      "unit": "GCUPS", "frac": ach16 / peak, "traffic": profiled_traffic("int16"),
-                     "traffic_unit": "bytes per batch (DRAM read+write, ncu, profiles/sdtw_sweep_sars_uneven_8192.md)",
+                     "traffic_unit": "bytes per batch (DRAM read+write, ncu at the default launch shape, "
+                                     "profiles/sdtw_sweep_sars_uneven_8192.md)",
                      "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (half-rate DPX pipe, 1.5 ops/cell) x "
                                    f"{max_mhz:.0f} MHz max SM clock",
                      "frac_at_sampled_clock": (ach16 / alu_peak_gcups(sms, clocks["sm_mhz"]))
@@ -444,6 +463,10 @@ def main():
                               "peak_basis": "3 issue slots per cell (sub, 3-input min, fma) at 4 warp-instr/clk/SM",
                               "peak_probe": probe32, "frac_of_probe": ach32 / probe32},
                  "clocks": clocks32},
+        "int16_exact_share": ({"value": total_cells / (msdpx / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": msdpx,
+                               "sweep_gcups": cells / (sweepdpx / 1e3) / 1e9,
+                               "note": "int16 with two thirds of the warps on exact-integer FP32 strips"}
+                              if msdpx == msdpx else None),
         "int16_over_fp32": value / value32 if value32 == value32 else None,
         "prep_ms_per_step": ms16 - sweep16,
         "e2e": {"value": e2e_value, "unit": "GCUPS", "ms_per_step": e2e_ms,
@@ -452,7 +475,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps * len(forms),
     }
-    if args.serve_seconds > 0:
+    if args.serve_seconds > 0 and args.workload == WORKLOAD:
         held = synth.workload("sars_heldout_1024", seed=103)
         hc, _ = ctx.sdtw_batch(haru.HARU_FP32, held.queries.events, held.queries.offsets)
         thr = pick_threshold(hc.astype(np.float64), held.queries.on_target)

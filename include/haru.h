@@ -79,6 +79,11 @@ typedef struct {
   uint32_t serve_prefix;    /* events per decision prefix; 0 = 250 (Section 4.1) */
   int units_target;         /* work units (query x reference segment) a batch is cut into, at least;
                                0 = 4 x SMs x warps_per_cta; 1 = never split the reference */
+  int int16_exact_share;    /* int16 batches: 0 (default) = every warp runs packed DPX query pairs;
+                               1 = two of every three warps compute their query exactly on the int16
+                               codes in FP32 instead (identical results: saturating every cell equals
+                               saturating the exact cost once), to load the FMA pipe as well as the
+                               half-rate min/DPX pipe. Measured slower on GB300; kept as an option. */
 } haru_config;
 
 /* Fill *cfg with defaults. Returns HARU_OK, or HARU_EINVAL if cfg is NULL. */
@@ -87,6 +92,13 @@ int haru_config_default(haru_config *cfg);
 /* Create a context on CUDA device `device` (the device is made current for
  * every later call on this context). cfg may be NULL (defaults). */
 int haru_create(haru_ctx **out, int device, const haru_config *cfg);
+
+/* Replace the context's configuration for later batches. The serving fields
+ * take effect only before the first haru_stream_submit. Errors: HARU_EINVAL. */
+int haru_configure(haru_ctx *ctx, const haru_config *cfg);
+
+/* Copy the context's current configuration (e.g. after haru_autotune). */
+int haru_get_config(haru_ctx *ctx, haru_config *cfg);
 
 /* Release the context, its device memory and its serving thread. NULL is a no-op. */
 void haru_destroy(haru_ctx *ctx);
@@ -235,6 +247,17 @@ int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep);
 #define HARU_NOALLOC_MAX_QUERIES 1024
 int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets,
                             uint32_t nq, float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);
+
+/* Autotuner: run the batch path on this batch (layout and flags as in
+ * haru_sdtw_batch; HARU_ON_DEVICE and HARU_RAW are honoured) under every
+ * combination of warps per CTA {4, 8}, tile width {2048, 4096, 8192, 16384}
+ * and work-unit target {1 (no reference segments), auto, 2 x auto}, keep the
+ * fastest (minimum of two timed runs each) in the context's configuration
+ * for later batches, and copy the resulting configuration to *chosen (may be
+ * NULL). The strip height is fixed by each query's length. Results of the
+ * trial runs are discarded. Errors: as haru_sdtw_batch. */
+int haru_autotune(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
+                  uint32_t flags, haru_config *chosen);
 
 /* Measured ceiling of the cell update: the per-cell instructions of the
  * given form (int16: vsub2, viaddmax_relu, vimin3, viaddmin per two cells;

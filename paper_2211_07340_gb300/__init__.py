@@ -58,6 +58,7 @@ class haru_config(ctypes.Structure):
         ("serve_max_batch", ctypes.c_uint32),
         ("serve_prefix", ctypes.c_uint32),
         ("units_target", ctypes.c_int),
+        ("int16_exact_share", ctypes.c_int),
     ]
 
 
@@ -85,6 +86,8 @@ _SIGS = {
     "haru_config_default": (ctypes.c_int, [ctypes.POINTER(haru_config)]),
     "haru_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(haru_config)]),
     "haru_destroy": (None, [ctypes.c_void_p]),
+    "haru_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_config)]),
+    "haru_get_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_config)]),
     "haru_ref_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int]),
     "haru_ref_build": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                                       ctypes.c_int, ctypes.c_int]),
@@ -104,6 +107,8 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_float)]),
     "haru_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "haru_probe_peak": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "haru_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                     ctypes.c_uint32, ctypes.POINTER(haru_config)]),
     "haru_sdtw_batch_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                ctypes.c_uint32]),
@@ -173,6 +178,16 @@ class Context:
     @property
     def handle(self):
         return self._h
+
+    def configure(self, **kw):
+        """Change configuration fields (launch shape, int16 mode, ...) for later batches."""
+        cfg = haru_config()
+        check(lib().haru_get_config(self._h, ctypes.byref(cfg)), "haru_get_config")
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        check(lib().haru_configure(self._h, ctypes.byref(cfg)), "haru_configure")
+        self.config = cfg
+        return cfg
 
     def close(self):
         if self._h:
@@ -268,6 +283,20 @@ class Context:
         st = haru_stream_stats()
         check(lib().haru_stream_get_stats(self._h, ctypes.byref(st)), "haru_stream_get_stats")
         return {f: int(getattr(st, f)) for f, _ in haru_stream_stats._fields_}
+
+    def autotune(self, precision: int, events, offsets, raw: bool = True, on_device: bool = False) -> dict:
+        """Pick warps per CTA, tile width and work-unit target on this batch;
+        the choice stays in the context. Returns the chosen settings."""
+        cfg = haru_config()
+        nq = int(offsets.shape[0]) - 1
+        flags = (HARU_RAW if raw else 0) | (HARU_ON_DEVICE if on_device else 0)
+        if not on_device:
+            events = np.ascontiguousarray(events, dtype=np.float32)
+            offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+        check(lib().haru_autotune(self._h, int(precision), _ptr(events), _ptr(offsets), nq, flags,
+                                  ctypes.byref(cfg)), "haru_autotune")
+        self.config = cfg
+        return {"warps_per_cta": cfg.warps_per_cta, "tile_cols": cfg.tile_cols, "units_target": cfg.units_target}
 
     def probe_peak(self, precision: int) -> float:
         """Measured cells/s ceiling of the form's cell update (no data movement)."""

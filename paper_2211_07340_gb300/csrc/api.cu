@@ -56,6 +56,7 @@ haru::LaunchCfg haru_ctx::launch_cfg() const {
   lc.ctas_per_sm = cfg.ctas_per_sm;
   lc.sms = sms;
   lc.units_target = cfg.units_target;
+  lc.int16_mode = cfg.int16_exact_share ? 2 : 1;
   lc.wait_ns = wait_ns(cfg);
   return lc;
 }
@@ -161,6 +162,20 @@ int haru_create(haru_ctx **out, int device, const haru_config *cfg) {
     return rc;
   }
   *out = ctx;
+  return HARU_OK;
+}
+
+int haru_configure(haru_ctx *ctx, const haru_config *cfg) {
+  if (!ctx || !cfg) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->cfg = *cfg;
+  return HARU_OK;
+}
+
+int haru_get_config(haru_ctx *ctx, haru_config *cfg) {
+  if (!ctx || !cfg) return HARU_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *cfg = ctx->cfg;
   return HARU_OK;
 }
 

@@ -25,11 +25,12 @@ void ws_free(Workspace &ws) {
 }
 
 cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCfg &lc) {
-  const size_t max_items = precision == HARU_INT16 ? (static_cast<size_t>(nq) + 1) / 2 + kMaxS : nq;
+  const int mode = plan_mode(precision, lc);
+  const size_t max_items = items_bound(mode, nq);
   // Work units: enough (query x reference segment) units to keep every SM
   // busy to the end; nseg_cap bounds the segments per item for storage.
   const int units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * lc.warps;
-  const size_t items_min = precision == HARU_INT16 ? (static_cast<size_t>(nq) + 1) / 2 : nq;
+  const size_t items_min = mode == 0 ? nq : (mode == 1 ? (static_cast<size_t>(nq) + 1) / 2 : (3 * static_cast<size_t>(nq)) / 4);
   int nseg_cap = static_cast<int>(
       std::min<size_t>(kMaxSeg, (static_cast<size_t>(units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
   if (nseg_cap < 1) nseg_cap = 1;
@@ -70,7 +71,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   pa.offsets = d_offsets;
   pa.nq = nq;
   pa.N = ref.N;
-  pa.pair = precision == HARU_INT16;
+  pa.pair = plan_mode(precision, lc);
   pa.warps = lc.warps;
   pa.units_target = ws.units_target;
   pa.nseg_cap = ws.nseg_cap;

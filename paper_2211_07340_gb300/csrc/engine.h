@@ -37,8 +37,21 @@ struct LaunchCfg {
   int ctas_per_sm = 0;
   int sms = 1;
   int units_target = 0;  // 0: 4 x sms x warps
+  int int16_mode = 1;    // int16 batches: 1 = DPX pairs only, 2 = pairs and exact-FP32 strips (1:2 warps)
   unsigned long long wait_ns = 2000000000ull;
 };
+
+// Planner mode of a batch: 0 FP32, 1 int16 pairs, 2 int16 pairs + exact strips.
+inline int plan_mode(int precision, const LaunchCfg &lc) {
+  return precision == HARU_INT16 ? (lc.int16_mode == 1 ? 1 : 2) : 0;
+}
+
+// Most items a batch of nq queries can make in `mode` (per-bucket rounding included).
+inline size_t items_bound(int mode, size_t nq) {
+  if (mode == 0) return nq;
+  if (mode == 1) return (nq + 1) / 2 + kMaxS;
+  return (3 * nq + 3) / 4 + 2 * kMaxS;
+}
 
 // The reference as the kernels read it.
 struct RefView {

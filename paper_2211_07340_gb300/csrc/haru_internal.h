@@ -10,14 +10,18 @@
 
 namespace haru {
 
-// One warp's work: a query (FP32) or a pair of queries packed into the two
-// 16-bit halves of every register (INT16). qb < 0 when the pair is short.
-// Its steps are cut into nseg segments (work units).
+// One warp's work: a query (FP32), a pair of queries packed into the two
+// 16-bit halves of every register (INT16 pair), or one query of an int16
+// batch computed exactly on integer codes in FP32 (INT16 exact). qb < 0 when
+// a pair is short. Its steps are cut into nseg segments (work units).
+constexpr int kItemF32 = 0, kItemPair = 1, kItemExact = 2;
 struct Item {
   int qa;
   int qb;
   int S;     // rows per lane of the warp strip: 32 * S >= longest query of the item
   int nseg;  // segments of its sweep
+  int kind;  // kItemF32, kItemPair or kItemExact
+  int pad[3];
 };
 
 // Consecutive items with the same S swept over the same segment by one CTA,
@@ -118,7 +122,7 @@ struct PlanArgs {
   const uint32_t *offsets;  // nq + 1
   uint32_t nq;
   long N;
-  int pair;                 // 1: INT16 (two queries per item)
+  int pair;                 // 0: FP32 singles; 1: INT16 pairs; 2: INT16 pairs and exact-FP32 singles (1:2 warps)
   int warps;                // items per group
   int units_target;         // wanted work units (item x segment) in the batch
   int nseg_cap;             // most segments per item (state storage is sized for it)

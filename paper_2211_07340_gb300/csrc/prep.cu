@@ -116,6 +116,16 @@ __device__ __forceinline__ int strip_rows(const uint32_t *off, uint32_t q, long 
   return static_cast<int>((m + 31) / 32);
 }
 
+// Items of a bucket of n queries. Mode 2 (int16 split over both pipes)
+// repeats the pattern [pair, exact, exact] over runs of four queries, so a
+// group's warps mix the DPX pairs and the exact-FP32 singles 1:2.
+__device__ __forceinline__ int bucket_items(int mode, int n) {
+  if (mode == 0) return n;
+  if (mode == 1) return (n + 1) / 2;
+  const int r = n % 4;
+  return 3 * (n / 4) + (r == 0 ? 0 : (r == 3 ? 2 : 1));
+}
+
 // One CTA of 1024 threads. Buckets queries by strip height S (descending,
 // the longest-processing-time-first order of the work queue), keeps the
 // input order inside a bucket, pairs neighbours for the int16 form, and cuts
@@ -135,7 +145,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
   if (tid == 0) {
     int base = 0;
     for (int S = kMaxS; S >= 1; --S) {
-      icount[S] = a.pair ? (cnt[S] + 1) / 2 : cnt[S];
+      icount[S] = bucket_items(a.pair, cnt[S]);
       ibase[S] = base;
       base += icount[S];
     }
@@ -181,6 +191,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
   for (int i = tid; i < n_items; i += blockDim.x) {
     Item it;
     it.qa = -1; it.qb = -1; it.S = 0; it.nseg = 1;
+    it.kind = a.pair == 0 ? kItemF32 : kItemPair;
+    it.pad[0] = it.pad[1] = it.pad[2] = 0;
     a.items[i] = it;
   }
   __syncthreads();
@@ -213,13 +225,23 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
       __syncthreads();
       if (pred) {
         const int pos = run[b] + wpre[warp] + __popc(mask & lt);
-        if (a.pair) {
+        if (a.pair == 1) {
           Item *it = &a.items[ibase[b] + pos / 2];
           if (pos % 2 == 0) { it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b]; }
           else it->qb = static_cast<int>(q);
+        } else if (a.pair == 2) {
+          const int w = pos % 4;
+          Item *it = &a.items[ibase[b] + 3 * (pos / 4) + (w < 2 ? 0 : w - 1)];
+          if (w == 1) {
+            it->qb = static_cast<int>(q);
+          } else {
+            it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b];
+            it->kind = w == 0 ? kItemPair : kItemExact;
+          }
         } else {
           Item it;
-          it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b];
+          it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b]; it.kind = kItemF32;
+          it.pad[0] = it.pad[1] = it.pad[2] = 0;
           a.items[ibase[b] + pos] = it;
         }
       }
@@ -256,7 +278,9 @@ __global__ void pack_kernel(PackArgs a) {
   int m[2] = {0, 0};
   uint32_t base[2] = {0, 0};
   double mean[2] = {0.0, 0.0}, sigma[2] = {1.0, 1.0};
-  const int halves = a.pair ? 2 : 1;
+  const bool packed = it.kind == kItemPair;   // two int16 queries per word
+  const bool codes = it.kind != kItemF32;     // int16 codes (packed, or as floats)
+  const int halves = packed ? 2 : 1;
   for (int h = 0; h < halves; ++h) {
     if (qs[h] >= 0) {
       base[h] = a.offsets[qs[h]];
@@ -293,14 +317,15 @@ __global__ void pack_kernel(PackArgs a) {
           z = x;
         if (!isfinite(z) || fabsf(z) > 1.0e20f) report(a.status, HARU_EINVAL);
       }
-      if (a.pair) {
+      if (packed) {
         // real row: (q, -q); pad row: (-4095, -4095), read by the sweep as distance 0
         const int qv = real ? quantise(z, s) : -4095;
         const int nv = real ? -qv : -4095;
         w0 |= (static_cast<uint32_t>(qv) & 0xffffu) << (16 * h);
         w1 |= (static_cast<uint32_t>(nv) & 0xffffu) << (16 * h);
       } else {
-        w0 = __float_as_uint(z);
+        // FP32: the z-value; exact form: the int16 code as a float; weight 0 on pad rows
+        w0 = __float_as_uint(codes ? (real ? static_cast<float>(quantise(z, s)) : 0.0f) : z);
         w1 = __float_as_uint(real ? 1.0f : 0.0f);
       }
     }

@@ -246,10 +246,20 @@ struct TrackI16 {
 };
 
 // ----------------------------------------------------------------- FP32 --
-template <int S>
+// CODES: the reference words are int16 codes (q | q << 16) and the query
+// samples are int16 codes held as floats: the exact-integer form of the
+// int16 arithmetic, run through the FP32 units (see FormOf below).
+template <int S, bool CODES>
 struct StripF32 {
   float Q[S], W[S], G[2][S], Rr[S];
   float gprev;
+
+  __device__ __forceinline__ static float ref_value(uint32_t w) {
+    if constexpr (CODES)
+      return __int2float_rn(static_cast<int>(static_cast<short>(w & 0xffffu)));
+    else
+      return __uint_as_float(w);
+  }
 
   __device__ __forceinline__ void load(const uint32_t *img, int lane) {
 #pragma unroll
@@ -273,7 +283,7 @@ struct StripF32 {
     for (int k = 0; k < S; ++k) {
       G[1][k] = __uint_as_float(st[k * 32 + lane]);
       G[0][k] = __uint_as_float(st[(S + k) * 32 + lane]);
-      Rr[(1 + k) % S] = __uint_as_float(gref[t - 1 - static_cast<long>(lane) * S - k]);
+      Rr[(1 + k) % S] = ref_value(gref[t - 1 - static_cast<long>(lane) * S - k]);
     }
     const float g = __shfl_up_sync(kFull, G[0][S - 1], 1);
     gprev = lane ? g : 0.0f;
@@ -302,7 +312,7 @@ struct StripF32 {
       const int b = u & 1;
       float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
       float rin = __shfl_up_sync(kFull, Rr[p], 1);
-      const float rv = __uint_as_float(win.get(ref, u));
+      const float rv = ref_value(win.get(ref, u));
       gup = lane ? gup : 0.0f;
       rin = lane ? rin : rv;
       Rr[p] = rin;
@@ -321,12 +331,17 @@ struct StripF32 {
   }
 };
 
+// CAPPED: last-row costs are compared as min(CAP, cost), the saturation of
+// the int16 form, so an exact-integer strip reports what a saturating one
+// would (saturating every cell equals saturating the exact result once).
+template <bool CAPPED>
 struct TrackF32 {
   float best;
   long col;
   __device__ TrackF32() : best(__builtin_huge_valf()), col(-1) {}
   __device__ __forceinline__ void add(uint32_t v, long c) {
-    const float f = __uint_as_float(v);
+    float f = __uint_as_float(v);
+    if constexpr (CAPPED) f = fminf(f, static_cast<float>(kCap));
     if (f < best) { best = f; col = c; }
   }
   __device__ __forceinline__ void reduce() {
@@ -345,18 +360,30 @@ struct TrackF32 {
   }
 };
 
-template <int PREC, int S>
+// Arithmetic forms of a strip: FP32 queries, int16 pairs (DPX), and int16
+// codes computed exactly in FP32. The last two give identical results; an
+// int16 batch runs both side by side so its cells use the half-rate DPX/min
+// pipe and the full-rate FMA pipe at once.
+constexpr int kFormF32 = 0, kFormI16 = 1, kFormExact = 2;
+
+template <int FORM, int S>
 struct FormOf;
 template <int S>
-struct FormOf<HARU_INT16, S> {
+struct FormOf<kFormI16, S> {
   using Strip = StripI16<S>;
   using Track = TrackI16;
   static constexpr bool kMasked = true;
 };
 template <int S>
-struct FormOf<HARU_FP32, S> {
-  using Strip = StripF32<S>;
-  using Track = TrackF32;
+struct FormOf<kFormF32, S> {
+  using Strip = StripF32<S, false>;
+  using Track = TrackF32<false>;
+  static constexpr bool kMasked = false;
+};
+template <int S>
+struct FormOf<kFormExact, S> {
+  using Strip = StripF32<S, true>;
+  using Track = TrackF32<true>;
   static constexpr bool kMasked = false;
 };
 
@@ -434,12 +461,12 @@ struct GlobalTiles {
 // the fresh state at t_start (masked prologue for the int16 form).
 // save_start / save_final: where to store the state before step t_own and
 // before step t_end (nullptr: not stored). Returns false on abort.
-template <int PREC, int S, class Src>
-__device__ bool run_steps(typename FormOf<PREC, S>::Strip &st, typename FormOf<PREC, S>::Track &tr, Src &src,
+template <int FORM, int S, class Src>
+__device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<FORM, S>::Track &tr, Src &src,
                           int TS, long t_start, long t_own, long t_end, bool fresh, long N, uint32_t *save_start,
                           uint32_t *save_final, uint32_t *ring, int lane) {
   constexpr int U = Geo<S>::U, F = Geo<S>::F;
-  constexpr bool kMasked = FormOf<PREC, S>::kMasked;
+  constexpr bool kMasked = FormOf<FORM, S>::kMasked;
   const uint32_t nl = lane != 0 ? 1u : 0u, l0 = 1u - nl;
   const long mask_end = fresh ? t_start + 32L * S : t_start;
   const long k_first = t_start / TS;
@@ -480,11 +507,11 @@ __device__ bool run_steps(typename FormOf<PREC, S>::Strip &st, typename FormOf<P
 }
 
 // Speculative sweep of one unit (item, segment) in the sweep kernel.
-template <int PREC, int S>
+template <int FORM, int S>
 __device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, int item, uint32_t *ring,
                            int lane) {
-  typename FormOf<PREC, S>::Strip st;
-  typename FormOf<PREC, S>::Track tr;
+  typename FormOf<FORM, S>::Strip st;
+  typename FormOf<FORM, S>::Track tr;
   st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
   st.fresh();
   long t_start, t_own, t_end;
@@ -493,9 +520,22 @@ __device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, in
   const size_t unit = static_cast<size_t>(item) * A.nseg_cap + g.seg;
   if (g.seg > 0) ss = A.states + (unit * 2 + 0) * kStateStride;
   if (g.seg + 1 < g.nseg) sf = A.states + (unit * 2 + 1) * kStateStride;
-  const bool ok = run_steps<PREC, S>(st, tr, ts, ts.tile_cols, t_start, t_own, t_end, true, A.N, ss, sf, ring, lane);
+  const bool ok = run_steps<FORM, S>(st, tr, ts, ts.tile_cols, t_start, t_own, t_end, true, A.N, ss, sf, ring, lane);
   tr.reduce();
   if (ok && lane == 0) tr.store(A.bests + unit);
+}
+
+template <int PREC, int S>
+__device__ __forceinline__ void sweep_any(const SdtwArgs &A, TileStream &ts, const Group &g, int item,
+                                          uint32_t *ring, int lane) {
+  if constexpr (PREC == HARU_FP32) {
+    sweep_unit<kFormF32, S>(A, ts, g, item, ring, lane);
+  } else {
+    if (A.items[item].kind == kItemExact)
+      sweep_unit<kFormExact, S>(A, ts, g, item, ring, lane);
+    else
+      sweep_unit<kFormI16, S>(A, ts, g, item, ring, lane);
+  }
 }
 
 // Strip heights of one kernel class: registers are allocated for the
@@ -512,7 +552,7 @@ __device__ __forceinline__ void dispatch_sweep(int s, const SdtwArgs &A, TileStr
                                                uint32_t *ring, int lane) {
   if constexpr (S <= Cls<CLS>::hi) {
     if (s == S)
-      sweep_unit<PREC, S>(A, ts, g, item, ring, lane);
+      sweep_any<PREC, S>(A, ts, g, item, ring, lane);
     else
       dispatch_sweep<PREC, CLS, S + 1>(s, A, ts, g, item, ring, lane);
   }
@@ -583,14 +623,14 @@ __global__ void __launch_bounds__(256, CLS == 0 ? 1 : 2) sdtw_kernel(SdtwArgs A)
 // speculative start state differs from the exact one, combine the segments'
 // last-row minima (smallest cost, then smallest column) and write the
 // outputs.
-template <int PREC, int S>
+template <int FORM, int S>
 __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane) {
   const Item it = A.items[item];
   const int nseg = it.nseg;
   const size_t base = static_cast<size_t>(item) * A.nseg_cap;
   Best b = A.bests[base];
   if (nseg > 1) {
-    typename FormOf<PREC, S>::Strip st;
+    typename FormOf<FORM, S>::Strip st;
     st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
     const int TS = tile_width(S, A.tile_cols);
     for (int s = 1; s < nseg; ++s) {
@@ -602,10 +642,10 @@ __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane
         long t_start, t_own, t_end;
         seg_bounds(S, nseg, s, A.N, &t_start, &t_own, &t_end);
         st.restore(exact, reinterpret_cast<const uint32_t *>(A.ref_img), t_own, lane);
-        typename FormOf<PREC, S>::Track tr;
+        typename FormOf<FORM, S>::Track tr;
         GlobalTiles src{reinterpret_cast<const uint32_t *>(A.ref_img), TS, t_own / TS};
         uint32_t *sf = s + 1 < nseg ? A.states + ((base + s) * 2 + 1) * kStateStride : nullptr;
-        run_steps<PREC, S>(st, tr, src, TS, t_own, t_own, t_end, false, A.N, nullptr, sf, ring, lane);
+        run_steps<FORM, S>(st, tr, src, TS, t_own, t_own, t_end, false, A.N, nullptr, sf, ring, lane);
         tr.reduce();
         if (lane == 0) {
           tr.store(A.bests + base + s);
@@ -614,7 +654,7 @@ __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane
         __syncwarp();
       }
       const Best o = A.bests[base + s];
-      if (PREC == HARU_INT16) {
+      if (FORM == kFormI16) {
         if (o.ia < b.ia) { b.ia = o.ia; b.ca = o.ca; }
         if (o.ib < b.ib) { b.ib = o.ib; b.cb = o.cb; }
       } else {
@@ -623,13 +663,16 @@ __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane
     }
   }
   if (lane == 0) {
-    if (PREC == HARU_INT16) {
+    if (FORM == kFormI16) {
       A.out_cost[it.qa] = static_cast<float>(b.ia) * A.inv_scale;
       A.out_col[it.qa] = b.ca;
       if (it.qb >= 0) {
         A.out_cost[it.qb] = static_cast<float>(b.ib) * A.inv_scale;
         A.out_col[it.qb] = b.cb;
       }
+    } else if (FORM == kFormExact) {
+      A.out_cost[it.qa] = b.f * A.inv_scale;
+      A.out_col[it.qa] = b.ca;
     } else {
       A.out_cost[it.qa] = b.f;
       A.out_col[it.qa] = b.ca;
@@ -637,11 +680,23 @@ __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane
   }
 }
 
+template <int PREC, int S>
+__device__ __forceinline__ void fixup_any(const SdtwArgs &A, int item, uint32_t *ring, int lane) {
+  if constexpr (PREC == HARU_FP32) {
+    fixup_item<kFormF32, S>(A, item, ring, lane);
+  } else {
+    if (A.items[item].kind == kItemExact)
+      fixup_item<kFormExact, S>(A, item, ring, lane);
+    else
+      fixup_item<kFormI16, S>(A, item, ring, lane);
+  }
+}
+
 template <int PREC, int CLS, int S = Cls<CLS>::lo>
 __device__ __forceinline__ void dispatch_fixup(int s, const SdtwArgs &A, int item, uint32_t *ring, int lane) {
   if constexpr (S <= Cls<CLS>::hi) {
     if (s == S)
-      fixup_item<PREC, S>(A, item, ring, lane);
+      fixup_any<PREC, S>(A, item, ring, lane);
     else
       dispatch_fixup<PREC, CLS, S + 1>(s, A, item, ring, lane);
   }

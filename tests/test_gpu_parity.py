@@ -231,3 +231,36 @@ def test_reference_segments_are_exact(haru, sars, units):
     idx = np.arange(0, 300, 37)
     compare_int16(c16, j16, ref, qs.events, qs.offsets, idx=idx)
     compare_fp32(c32, j32, ref, qs.events, qs.offsets, idx=idx)
+
+
+def test_autotuner_keeps_results(haru, sars):
+    _, ref = sars
+    qs = synth.workload("sars_uneven_8192", nq=600).queries
+    with haru.Context() as ctx:
+        ctx.ref_load(ref)
+        before = [ctx.sdtw_batch(p, qs.events, qs.offsets) for p in (haru.HARU_INT16, haru.HARU_FP32)]
+        for i, p in enumerate((haru.HARU_INT16, haru.HARU_FP32)):
+            chosen = ctx.autotune(p, qs.events, qs.offsets)
+            assert chosen["warps_per_cta"] in (4, 8) and chosen["tile_cols"] in (2048, 4096, 8192, 16384)
+            c, j = ctx.sdtw_batch(p, qs.events, qs.offsets)
+            np.testing.assert_array_equal(c, before[i][0])
+            np.testing.assert_array_equal(j, before[i][1])
+
+
+def test_int16_split_over_both_pipes_is_identical(haru, sars):
+    """int16 batches can run two thirds of their warps as exact-integer FP32
+    strips or (default) all as packed DPX pairs; results are bit-identical,
+    with and without reference segments, and equal the int16 oracle."""
+    _, ref = sars
+    qs = synth.workload("sars_uneven_8192", nq=523).queries
+    out = {}
+    for share in (0, 1):
+        for units in (1, 0):
+            with haru.Context(int16_exact_share=share, units_target=units) as ctx:
+                ctx.ref_load(ref)
+                out[(share, units)] = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
+    base = out[(0, 1)]
+    for k, (c, j) in out.items():
+        np.testing.assert_array_equal(c, base[0], err_msg=str(k))
+        np.testing.assert_array_equal(j, base[1], err_msg=str(k))
+    compare_int16(base[0], base[1], ref, qs.events, qs.offsets, idx=np.arange(0, 523, 29))
