@@ -71,16 +71,20 @@ def profiled_traffic(form: str):
     return float(v) if v is not None else None
 
 
-def alu_peak_gcups(sms: int, clock_mhz: float) -> float:
-    """Peak cell rate of the sweep for both forms at the given SM clock.
+def alu_peak_gcups(sms: int, clock_mhz: float, form: str = "int16") -> float:
+    """Peak cell rate of the sweep at the given SM clock, from pipe rates.
 
-    int16: per 2 cells (two packed queries) 3 instructions issue to the
-    half-rate min/DPX pipe (abs via viaddmax, vimin3, viaddmin; the vsub2
-    half of |q - r| issues to another pipe): 64 lane-ops/clk/SM / 1.5 = 42.7
-    cells/clk/SM. FP32: 3 instructions per cell (sub, 3-input min, fma) at
-    one warp-instruction per clock per scheduler: 128 / 3 = 42.7 cells/clk/SM.
+    int16: one packed cell pair takes 4 instructions, 2 on the half-rate
+    min/DPX pipe (|q - r| by viaddmax_relu, vimin3) and 2 on the other
+    half-rate integer pipe (vsub2, and vadd2 on rows that do not saturate;
+    the saturating rows' viaddmin is charged to the first pipe and is left
+    out of this minimum): 2 warp-instructions/clk/SM per pipe and 4
+    issued/clk/SM both give 64 cells/clk/SM. FP32: 3 instructions per cell
+    (sub, 3-input min, fma) at one warp-instruction per clock per scheduler:
+    128 / 3 = 42.7 cells/clk/SM.
     """
-    return sms * (128.0 / 3.0) * clock_mhz * 1e6 / 1e9
+    per_clk = 64.0 if form == "int16" else 128.0 / 3.0
+    return sms * per_clk * clock_mhz * 1e6 / 1e9
 
 
 class ClockSampler:
@@ -272,6 +276,9 @@ def main():
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--nq", type=int, default=0, help="first nq queries only (profiling runs)")
     ap.add_argument("--units", type=int, default=0, help="work units target (0 = library default)")
+    ap.add_argument("--fixed-len", type=int, default=0, help="profiling: every query this many events")
+    ap.add_argument("--single", type=int, default=-1, help="1: one sweep kernel, 0: four class kernels "
+                    "(-1 = library default; the autotuner may change it)")
     ap.add_argument("--forms", default="int16,fp32", help="forms to time: int16, int16exact, fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the library defaults)")
@@ -300,6 +307,9 @@ def main():
     # Weak scaling: every rank aligns its own batch (independent seeds).
     w = synth.workload(args.workload, seed=(101 if args.workload == WORKLOAD else 104) + 1000 * rank)
     q = w.queries if not args.nq else w.queries.subset(np.arange(min(args.nq, w.queries.nq)))
+    if args.fixed_len:
+        g_off = synth.genome(synth.SARS_COV_2_BASES, synth.SEED_GENOME_OFF)
+        q = synth.make_queries(np.full(q.nq, args.fixed_len), 0.5, 777, w.genome, g_off, w.model, w.k)
     cfg = haru.default_config()
     if args.tile:
         cfg.tile_cols = args.tile
@@ -307,6 +317,8 @@ def main():
         cfg.warps_per_cta = args.warps
     if args.units:
         cfg.units_target = args.units
+    if args.single >= 0:
+        cfg.single_kernel = args.single
     ctx = haru.Context(local, config=cfg)
     ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
     N = ctx.ref_length
@@ -317,7 +329,12 @@ def main():
     col_d = torch.empty(q.nq, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    launches_per_step = 3  # planner, pack, sweep
+    launches = []  # own kernels per timed step of each form
+
+    def kernels_per_step():
+        # planner, query statistics (raw events), pack, then a sweep and a
+        # segment fix-up kernel per strip-height class
+        return 3 + 2 * (1 if ctx.configure().single_kernel else 4)
 
     tuned = {}
 
@@ -342,6 +359,7 @@ def main():
             except Exception as e:  # capture unsupported: direct launches
                 print(f"graph capture failed ({e}); timing direct launches", file=sys.stderr)
                 graph = None
+        launches.append(kernels_per_step() * args.steps)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
 
@@ -432,7 +450,8 @@ def main():
     sms = props.multi_processor_count
     pk = peaks_file()
     max_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak = alu_peak_gcups(sms, max_mhz)
+    peak = alu_peak_gcups(sms, max_mhz, "int16")
+    peak32 = alu_peak_gcups(sms, max_mhz, "fp32")
     ach16 = cells / (sweep16 / 1e3) / 1e9
     ach32 = cells / (sweep32 / 1e3) / 1e9
     result = {
@@ -450,17 +469,18 @@ def main():
                      "unit": "GCUPS", "frac": ach16 / peak, "traffic": profiled_traffic("int16"),
                      "traffic_unit": "bytes per batch (DRAM read+write, ncu at the default launch shape, "
                                      "profiles/sdtw_sweep_sars_uneven_8192.md)",
-                     "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (half-rate DPX pipe, 1.5 ops/cell) x "
-                                   f"{max_mhz:.0f} MHz max SM clock",
-                     "frac_at_sampled_clock": (ach16 / alu_peak_gcups(sms, clocks["sm_mhz"]))
+                     "peak_basis": f"{sms} SMs x 64 cells/clk/SM (4 instructions per packed cell pair, 2 on "
+                                   f"each half-rate integer pipe) x {max_mhz:.0f} MHz max SM clock",
+                     "frac_at_sampled_clock": (ach16 / alu_peak_gcups(sms, clocks["sm_mhz"], "int16"))
                      if clocks.get("sm_mhz") else None,
                      "peak_probe": probe16, "frac_of_probe": ach16 / probe16,
                      "peak_probe_basis": "haru_probe_peak: the int16 cell-pair instructions on independent "
                                          "chains, no shuffles/reference/tracking, same run"},
         "fp32": {"value": value32, "unit": "GCUPS", "ms_per_step": ms32, "dtype": "f32",
-                 "roofline": {"bound": "alu", "kernel": "sdtw_kernel<FP32>", "achieved": ach32, "peak": peak,
-                              "unit": "GCUPS", "frac": ach32 / peak, "traffic": profiled_traffic("fp32"),
-                              "peak_basis": "3 issue slots per cell (sub, 3-input min, fma) at 4 warp-instr/clk/SM",
+                 "roofline": {"bound": "alu", "kernel": "sdtw_kernel<FP32>", "achieved": ach32, "peak": peak32,
+                              "unit": "GCUPS", "frac": ach32 / peak32, "traffic": profiled_traffic("fp32"),
+                              "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (3 issue slots per cell: sub, "
+                                            f"3-input min, fma at 4 warp-instr/clk/SM) x {max_mhz:.0f} MHz",
                               "peak_probe": probe32, "frac_of_probe": ach32 / probe32},
                  "clocks": clocks32},
         "int16_exact_share": ({"value": total_cells / (msdpx / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": msdpx,
@@ -473,7 +493,7 @@ def main():
                 "h2d_bytes_per_step": int(q.events.nbytes + q.offsets.nbytes),
                 "d2h_bytes_per_step": int(q.nq * (4 + 8))},
         "clocks": clocks,
-        "gpu_launches": launches_per_step * args.steps * len(forms),
+        "gpu_launches": int(sum(launches)),
     }
     if args.serve_seconds > 0 and args.workload == WORKLOAD:
         held = synth.workload("sars_heldout_1024", seed=103)

@@ -79,6 +79,9 @@ typedef struct {
   uint32_t serve_prefix;    /* events per decision prefix; 0 = 250 (Section 4.1) */
   int units_target;         /* work units (query x reference segment) a batch is cut into, at least;
                                0 = 4 x SMs x warps_per_cta; 1 = never split the reference */
+  int single_kernel;        /* 1 (default): one sweep kernel covers every strip height with one
+                               longest-first queue; 0: four kernels by strip height run side by side,
+                               each with registers sized for its tallest strip */
   int int16_exact_share;    /* int16 batches: 0 (default) = every warp runs packed DPX query pairs;
                                1 = two of every three warps compute their query exactly on the int16
                                codes in FP32 instead (identical results: saturating every cell equals
@@ -250,8 +253,9 @@ int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, c
 
 /* Autotuner: run the batch path on this batch (layout and flags as in
  * haru_sdtw_batch; HARU_ON_DEVICE and HARU_RAW are honoured) under every
- * combination of warps per CTA {4, 8}, tile width {2048, 4096, 8192, 16384}
- * and work-unit target {1 (no reference segments), auto, 2 x auto}, keep the
+ * combination of warps per CTA {4, 8}, tile width {2048, 4096, 8192, 16384},
+ * work-unit target {1 (no reference segments), auto, 2 x auto} and one or
+ * four sweep kernels, keep the
  * fastest (minimum of two timed runs each) in the context's configuration
  * for later batches, and copy the resulting configuration to *chosen (may be
  * NULL). The strip height is fixed by each query's length. Results of the

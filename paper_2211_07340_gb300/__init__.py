@@ -58,6 +58,7 @@ class haru_config(ctypes.Structure):
         ("serve_max_batch", ctypes.c_uint32),
         ("serve_prefix", ctypes.c_uint32),
         ("units_target", ctypes.c_int),
+        ("single_kernel", ctypes.c_int),
         ("int16_exact_share", ctypes.c_int),
     ]
 
@@ -296,7 +297,8 @@ class Context:
         check(lib().haru_autotune(self._h, int(precision), _ptr(events), _ptr(offsets), nq, flags,
                                   ctypes.byref(cfg)), "haru_autotune")
         self.config = cfg
-        return {"warps_per_cta": cfg.warps_per_cta, "tile_cols": cfg.tile_cols, "units_target": cfg.units_target}
+        return {"warps_per_cta": cfg.warps_per_cta, "tile_cols": cfg.tile_cols, "units_target": cfg.units_target,
+                "single_kernel": cfg.single_kernel}
 
     def probe_peak(self, precision: int) -> float:
         """Measured cells/s ceiling of the form's cell update (no data movement)."""

@@ -57,6 +57,7 @@ haru::LaunchCfg haru_ctx::launch_cfg() const {
   lc.sms = sms;
   lc.units_target = cfg.units_target;
   lc.int16_mode = cfg.int16_exact_share ? 2 : 1;
+  lc.single_kernel = cfg.single_kernel ? 1 : 0;
   lc.wait_ns = wait_ns(cfg);
   return lc;
 }
@@ -109,6 +110,7 @@ int haru_config_default(haru_config *cfg) {
   cfg->serve_budget_bytes = 64u << 20;
   cfg->serve_max_batch = 1024;
   cfg->serve_prefix = 250;
+  cfg->single_kernel = 1;
   return HARU_OK;
 }
 

@@ -18,7 +18,7 @@ cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
 }
 
 void ws_free(Workspace &ws) {
-  void *p[] = {ws.ints, ws.items, ws.groups, ws.img, ws.states, ws.bests};
+  void *p[] = {ws.ints, ws.items, ws.groups, ws.img, ws.states, ws.bests, ws.qstats};
   for (void *q : p)
     if (q) cudaFree(q);
   ws = Workspace();
@@ -52,7 +52,8 @@ cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCf
     ws.cap_items = max_items;
   }
   const size_t units = max_items * static_cast<size_t>(nseg_cap);
-  if ((e = grow(&ws.bests, &ws.cap_bests, units)) != cudaSuccess) return e;
+  if ((e = grow(&ws.bests, &ws.cap_bests, 2 * units)) != cudaSuccess) return e;
+  if ((e = grow(&ws.qstats, &ws.cap_qstats, 2 * static_cast<size_t>(nq))) != cudaSuccess) return e;
   if (nseg_cap > 1 && (e = grow(&ws.states, &ws.cap_states, units * 2 * kStateStride)) != cudaSuccess) return e;
   ws.max_items = max_items;
   ws.nseg_cap = nseg_cap;
@@ -74,11 +75,14 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   pa.pair = plan_mode(precision, lc);
   pa.warps = lc.warps;
   pa.units_target = ws.units_target;
+  pa.single = lc.single_kernel ? 1 : 0;
   pa.nseg_cap = ws.nseg_cap;
   pa.items = ws.items;
   pa.groups = ws.groups;
   pa.ints = ws.ints;
   if ((e = launch_plan(pa, s)) != cudaSuccess) return e;
+  if (raw && (e = launch_qstats(d_events, d_offsets, nq, ws.qstats, ws.ints + kIntStatus, s)) != cudaSuccess)
+    return e;
 
   PackArgs ka;
   ka.events = d_events;
@@ -87,6 +91,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   ka.n_items = ws.ints + kIntItems;
   ka.img = ws.img;
   ka.raw = raw;
+  ka.qstats = ws.qstats;
   ka.pair = pa.pair;
   ka.scale_log2 = ref.scale_log2;
   ka.status = ws.ints + kIntStatus;
@@ -101,6 +106,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   sa.ints = ws.ints;
   sa.states = ws.states;
   sa.bests = ws.bests;
+  sa.bests2 = ws.bests + ws.max_items * static_cast<size_t>(ws.nseg_cap);
   sa.nseg_cap = ws.nseg_cap;
   sa.out_cost = d_cost;
   sa.out_col = d_col;
@@ -114,6 +120,12 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   // streams are given, else one after the other on s; each is persistent
   // over its own part of the group list, then verifies its segments and
   // writes its queries' results.
+  if (lc.single_kernel) {
+    int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, kClassAll, lc.tile, lc.warps);
+    if (per_sm < 1) per_sm = 1;
+    const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
+    return launch_sdtw(precision, kClassAll, sa, grid, static_cast<int>(ws.max_items), s);
+  }
   if (fj && fj->ok() && (e = cudaEventRecord(fj->fork, s)) != cudaSuccess) return e;
   for (int c = 0; c < kClasses; ++c) {
     int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, c, lc.tile, lc.warps);

@@ -38,6 +38,7 @@ struct LaunchCfg {
   int sms = 1;
   int units_target = 0;  // 0: 4 x sms x warps
   int int16_mode = 1;    // int16 batches: 1 = DPX pairs only, 2 = pairs and exact-FP32 strips (1:2 warps)
+  int single_kernel = 0; // 1: one sweep kernel for every strip height instead of four class kernels
   unsigned long long wait_ns = 2000000000ull;
 };
 
@@ -46,10 +47,11 @@ inline int plan_mode(int precision, const LaunchCfg &lc) {
   return precision == HARU_INT16 ? (lc.int16_mode == 1 ? 1 : 2) : 0;
 }
 
-// Most items a batch of nq queries can make in `mode` (per-bucket rounding included).
+// Most items a batch of nq queries can make in `mode` (per-bucket rounding
+// included: each strip height has a plain and a stacked bucket).
 inline size_t items_bound(int mode, size_t nq) {
-  if (mode == 0) return nq;
-  if (mode == 1) return (nq + 1) / 2 + kMaxS;
+  if (mode == 0) return nq + kMaxS;
+  if (mode == 1) return (nq + 1) / 2 + 2 * kMaxS;
   return (3 * nq + 3) / 4 + 2 * kMaxS;
 }
 
@@ -71,8 +73,10 @@ struct Workspace {
   size_t cap_items = 0;
   uint32_t *states = nullptr;
   size_t cap_states = 0;
-  Best *bests = nullptr;
+  Best *bests = nullptr;  // 2 x units: upper stacks, then lower stacks
   size_t cap_bests = 0;
+  double *qstats = nullptr;  // per query (mean, sigma) of raw batches
+  size_t cap_qstats = 0;
   // plan of the last reservation
   size_t max_items = 0;
   int nseg_cap = 1;

@@ -15,14 +15,24 @@ namespace haru {
 // batch computed exactly on integer codes in FP32 (INT16 exact). qb < 0 when
 // a pair is short. Its steps are cut into nseg segments (work units).
 constexpr int kItemF32 = 0, kItemPair = 1, kItemExact = 2;
+// A stacked item holds two strips one above the other in the warp's PE
+// chain: lanes 0..15 sweep qa (and qb, INT16), lanes 16..31 sweep qc (and
+// qd), each 16 * S rows high; lane 16 starts its stack from the free-start
+// row instead of lane 15's last row.
 struct Item {
   int qa;
   int qb;
-  int S;     // rows per lane of the warp strip: 32 * S >= longest query of the item
-  int nseg;  // segments of its sweep
-  int kind;  // kItemF32, kItemPair or kItemExact
-  int pad[3];
+  int S;        // rows per lane of the warp strip: 32 * S (16 * S if stacked) >= longest query
+  int nseg;     // segments of its sweep
+  int kind;     // kItemF32, kItemPair or kItemExact
+  int qc;       // stacked: lower stack's queries (-1: none)
+  int qd;
+  int stacked;  // 1: two stacks of 16 lanes
 };
+
+// Queries of at most this many events are stacked two to a warp strip
+// (planner modes 0 and 1).
+constexpr int kStackMax = 16 * 16;
 
 // Consecutive items with the same S swept over the same segment by one CTA,
 // sharing one stream of reference tiles.
@@ -58,8 +68,10 @@ constexpr int kCap = HARU_INT16_CAP;
 constexpr int kMaxTile = 16384;
 constexpr long kRefPad = 32 * kMaxS + kMaxTile + 64;
 
-// Strip-height classes, tallest first: S in 13..16, 9..12, 5..8, 1..4.
+// Strip-height classes, tallest first: S in 13..16, 9..12, 5..8, 1..4; kernel
+// class 4 covers 1..16 in one kernel (single queue, planned into slot 0).
 constexpr int kClasses = 4;
+constexpr int kClassAll = 4;
 
 // Layout of the small integer block every batch uses (status and counters).
 constexpr int kIntStatus = 0, kIntGroups = 1, kIntItems = 2, kIntFixups = 3, kIntQueues = 4, kIntClassFirst = 8,
@@ -107,7 +119,8 @@ struct SdtwArgs {
   const Group *groups;
   int *ints;               // kIntWords status and counter words
   uint32_t *states;        // [item][nseg_cap][2] saved states (start, final), kStateStride words each
-  Best *bests;             // [item][nseg_cap]
+  Best *bests;             // [item][nseg_cap]: the strip's (upper stack's) last-row minimum
+  Best *bests2;            // [item][nseg_cap]: the lower stack's, for stacked items
   int nseg_cap;
   float *out_cost;
   int64_t *out_col;
@@ -125,6 +138,7 @@ struct PlanArgs {
   int pair;                 // 0: FP32 singles; 1: INT16 pairs; 2: INT16 pairs and exact-FP32 singles (1:2 warps)
   int warps;                // items per group
   int units_target;         // wanted work units (item x segment) in the batch
+  int single;               // 1: every strip height in slot 0 (one kernel, one queue)
   int nseg_cap;             // most segments per item (state storage is sized for it)
   Item *items;
   Group *groups;
@@ -138,6 +152,7 @@ struct PackArgs {
   const int *n_items;
   uint32_t *img;
   int raw;                  // z-score each query first
+  const double *qstats;     // raw: (mean, sigma) of query q at 2q, 2q+1 (launch_qstats)
   int pair;
   int scale_log2;
   int *status;
@@ -146,6 +161,9 @@ struct PackArgs {
 // Kernel launchers (stream-ordered, no synchronisation).
 cudaError_t launch_plan(const PlanArgs &a, cudaStream_t s);
 cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s);
+// Mean and population sigma (FP64, sequential order) of each query of 1..512 events.
+cudaError_t launch_qstats(const float *events, const uint32_t *offsets, uint32_t nq, double *qstats, int *status,
+                          cudaStream_t s);
 cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s);
 size_t sdtw_smem_bytes(int tile_cols, int warps);
 int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps);

@@ -23,17 +23,19 @@ namespace haru {
 namespace {
 
 // Layout of the scratch array (bytes): the status and counter words, then
-// items, groups, per-item last-row minima and the per-item register images
+// items, groups, per-item last-row minima (upper and lower stacks), the per-item register images
 // for up to HARU_NOALLOC_MAX_QUERIES queries (the FP32 form needs one item
-// per query, the int16 form one per pair). This path never splits the
-// reference into segments, so it needs no saved states.
-constexpr size_t kNaItems = HARU_NOALLOC_MAX_QUERIES + kMaxS;
+// per query, the int16 form one per pair) and each query's mean and sigma
+// (raw events). This path never splits the reference into segments, so it
+// needs no saved states.
+constexpr size_t kNaItems = HARU_NOALLOC_MAX_QUERIES + kMaxS;  // items_bound(0, max), >= items_bound(1, max)
 constexpr size_t kNaHead = 256;  // kIntWords status and counter words
 constexpr size_t kNaItemsOff = kNaHead;
 constexpr size_t kNaGroupsOff = kNaItemsOff + ((kNaItems * sizeof(Item) + 255) / 256) * 256;
 constexpr size_t kNaBestsOff = kNaGroupsOff + ((kNaItems * sizeof(Group) + 255) / 256) * 256;
-constexpr size_t kNaImgOff = kNaBestsOff + ((kNaItems * sizeof(Best) + 255) / 256) * 256;
-constexpr size_t kNaBytes = kNaImgOff + kNaItems * kImgStride * sizeof(uint32_t);
+constexpr size_t kNaImgOff = kNaBestsOff + ((2 * kNaItems * sizeof(Best) + 255) / 256) * 256;
+constexpr size_t kNaStatsOff = kNaImgOff + ((kNaItems * kImgStride * sizeof(uint32_t) + 255) / 256) * 256;
+constexpr size_t kNaBytes = kNaStatsOff + 2 * HARU_NOALLOC_MAX_QUERIES * sizeof(double);
 
 static __device__ __align__(256) unsigned char scratch[kNaBytes];
 
@@ -90,7 +92,8 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   Group *groups = reinterpret_cast<Group *>(base + kNaGroupsOff);
   Best *bests = reinterpret_cast<Best *>(base + kNaBestsOff);
   uint32_t *imgs = reinterpret_cast<uint32_t *>(base + kNaImgOff);
-  const size_t max_items = precision == HARU_INT16 ? (static_cast<size_t>(nq) + 1) / 2 + kMaxS : nq;
+  double *qstats = reinterpret_cast<double *>(base + kNaStatsOff);
+  const size_t max_items = items_bound(precision == HARU_INT16 ? 1 : 0, nq);
 
   // The array keeps the previous call's contents: the status word and the
   // counters must start at zero; items, groups and images are rewritten.
@@ -102,11 +105,14 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   pa.pair = precision == HARU_INT16;
   pa.warps = warps;
   pa.units_target = 1;
+  pa.single = 0;
   pa.nseg_cap = 1;
   pa.items = items;
   pa.groups = groups;
   pa.ints = status;
   if (launch_plan(pa, s) != cudaSuccess) return HARU_ECUDA;
+  if ((flags & HARU_RAW) && launch_qstats(events, offsets, nq, qstats, status + kIntStatus, s) != cudaSuccess)
+    return HARU_ECUDA;
   PackArgs ka;
   ka.events = events;
   ka.offsets = offsets;
@@ -114,6 +120,7 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   ka.n_items = status + kIntItems;
   ka.img = imgs;
   ka.raw = (flags & HARU_RAW) ? 1 : 0;
+  ka.qstats = qstats;
   ka.pair = pa.pair;
   ka.scale_log2 = scale;
   ka.status = status + kIntStatus;
@@ -127,6 +134,7 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   sa.ints = status;
   sa.states = nullptr;
   sa.bests = bests;
+  sa.bests2 = bests + kNaItems;
   sa.nseg_cap = 1;
   sa.out_cost = out_cost;
   sa.out_col = out_col;

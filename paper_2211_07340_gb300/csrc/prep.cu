@@ -106,19 +106,23 @@ __global__ void ref_finish_kernel(const float *x, size_t n, const double *stats,
 // --------------------------------------------------------------- planner --
 __device__ __forceinline__ int sdtw_class_dev(int S) { return S >= 13 ? 0 : (S >= 9 ? 1 : (S >= 5 ? 2 : 3)); }
 
-__device__ __forceinline__ int strip_rows(const uint32_t *off, uint32_t q, long N, int *status) {
+// Bucket key of query q: its strip height S (rows per lane), plus kMaxS + 1
+// if it is stacked (16 lanes, S = ceil(M / 16)); 0 for an invalid length.
+__device__ __forceinline__ int bucket_key(const uint32_t *off, uint32_t q, long N, int mode, int *status) {
   const uint32_t m = off[q + 1] - off[q];
   const long lim = N < HARU_MAX_QUERY ? N : HARU_MAX_QUERY;
   if (m < 1 || static_cast<long>(m) > lim) {
-    report(status, HARU_EINVAL);
+    if (status) report(status, HARU_EINVAL);
     return 0;
   }
+  if (mode != 2 && m <= static_cast<uint32_t>(kStackMax)) return static_cast<int>((m + 15) / 16) + kMaxS + 1;
   return static_cast<int>((m + 31) / 32);
 }
 
 // Items of a bucket of n queries. Mode 2 (int16 split over both pipes)
 // repeats the pattern [pair, exact, exact] over runs of four queries, so a
 // group's warps mix the DPX pairs and the exact-FP32 singles 1:2.
+__device__ __forceinline__ int stacked_items(int mode, int n) { return mode == 0 ? (n + 1) / 2 : (n + 3) / 4; }
 __device__ __forceinline__ int bucket_items(int mode, int n) {
   if (mode == 0) return n;
   if (mode == 1) return (n + 1) / 2;
@@ -131,22 +135,44 @@ __device__ __forceinline__ int bucket_items(int mode, int n) {
 // input order inside a bucket, pairs neighbours for the int16 form, and cuts
 // each bucket into groups of `warps` items.
 __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
-  __shared__ int cnt[kMaxS + 1], run[kMaxS + 1], ibase[kMaxS + 1], icount[kMaxS + 1], nseg_of[kMaxS + 1];
-  __shared__ int wpre[32], wtot;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kKeys = 2 * (kMaxS + 1);  // plain and stacked buckets of each S
+  __shared__ int cnt[kKeys], ibase[kMaxS + 1], sbase[kMaxS + 1], icount[kMaxS + 1], nseg_of[kMaxS + 1];
+  __shared__ int gbase[kMaxS + 1], gcount[kMaxS + 1];
+  __shared__ int wrun[32][kKeys];  // per warp and bucket: count, then next position
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   int *status = a.ints + kIntStatus;
-  if (tid <= kMaxS) { cnt[tid] = 0; run[tid] = 0; }
+  // Each warp owns a contiguous range of queries, so bucket positions
+  // (earlier warps first, then the order inside the warp) keep input order.
+  const uint32_t per_warp = (a.nq + nw - 1) / nw;
+  const uint32_t q_lo = min(a.nq, static_cast<uint32_t>(warp) * per_warp);
+  const uint32_t q_hi = min(a.nq, q_lo + per_warp);
+  for (int b = lane; b < kKeys; b += 32) wrun[warp][b] = 0;
+  __syncwarp();
+  for (uint32_t q0 = q_lo; q0 < q_hi; q0 += 32) {
+    const uint32_t q = q0 + lane;
+    const int key = q < q_hi ? bucket_key(a.offsets, q, a.N, a.pair, status) : 0;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key && lane == __ffs(peers) - 1) wrun[warp][key] += __popc(peers);
+    __syncwarp();
+  }
   __syncthreads();
-  for (uint32_t q = tid; q < a.nq; q += blockDim.x) {
-    const int S = strip_rows(a.offsets, q, a.N, status);
-    if (S) atomicAdd(&cnt[S], 1);
+  if (tid >= 1 && tid < kKeys) {
+    int c = 0;
+    for (int w = 0; w < nw; ++w) {
+      const int t = wrun[w][tid];
+      wrun[w][tid] = c;
+      c += t;
+    }
+    cnt[tid] = c;
   }
   __syncthreads();
   if (tid == 0) {
     int base = 0;
-    for (int S = kMaxS; S >= 1; --S) {
-      icount[S] = bucket_items(a.pair, cnt[S]);
+    for (int S = kMaxS; S >= 1; --S) {  // plain items of height S, then stacked ones
+      const int plain = bucket_items(a.pair, cnt[S]);
+      icount[S] = plain + stacked_items(a.pair, cnt[S + kMaxS + 1]);
       ibase[S] = base;
+      sbase[S] = base + plain;
       base += icount[S];
     }
     a.ints[kIntItems] = base;
@@ -161,24 +187,16 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
       a.ints[kIntQueues + c] = 0;
       int ifirst = -1, icnt = 0;
       for (int S = kMaxS; S >= 1; --S) {
-        if (sdtw_class_dev(S) != c) continue;
+        if ((a.single ? 0 : sdtw_class_dev(S)) != c) continue;
         if (icount[S] > 0 && ifirst < 0) ifirst = ibase[S];
         icnt += icount[S];
         const long minlen = 4 * warmup_steps(S) > 2048 ? 4 * warmup_steps(S) : 2048;
         long lim = sweep_steps(S, a.N) / minlen;
         if (lim < 1) lim = 1;
         nseg_of[S] = want < lim ? want : static_cast<int>(lim);
-        for (int seg = 0; seg < nseg_of[S]; ++seg)
-          for (int f = 0; f < icount[S]; f += a.warps) {
-            Group gr;
-            gr.S = S;
-            gr.first = ibase[S] + f;
-            gr.count = icount[S] - f < a.warps ? icount[S] - f : a.warps;
-            gr.seg = seg;
-            gr.nseg = nseg_of[S];
-            gr.pad[0] = gr.pad[1] = gr.pad[2] = 0;
-            a.groups[g++] = gr;
-          }
+        gbase[S] = g;
+        gcount[S] = nseg_of[S] * ((icount[S] + a.warps - 1) / a.warps);
+        g += gcount[S];
       }
       a.ints[kIntClassCount + c] = g - a.ints[kIntClassFirst + c];
       a.ints[kIntClassItemFirst + c] = ifirst < 0 ? 0 : ifirst;
@@ -187,94 +205,140 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     a.ints[kIntGroups] = g;
   }
   __syncthreads();
+  // Groups of each bucket, segment-major: (seg, first item), in parallel.
+  for (int S = kMaxS; S >= 1; --S) {
+    const int per_seg = (icount[S] + a.warps - 1) / a.warps;
+    for (int j = tid; j < gcount[S]; j += blockDim.x) {
+      const int seg = j / per_seg, f = (j % per_seg) * a.warps;
+      Group gr;
+      gr.S = S;
+      gr.first = ibase[S] + f;
+      gr.count = icount[S] - f < a.warps ? icount[S] - f : a.warps;
+      gr.seg = seg;
+      gr.nseg = nseg_of[S];
+      gr.pad[0] = gr.pad[1] = gr.pad[2] = 0;
+      a.groups[gbase[S] + j] = gr;
+    }
+  }
+  __syncthreads();
   const int n_items = a.ints[kIntItems];
   for (int i = tid; i < n_items; i += blockDim.x) {
     Item it;
     it.qa = -1; it.qb = -1; it.S = 0; it.nseg = 1;
     it.kind = a.pair == 0 ? kItemF32 : kItemPair;
-    it.pad[0] = it.pad[1] = it.pad[2] = 0;
+    it.qc = -1; it.qd = -1; it.stacked = 0;
     a.items[i] = it;
   }
   __syncthreads();
   const unsigned lt = (1u << lane) - 1u;
-  for (uint32_t r0 = 0; r0 < a.nq; r0 += blockDim.x) {
-    const uint32_t q = r0 + tid;
-    int S = 0;
-    if (q < a.nq) {
-      const uint32_t m = a.offsets[q + 1] - a.offsets[q];
-      const long lim = a.N < HARU_MAX_QUERY ? a.N : HARU_MAX_QUERY;
-      if (m >= 1 && static_cast<long>(m) <= lim) S = static_cast<int>((m + 31) / 32);
-    }
-    for (int b = kMaxS; b >= 1; --b) {
-      const bool pred = (S == b);
-      const unsigned mask = __ballot_sync(0xffffffffu, pred);
-      if (lane == 0) wpre[warp] = __popc(mask);
-      __syncthreads();
-      if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        int v = lane < nw ? wpre[lane] : 0;
-        int incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          int t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
-        }
-        if (lane < nw) wpre[lane] = incl - v;
-        if (lane == 31) wtot = incl;
-      }
-      __syncthreads();
-      if (pred) {
-        const int pos = run[b] + wpre[warp] + __popc(mask & lt);
-        if (a.pair == 1) {
-          Item *it = &a.items[ibase[b] + pos / 2];
-          if (pos % 2 == 0) { it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b]; }
-          else it->qb = static_cast<int>(q);
-        } else if (a.pair == 2) {
-          const int w = pos % 4;
-          Item *it = &a.items[ibase[b] + 3 * (pos / 4) + (w < 2 ? 0 : w - 1)];
-          if (w == 1) {
-            it->qb = static_cast<int>(q);
-          } else {
-            it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b];
-            it->kind = w == 0 ? kItemPair : kItemExact;
-          }
+  for (uint32_t q0 = q_lo; q0 < q_hi; q0 += 32) {
+    const uint32_t q = q0 + lane;
+    const int key = q < q_hi ? bucket_key(a.offsets, q, a.N, a.pair, nullptr) : 0;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key > kMaxS) {  // stacked: slots qa, qb | qc, qd (INT16) or qa | qc (FP32)
+      const int b = key - kMaxS - 1;
+      const int pos = wrun[warp][key] + __popc(peers & lt);
+      const int per = a.pair == 0 ? 2 : 4;
+      const int slot = a.pair == 0 ? 2 * (pos % 2) : pos % 4;
+      Item *it = &a.items[sbase[b] + pos / per];
+      if (slot == 0) { it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b]; it->stacked = 1; }
+      else if (slot == 1) it->qb = static_cast<int>(q);
+      else if (slot == 2) it->qc = static_cast<int>(q);
+      else it->qd = static_cast<int>(q);
+    } else if (key) {
+      const int b = key;
+      const int pos = wrun[warp][b] + __popc(peers & lt);  // position in bucket b
+      if (a.pair == 1) {
+        Item *it = &a.items[ibase[b] + pos / 2];
+        if (pos % 2 == 0) { it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b]; }
+        else it->qb = static_cast<int>(q);
+      } else if (a.pair == 2) {
+        const int w = pos % 4;
+        Item *it = &a.items[ibase[b] + 3 * (pos / 4) + (w < 2 ? 0 : w - 1)];
+        if (w == 1) {
+          it->qb = static_cast<int>(q);
         } else {
-          Item it;
-          it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b]; it.kind = kItemF32;
-          it.pad[0] = it.pad[1] = it.pad[2] = 0;
-          a.items[ibase[b] + pos] = it;
+          it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b];
+          it->kind = w == 0 ? kItemPair : kItemExact;
         }
+      } else {
+        Item it;
+        it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b]; it.kind = kItemF32;
+        it.qc = -1; it.qd = -1; it.stacked = 0;
+        a.items[ibase[b] + pos] = it;
       }
-      __syncthreads();
-      if (tid == 0) run[b] += wtot;
-      __syncthreads();
     }
+    __syncwarp();
+    if (key && lane == __ffs(peers) - 1) wrun[warp][key] += __popc(peers);
+    __syncwarp();
   }
 }
 
 // ----------------------------------------------------------------- pack --
 // Mean and sigma of one query, sequentially (a query is shorter than one
 // z-score block, so this is the blocked rule's order).
+// Loads are issued eight at a time ahead of the (sequential) additions.
 __device__ void query_stats(const float *x, int m, double &mean, double &sigma) {
+  constexpr int B = 8;
+  float v[B];
   double acc = 0.0;
-  for (int i = 0; i < m; ++i) acc = __dadd_rn(acc, static_cast<double>(x[i]));
+  int i = 0;
+  for (; i + B <= m; i += B) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = __ldg(x + i + j);
+#pragma unroll
+    for (int j = 0; j < B; ++j) acc = __dadd_rn(acc, static_cast<double>(v[j]));
+  }
+  for (; i < m; ++i) acc = __dadd_rn(acc, static_cast<double>(__ldg(x + i)));
   mean = __ddiv_rn(acc, static_cast<double>(m));
   double ss = 0.0;
-  for (int i = 0; i < m; ++i) {
-    const double d = __dsub_rn(static_cast<double>(x[i]), mean);
+  i = 0;
+  for (; i + B <= m; i += B) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) v[j] = __ldg(x + i + j);
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const double d = __dsub_rn(static_cast<double>(v[j]), mean);
+      ss = __dadd_rn(ss, __dmul_rn(d, d));
+    }
+  }
+  for (; i < m; ++i) {
+    const double d = __dsub_rn(static_cast<double>(__ldg(x + i)), mean);
     ss = __dadd_rn(ss, __dmul_rn(d, d));
   }
   sigma = __dsqrt_rn(__ddiv_rn(ss, static_cast<double>(m)));
 }
 
-// One warp per item: lane l writes rows l*S .. l*S+S-1 of both halves.
+// One thread per query: its mean and sigma (the sums are sequential chains,
+// so a query gets a thread of its own rather than a lane of a packing warp).
+__global__ void qstats_kernel(const float *events, const uint32_t *offsets, uint32_t nq, double *qstats,
+                              int *status) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const uint32_t b = offsets[q];
+  const uint32_t m = offsets[q + 1] - b;
+  double mu = 0.0, sg = 1.0;
+  if (m >= 1 && m <= HARU_MAX_QUERY) {  // other lengths are rejected by the planner
+    query_stats(events + b, static_cast<int>(m), mu, sg);
+    if (!(sg > 0.0) || !isfinite(sg) || !isfinite(mu)) report(status, HARU_EINVAL);
+  }
+  qstats[2 * static_cast<size_t>(q)] = mu;
+  qstats[2 * static_cast<size_t>(q) + 1] = sg;
+}
+
+// One warp per item: lane l writes rows l*S .. l*S+S-1 of both halves (of
+// its own stack, for stacked items).
 __global__ void pack_kernel(PackArgs a) {
   const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (item >= *a.n_items) return;
   const Item it = a.items[item];
   const int S = it.S;
-  const int qs[2] = {it.qa, it.qb};
+  // Stacked items: lanes 16..31 hold the lower stack (qc, qd).
+  const bool low = it.stacked && lane >= 16;
+  const int qs[2] = {low ? it.qc : it.qa, low ? it.qd : it.qb};
+  const int H = it.stacked ? 16 * S : 32 * S;             // rows of this lane's stack
+  const int lane_in = it.stacked ? (lane & 15) : lane;   // lane within the stack
   int m[2] = {0, 0};
   uint32_t base[2] = {0, 0};
   double mean[2] = {0.0, 0.0}, sigma[2] = {1.0, 1.0};
@@ -288,25 +352,20 @@ __global__ void pack_kernel(PackArgs a) {
     }
   }
   if (a.raw) {
-    double mu = 0.0, sg = 1.0;
-    const int mh = lane == 0 ? m[0] : m[1];
-    const uint32_t bh = lane == 0 ? base[0] : base[1];
-    if (lane < halves && mh > 0) {
-      query_stats(a.events + bh, mh, mu, sg);
-      if (!(sg > 0.0) || !isfinite(sg) || !isfinite(mu)) report(a.status, HARU_EINVAL);
-    }
     for (int h = 0; h < halves; ++h) {
-      mean[h] = __shfl_sync(0xffffffffu, mu, h);
-      sigma[h] = __shfl_sync(0xffffffffu, sg, h);
+      if (qs[h] >= 0) {
+        mean[h] = a.qstats[2 * static_cast<size_t>(qs[h])];
+        sigma[h] = a.qstats[2 * static_cast<size_t>(qs[h]) + 1];
+      }
     }
   }
   const float s = static_cast<float>(1 << a.scale_log2);
   uint32_t *img = a.img + static_cast<size_t>(item) * kImgStride;
   for (int k = 0; k < S; ++k) {
-    const int row = lane * S + k;
+    const int row = lane_in * S + k;
     uint32_t w0 = 0, w1 = 0;
     for (int h = 0; h < halves; ++h) {
-      const int P = 32 * S - m[h];
+      const int P = H - m[h];
       const bool real = m[h] > 0 && row >= P;
       float z = 0.0f;
       if (real) {
@@ -345,6 +404,14 @@ cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s) {
   if (max_items == 0) return cudaSuccess;
   const int warps = 8;
   pack_kernel<<<(max_items + warps - 1) / warps, warps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qstats(const float *events, const uint32_t *offsets, uint32_t nq, double *qstats, int *status,
+                          cudaStream_t s) {
+  if (nq == 0) return cudaSuccess;
+  const int th = 32;  // one warp per block: the sequential chains spread over every SM
+  qstats_kernel<<<(nq + th - 1) / th, th, 0, s>>>(events, offsets, nq, qstats, status);
   return cudaGetLastError();
 }
 

@@ -19,7 +19,8 @@ __device__ __forceinline__ float fmin3p(float a, float b, float c) {
 }
 
 // Each level updates kChains cells (int16: cell pairs) from the previous
-// level's values, like one oblique step: d = |q - r|, m = min3, new = d + m.
+// level's values, like one oblique step: d = |q - r|, m = min3, new = d + m
+// (int16: saturated at CAP in one chain of eight, as the sweep's rows are).
 template <int PREC>
 __global__ void probe_kernel(uint32_t *out, int iters) {
   uint32_t a[kChains], x[kChains];
@@ -41,8 +42,8 @@ __global__ void probe_kernel(uint32_t *out, int iters) {
         const int j = (i + 1) % kChains, k = (i + 3) % kChains;
         if (PREC == HARU_INT16) {
           const uint32_t d = __viaddmax_s16x2_relu(x[i], a[k], __vsub2(x[j], x[i]));
-          const uint32_t m = __vimin3_s16x2(a[i], a[j], a[k]);
-          an[i] = __viaddmin_s16x2(d, m, x[k]);
+          const uint32_t m = __vimin3_u16x2(a[i], a[j], a[k]);
+          an[i] = i == 0 ? __viaddmin_u16x2(d, m, x[k]) : __vadd2(m, d);  // one row in eight saturates
           xn[i] = d;
         } else {
           const float t = __fsub_rn(g[i], g[j]);

@@ -16,8 +16,8 @@
 // boundary row, so the last query row is always lane 31's last register.
 //
 // INT16 form: two queries share a warp, one per 16-bit half (DPX
-// __vimin3_s16x2 / __viaddmin_s16x2 / __viaddmax_s16x2); costs saturate at
-// CAP, pad rows have cap 0. FP32 form: one query per warp, 3-input min.f32,
+// __viaddmax_s16x2_relu for |q - r|, __vimin3_u16x2, and __viaddmin_u16x2 on
+// the rows that saturate at CAP); pad rows hold 0. FP32 form: one query per warp, 3-input min.f32,
 // pad rows have weight 0 in gamma = fma(|q - r|, w, min3).
 //
 // Segments. The steps of one query are cut into segments that run as
@@ -143,6 +143,18 @@ struct Geo {
 constexpr uint32_t kPadQ2 = 0xf001f001u;  // -4095 in both halves
 constexpr uint32_t kCap2 = (static_cast<uint32_t>(kCap) << 16) | static_cast<uint32_t>(kCap);
 
+// Sparse saturation. Costs are held as unsigned 16-bit halves and only rows
+// k = S-1, S-1-kCapRun, ... of each lane take min(CAP, .); the rows between
+// add without a cap (__vadd2 on the full-rate pipe instead of a DPX
+// instruction on the half-rate one). Every cell lies between min(CAP, exact)
+// and the exact cost, and a min3 is at most its `up` input, so the j-th
+// uncapped row after a capped one holds at most CAP + j * 4094. Runs are at
+// most kCapRun - 1 = 8 rows (also across lanes: row S-1 is capped), so every
+// value and every sum before a cap stays below 2^16 (28673 + 9 * 4094 =
+// 65519), and each capped row -- the query's last row among them -- equals
+// min(CAP, exact), the value of the all-saturating recurrence.
+constexpr int kCapRun = 9;
+
 template <int S>
 struct StripI16 {
   uint32_t Q[S], NQ[S], G[2][S], Rr[S];
@@ -171,7 +183,7 @@ struct StripI16 {
   }
   // Exact state before step t: G[1] = step t-1, G[0] = step t-2, and the
   // reference samples the cells used at step t-1 (from the global image).
-  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane) {
+  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane, uint32_t ng) {
 #pragma unroll
     for (int k = 0; k < S; ++k) {
       G[1][k] = st[k * 32 + lane];
@@ -179,7 +191,7 @@ struct StripI16 {
       Rr[(1 + k) % S] = gref[t - 1 - static_cast<long>(lane) * S - k];
     }
     const uint32_t g = __shfl_up_sync(kFull, G[0][S - 1], 1);
-    gprev = lane ? g : 0u;
+    gprev = ng ? g : 0u;
   }
   __device__ __forceinline__ void save(uint32_t *st, int lane) const {
 #pragma unroll
@@ -190,8 +202,8 @@ struct StripI16 {
   }
 
   template <bool MASK>
-  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t nl,
-                                        uint32_t l0) {
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+                                        uint32_t nr, bool tracked) {
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
 #pragma unroll
@@ -202,8 +214,8 @@ struct StripI16 {
       uint32_t gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
       uint32_t rin = __shfl_up_sync(kFull, Rr[p], 1);
       const uint32_t rv = win.get(ref, u);
-      gup = imad(gup, nl, 0u);               // lane 0: the free-start row, 0
-      rin = imad(rin, nl, imad(rv, l0, 0u));  // lane 0: reference sample t
+      gup = imad(gup, ng, 0u);                    // a stack's first lane: the free-start row, 0
+      rin = imad(rin, nr, imad(rv, 1u - nr, 0u));  // lane 0: reference sample t
       Rr[p] = rin;
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
@@ -211,13 +223,13 @@ struct StripI16 {
         const uint32_t d = __viaddmax_s16x2_relu(r, NQ[k], __vsub2(Q[k], r));  // |q - r| per half
         const uint32_t up = k ? G[a][k - 1] : gup;
         const uint32_t dg = k ? G[b][k - 1] : gprev;
-        const uint32_t m = __vimin3_s16x2(up, dg, G[a][k]);
-        uint32_t v = __viaddmin_s16x2(d, m, kCap2);
+        const uint32_t m = __vimin3_u16x2(up, dg, G[a][k]);
+        uint32_t v = (S - 1 - k) % kCapRun == 0 ? __viaddmin_u16x2(d, m, kCap2) : __vadd2(m, d);
         if (MASK) v = (trel + u - lane * S >= k) ? v : init(k);
         G[b][k] = v;
       }
       gprev = gup;
-      if (lane == 31) ring[e0 + u] = G[b][S - 1];
+      if (tracked) ring[e0 + u] = G[b][S - 1];
     }
   }
 };
@@ -231,9 +243,8 @@ struct TrackI16 {
     if (va < ba) { ba = va; ca = c; }
     if (vb < bb) { bb = vb; cb = c; }
   }
-  __device__ __forceinline__ void reduce() {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+  __device__ __forceinline__ void reduce(int width) {  // over aligned groups of `width` lanes
+    for (int o = width >> 1; o > 0; o >>= 1) {
       int oa = __shfl_xor_sync(kFull, ba, o), ob = __shfl_xor_sync(kFull, bb, o);
       long pa = __shfl_xor_sync(kFull, ca, o), pb = __shfl_xor_sync(kFull, cb, o);
       if (oa < ba || (oa == ba && static_cast<unsigned long>(pa) < static_cast<unsigned long>(ca))) { ba = oa; ca = pa; }
@@ -278,7 +289,7 @@ struct StripF32 {
     }
     gprev = 0.0f;
   }
-  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane) {
+  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane, uint32_t ng) {
 #pragma unroll
     for (int k = 0; k < S; ++k) {
       G[1][k] = __uint_as_float(st[k * 32 + lane]);
@@ -286,7 +297,7 @@ struct StripF32 {
       Rr[(1 + k) % S] = ref_value(gref[t - 1 - static_cast<long>(lane) * S - k]);
     }
     const float g = __shfl_up_sync(kFull, G[0][S - 1], 1);
-    gprev = lane ? g : 0.0f;
+    gprev = ng ? g : 0.0f;
   }
   __device__ __forceinline__ void save(uint32_t *st, int lane) const {
 #pragma unroll
@@ -297,11 +308,9 @@ struct StripF32 {
   }
 
   template <bool MASK>
-  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t nl,
-                                        uint32_t l0) {
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+                                        uint32_t nr, bool tracked) {
     (void)trel;
-    (void)nl;
-    (void)l0;
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
     float *fring = reinterpret_cast<float *>(ring);
@@ -313,8 +322,8 @@ struct StripF32 {
       float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
       float rin = __shfl_up_sync(kFull, Rr[p], 1);
       const float rv = ref_value(win.get(ref, u));
-      gup = lane ? gup : 0.0f;
-      rin = lane ? rin : rv;
+      gup = ng ? gup : 0.0f;  // a stack's first lane: the free-start row, 0
+      rin = nr ? rin : rv;    // lane 0: reference sample t
       Rr[p] = rin;
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
@@ -326,7 +335,7 @@ struct StripF32 {
         G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
       }
       gprev = gup;
-      if (lane == 31) fring[e0 + u] = G[b][S - 1];
+      if (tracked) fring[e0 + u] = G[b][S - 1];
     }
   }
 };
@@ -344,9 +353,8 @@ struct TrackF32 {
     if constexpr (CAPPED) f = fminf(f, static_cast<float>(kCap));
     if (f < best) { best = f; col = c; }
   }
-  __device__ __forceinline__ void reduce() {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+  __device__ __forceinline__ void reduce(int width) {  // over aligned groups of `width` lanes
+    for (int o = width >> 1; o > 0; o >>= 1) {
       float ob = __shfl_xor_sync(kFull, best, o);
       long oc = __shfl_xor_sync(kFull, col, o);
       if (ob < best || (ob == best && static_cast<unsigned long>(oc) < static_cast<unsigned long>(col))) {
@@ -460,14 +468,24 @@ struct GlobalTiles {
 // the last row over own steps [t_own, t_end). fresh: the strip starts from
 // the fresh state at t_start (masked prologue for the int16 form).
 // save_start / save_final: where to store the state before step t_own and
-// before step t_end (nullptr: not stored). Returns false on abort.
+// before step t_end (nullptr: not stored). stk: a stacked item (lanes 0..15
+// and 16..31 are two strips; each lane tracks its own stack's last row).
+// `ring` holds 128 words per warp: two flush buffers of 64, the upper
+// stack's (or the whole strip's) entries first, the lower stack's at +32.
+// Returns false on abort.
 template <int FORM, int S, class Src>
 __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<FORM, S>::Track &tr, Src &src,
                           int TS, long t_start, long t_own, long t_end, bool fresh, long N, uint32_t *save_start,
-                          uint32_t *save_final, uint32_t *ring, int lane) {
+                          uint32_t *save_final, uint32_t *ring, int lane, bool stk) {
   constexpr int U = Geo<S>::U, F = Geo<S>::F;
   constexpr bool kMasked = FormOf<FORM, S>::kMasked;
-  const uint32_t nl = lane != 0 ? 1u : 0u, l0 = 1u - nl;
+  // ng: 0 on a lane that starts a stack from the free-start row; nr: 0 on
+  // lane 0, which injects the reference (it flows on through every lane)
+  const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u, nr = lane != 0 ? 1u : 0u;
+  const bool tracked = lane == 31 || (stk && lane == 15);
+  const int soff = stk && lane >= 16 ? 32 : 0;
+  const long last_row = (stk && lane < 16 ? 16L : 32L) * S - 1;
+  const int nscan = stk ? 2 : 1;
   const long mask_end = fresh ? t_start + 32L * S : t_start;
   const long k_first = t_start / TS;
   const int K = static_cast<int>((t_end + TS - 1) / TS - k_first);
@@ -481,18 +499,21 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
     const long hi = tk0 + TS < t_end ? tk0 + TS : t_end;
     for (long t0 = lo; t0 < hi; t0 += U) {
       if (save_start && t0 == t_own) st.save(save_start, lane);
-      uint32_t *rg = ring + buf * 32;
+      uint32_t *rg = ring + buf * 64 + soff;
       const uint32_t *ref = tile + (t0 - tk0);
       if (kMasked && t0 < mask_end)
-        st.template chunk<true>(ref, static_cast<int>(t0 - t_start), lane, rg, fl * U, nl, l0);
+        st.template chunk<true>(ref, static_cast<int>(t0 - t_start), lane, rg, fl * U, ng, nr, tracked);
       else
-        st.template chunk<false>(ref, 0, lane, rg, fl * U, nl, l0);
+        st.template chunk<false>(ref, 0, lane, rg, fl * U, ng, nr, tracked);
       if (++fl == F || t0 + U >= t_end) {
         __syncwarp();
-        if (lane < fl * U) {
-          const long t = tflush + lane;
-          const long c = t - (32L * S - 1);
-          if (t >= t_own && c >= 0 && c < N) tr.add(rg[lane], c);
+        for (int r = 0; r < nscan; ++r) {  // entry j = step tflush + j of this lane's stack
+          const int j = stk ? (lane & 15) + 16 * r : lane;
+          if (j < fl * U) {
+            const long t = tflush + j;
+            const long c = t - last_row;
+            if (t >= t_own && c >= 0 && c < N) tr.add(rg[j], c);
+          }
         }
         tflush += static_cast<long>(fl) * U;
         fl = 0;
@@ -520,9 +541,12 @@ __device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, in
   const size_t unit = static_cast<size_t>(item) * A.nseg_cap + g.seg;
   if (g.seg > 0) ss = A.states + (unit * 2 + 0) * kStateStride;
   if (g.seg + 1 < g.nseg) sf = A.states + (unit * 2 + 1) * kStateStride;
-  const bool ok = run_steps<FORM, S>(st, tr, ts, ts.tile_cols, t_start, t_own, t_end, true, A.N, ss, sf, ring, lane);
-  tr.reduce();
+  const bool stk = A.items[item].stacked != 0;
+  const bool ok =
+      run_steps<FORM, S>(st, tr, ts, ts.tile_cols, t_start, t_own, t_end, true, A.N, ss, sf, ring, lane, stk);
+  tr.reduce(stk ? 16 : 32);
   if (ok && lane == 0) tr.store(A.bests + unit);
+  if (ok && stk && lane == 16) tr.store(A.bests2 + unit);
 }
 
 template <int PREC, int S>
@@ -546,6 +570,9 @@ template <> struct Cls<0> { static constexpr int lo = 13, hi = 16; };
 template <> struct Cls<1> { static constexpr int lo = 9, hi = 12; };
 template <> struct Cls<2> { static constexpr int lo = 5, hi = 8; };
 template <> struct Cls<3> { static constexpr int lo = 1, hi = 4; };
+// One kernel for every strip height (a single longest-first queue), planned into slot 0.
+template <> struct Cls<4> { static constexpr int lo = 1, hi = 16; };
+template <int CLS> constexpr int slot_of() { return CLS == 4 ? 0 : CLS; }
 
 template <int PREC, int CLS, int S = Cls<CLS>::lo>
 __device__ __forceinline__ void dispatch_sweep(int s, const SdtwArgs &A, TileStream &ts, const Group &g, int item,
@@ -558,14 +585,15 @@ __device__ __forceinline__ void dispatch_sweep(int s, const SdtwArgs &A, TileStr
   }
 }
 
-// Two CTAs (16 warps) per SM for strips up to 12 rows per lane; the tallest
-// class needs more registers than that allows without spilling.
+// Two CTAs (16 warps) per SM for strips up to 12 rows per lane; kernels that
+// run strips of 13..16 rows need more registers than that allows without
+// spilling (a 168-register cap, for 12 warps per SM, measured ~20% slower).
 template <int PREC, int CLS>
-__global__ void __launch_bounds__(256, CLS == 0 ? 1 : 2) sdtw_kernel(SdtwArgs A) {
+__global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kernel(SdtwArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared *sh = reinterpret_cast<Shared *>(smem);
   uint32_t *rings = reinterpret_cast<uint32_t *>(smem + 128);
-  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * 64 * 4);
+  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * 128 * 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(&sh->full[0], 1);
@@ -577,9 +605,9 @@ __global__ void __launch_bounds__(256, CLS == 0 ? 1 : 2) sdtw_kernel(SdtwArgs A)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int first = A.ints[kIntClassFirst + CLS];
-  const int count = A.ints[kIntClassCount + CLS];
-  int *queue = A.ints + kIntQueues + CLS;
+  const int first = A.ints[kIntClassFirst + slot_of<CLS>()];
+  const int count = A.ints[kIntClassCount + slot_of<CLS>()];
+  int *queue = A.ints + kIntQueues + slot_of<CLS>();
   for (;;) {
     if (threadIdx.x == 0) sh->group = atomicAdd(queue, 1);
     __syncthreads();
@@ -605,7 +633,7 @@ __global__ void __launch_bounds__(256, CLS == 0 ? 1 : 2) sdtw_kernel(SdtwArgs A)
       if (ts.K > 1) ts.issue(1);
     }
     __syncthreads();
-    if (warp < grp.count) dispatch_sweep<PREC, CLS>(S, A, ts, grp, grp.first + warp, rings + warp * 64, lane);
+    if (warp < grp.count) dispatch_sweep<PREC, CLS>(S, A, ts, grp, grp.first + warp, rings + warp * 128, lane);
     __syncthreads();
     if (threadIdx.x == 0) sh->tile_base += ts.K;
   }
@@ -623,16 +651,50 @@ __global__ void __launch_bounds__(256, CLS == 0 ? 1 : 2) sdtw_kernel(SdtwArgs A)
 // speculative start state differs from the exact one, combine the segments'
 // last-row minima (smallest cost, then smallest column) and write the
 // outputs.
+// Segment minima combine in segment order: the smaller cost wins, and on a
+// tie the earlier segment's (smaller) column stays.
+template <int FORM>
+__device__ __forceinline__ void combine(Best &b, const Best &o) {
+  if (FORM == kFormI16) {
+    if (o.ia < b.ia) { b.ia = o.ia; b.ca = o.ca; }
+    if (o.ib < b.ib) { b.ib = o.ib; b.cb = o.cb; }
+  } else {
+    if (o.f < b.f) { b.f = o.f; b.ca = o.ca; }
+  }
+}
+
+template <int FORM>
+__device__ __forceinline__ void write_out(const SdtwArgs &A, const Best &b, int qa, int qb) {
+  if (qa < 0) return;
+  if (FORM == kFormI16) {
+    A.out_cost[qa] = static_cast<float>(b.ia) * A.inv_scale;
+    A.out_col[qa] = b.ca;
+    if (qb >= 0) {
+      A.out_cost[qb] = static_cast<float>(b.ib) * A.inv_scale;
+      A.out_col[qb] = b.cb;
+    }
+  } else if (FORM == kFormExact) {
+    A.out_cost[qa] = b.f * A.inv_scale;
+    A.out_col[qa] = b.ca;
+  } else {
+    A.out_cost[qa] = b.f;
+    A.out_col[qa] = b.ca;
+  }
+}
+
 template <int FORM, int S>
 __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane) {
   const Item it = A.items[item];
   const int nseg = it.nseg;
+  const bool stk = it.stacked != 0;
   const size_t base = static_cast<size_t>(item) * A.nseg_cap;
   Best b = A.bests[base];
+  Best b2 = stk ? A.bests2[base] : b;
   if (nseg > 1) {
     typename FormOf<FORM, S>::Strip st;
     st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
     const int TS = tile_width(S, A.tile_cols);
+    const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u;
     for (int s = 1; s < nseg; ++s) {
       const uint32_t *exact = A.states + ((base + s - 1) * 2 + 1) * kStateStride;
       const uint32_t *spec = A.states + ((base + s) * 2 + 0) * kStateStride;
@@ -641,42 +703,26 @@ __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane
       if (!__all_sync(kFull, eq)) {
         long t_start, t_own, t_end;
         seg_bounds(S, nseg, s, A.N, &t_start, &t_own, &t_end);
-        st.restore(exact, reinterpret_cast<const uint32_t *>(A.ref_img), t_own, lane);
+        st.restore(exact, reinterpret_cast<const uint32_t *>(A.ref_img), t_own, lane, ng);
         typename FormOf<FORM, S>::Track tr;
         GlobalTiles src{reinterpret_cast<const uint32_t *>(A.ref_img), TS, t_own / TS};
         uint32_t *sf = s + 1 < nseg ? A.states + ((base + s) * 2 + 1) * kStateStride : nullptr;
-        run_steps<FORM, S>(st, tr, src, TS, t_own, t_own, t_end, false, A.N, nullptr, sf, ring, lane);
-        tr.reduce();
+        run_steps<FORM, S>(st, tr, src, TS, t_own, t_own, t_end, false, A.N, nullptr, sf, ring, lane, stk);
+        tr.reduce(stk ? 16 : 32);
         if (lane == 0) {
           tr.store(A.bests + base + s);
           atomicAdd(A.ints + kIntFixups, 1);
         }
+        if (stk && lane == 16) tr.store(A.bests2 + base + s);
         __syncwarp();
       }
-      const Best o = A.bests[base + s];
-      if (FORM == kFormI16) {
-        if (o.ia < b.ia) { b.ia = o.ia; b.ca = o.ca; }
-        if (o.ib < b.ib) { b.ib = o.ib; b.cb = o.cb; }
-      } else {
-        if (o.f < b.f) { b.f = o.f; b.ca = o.ca; }
-      }
+      combine<FORM>(b, A.bests[base + s]);
+      if (stk) combine<FORM>(b2, A.bests2[base + s]);
     }
   }
   if (lane == 0) {
-    if (FORM == kFormI16) {
-      A.out_cost[it.qa] = static_cast<float>(b.ia) * A.inv_scale;
-      A.out_col[it.qa] = b.ca;
-      if (it.qb >= 0) {
-        A.out_cost[it.qb] = static_cast<float>(b.ib) * A.inv_scale;
-        A.out_col[it.qb] = b.cb;
-      }
-    } else if (FORM == kFormExact) {
-      A.out_cost[it.qa] = b.f * A.inv_scale;
-      A.out_col[it.qa] = b.ca;
-    } else {
-      A.out_cost[it.qa] = b.f;
-      A.out_col[it.qa] = b.ca;
-    }
+    write_out<FORM>(A, b, it.qa, it.qb);
+    if (stk) write_out<FORM>(A, b2, it.qc, it.qd);
   }
 }
 
@@ -706,14 +752,14 @@ constexpr int kFixWarps = 4;
 
 template <int PREC, int CLS>
 __global__ void __launch_bounds__(kFixWarps * 32) fixup_kernel(SdtwArgs A) {
-  __shared__ uint32_t rings[kFixWarps * 64];
+  __shared__ uint32_t rings[kFixWarps * 128];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int first = A.ints[kIntClassItemFirst + CLS];
-  const int count = A.ints[kIntClassItemCount + CLS];
+  const int first = A.ints[kIntClassItemFirst + slot_of<CLS>()];
+  const int count = A.ints[kIntClassItemCount + slot_of<CLS>()];
   const int i = blockIdx.x * kFixWarps + warp;
   if (i >= count) return;
   const int item = first + i;
-  dispatch_fixup<PREC, CLS>(A.items[item].S, A, item, rings + warp * 64, lane);
+  dispatch_fixup<PREC, CLS>(A.items[item].S, A, item, rings + warp * 128, lane);
 }
 
 template <int PREC, int CLS>
@@ -740,7 +786,7 @@ int occupancy_cls(int tile_cols, int warps) {
 }  // namespace
 
 size_t sdtw_smem_bytes(int tile_cols, int warps) {
-  return 128 + static_cast<size_t>(warps) * 64 * 4 + 2 * static_cast<size_t>(tile_cols) * 4;
+  return 128 + static_cast<size_t>(warps) * 128 * 4 + 2 * static_cast<size_t>(tile_cols) * 4;
 }
 
 int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
@@ -749,6 +795,7 @@ int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
       case 0: return occupancy_cls<HARU_INT16, 0>(tile_cols, warps);
       case 1: return occupancy_cls<HARU_INT16, 1>(tile_cols, warps);
       case 2: return occupancy_cls<HARU_INT16, 2>(tile_cols, warps);
+      case 4: return occupancy_cls<HARU_INT16, 4>(tile_cols, warps);
       default: return occupancy_cls<HARU_INT16, 3>(tile_cols, warps);
     }
   }
@@ -756,6 +803,7 @@ int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
     case 0: return occupancy_cls<HARU_FP32, 0>(tile_cols, warps);
     case 1: return occupancy_cls<HARU_FP32, 1>(tile_cols, warps);
     case 2: return occupancy_cls<HARU_FP32, 2>(tile_cols, warps);
+    case 4: return occupancy_cls<HARU_FP32, 4>(tile_cols, warps);
     default: return occupancy_cls<HARU_FP32, 3>(tile_cols, warps);
   }
 }
@@ -766,6 +814,7 @@ cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int
       case 0: return launch_cls<HARU_INT16, 0>(a, grid, fix_items, s);
       case 1: return launch_cls<HARU_INT16, 1>(a, grid, fix_items, s);
       case 2: return launch_cls<HARU_INT16, 2>(a, grid, fix_items, s);
+      case 4: return launch_cls<HARU_INT16, 4>(a, grid, fix_items, s);
       default: return launch_cls<HARU_INT16, 3>(a, grid, fix_items, s);
     }
   }
@@ -773,6 +822,7 @@ cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int
     case 0: return launch_cls<HARU_FP32, 0>(a, grid, fix_items, s);
     case 1: return launch_cls<HARU_FP32, 1>(a, grid, fix_items, s);
     case 2: return launch_cls<HARU_FP32, 2>(a, grid, fix_items, s);
+    case 4: return launch_cls<HARU_FP32, 4>(a, grid, fix_items, s);
     default: return launch_cls<HARU_FP32, 3>(a, grid, fix_items, s);
   }
 }

@@ -264,3 +264,50 @@ def test_int16_split_over_both_pipes_is_identical(haru, sars):
         np.testing.assert_array_equal(c, base[0], err_msg=str(k))
         np.testing.assert_array_equal(j, base[1], err_msg=str(k))
     compare_int16(base[0], base[1], ref, qs.events, qs.offsets, idx=np.arange(0, 523, 29))
+
+
+@pytest.mark.parametrize("units", [1, 0])
+def test_single_sweep_kernel_is_identical(haru, sars, units):
+    """One sweep kernel over every strip height (one longest-first queue)
+    gives the four class kernels' results bit for bit, for both forms."""
+    _, ref = sars
+    qs = synth.workload("sars_uneven_8192", nq=611).queries
+    out = {}
+    for one in (0, 1):
+        with haru.Context(single_kernel=one, units_target=units) as ctx:
+            ctx.ref_load(ref)
+            out[one] = [ctx.sdtw_batch(p, qs.events, qs.offsets) for p in (haru.HARU_INT16, haru.HARU_FP32)]
+    for p in range(2):
+        np.testing.assert_array_equal(out[1][p][0], out[0][p][0])
+        np.testing.assert_array_equal(out[1][p][1], out[0][p][1])
+    idx = np.arange(0, 611, 47)
+    compare_int16(out[1][0][0], out[1][0][1], ref, qs.events, qs.offsets, idx=idx)
+    compare_fp32(out[1][1][0], out[1][1][1], ref, qs.events, qs.offsets, idx=idx)
+
+
+@pytest.mark.parametrize("units", [1, 4096])
+def test_int16_saturation_extremes(haru, units):
+    """Codes at the clamp limits (|q - r| up to 4094 per cell) and costs
+    around CAP: the int16 form saturates exactly like the oracle's
+    all-saturating recurrence, with and without reference segments."""
+    rng = np.random.default_rng(21)
+    N = 7000
+    ref = np.where(rng.random(N) < 0.5, rng.choice([-40.0, 40.0], N), rng.uniform(-40.0, 40.0, N))
+    lens = np.concatenate([np.full(8, 512), np.full(4, 480), rng.integers(1, 513, 36)])
+    parts = []
+    for i, m in enumerate(lens):
+        s = int(rng.integers(0, N - m + 1))
+        if i % 3 == 0:
+            parts.append(rng.choice([-40.0, 40.0], m))                    # extremes everywhere
+        elif i % 3 == 1:
+            parts.append(ref[s:s + m] + rng.normal(0.0, rng.uniform(0.5, 2.0), m))  # cost near CAP
+        else:
+            parts.append(-ref[s:s + m])                                    # |q - r| = 2 |r|
+    ev = np.concatenate(parts).astype(np.float32)
+    off = offsets_of(lens)
+    with haru.Context(units_target=units) as ctx:
+        ctx.ref_load(ref, normalize=False)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off, raw=False)
+    o = compare_int16(c16, j16, ref, ev, off, normalize_ref=False, normalize_q=False)
+    capped = o.icost >= oracle.cap()
+    assert capped.sum() >= 10 and (~capped).sum() >= 10
