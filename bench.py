@@ -64,7 +64,8 @@ def profiled_traffic(form: str):
                 k, v = line.strip().split(":", 1)
                 vals[k.strip()] = v.strip()
     csrc = os.path.join(ROOT, "paper_2211_07340_gb300", "csrc")
-    src = open(os.path.join(csrc, "sdtw.cu"), "rb").read() + open(os.path.join(csrc, "haru_internal.h"), "rb").read()
+    src = (open(os.path.join(csrc, "sdtw_kernels.cuh"), "rb").read() +
+           open(os.path.join(csrc, "haru_internal.h"), "rb").read())
     if vals.get("kernel_source_sha1") != hashlib.sha1(src).hexdigest():
         return None
     v = vals.get(f"traffic_bytes_per_step_{form}")

@@ -59,6 +59,7 @@ class haru_config(ctypes.Structure):
         ("serve_prefix", ctypes.c_uint32),
         ("units_target", ctypes.c_int),
         ("single_kernel", ctypes.c_int),
+        ("stack_short", ctypes.c_int),
         ("int16_exact_share", ctypes.c_int),
     ]
 

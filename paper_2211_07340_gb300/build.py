@@ -1,6 +1,7 @@
 """Build libharu.so (the CUDA library behind include/haru.h) in-tree for sm_103a.
 
-Each .cu translation unit is compiled in parallel with nvcc, then linked into
+Each .cu translation unit is compiled in parallel with nvcc (the sweep kernels
+are split one (precision, strip-height class) per unit), then linked into
 paper_2211_07340_gb300/_lib/libharu.so. No CMake, one -gencode.
 """
 from __future__ import annotations
@@ -36,8 +37,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(HERE, "..", "include", "haru.h"),
-                                                                   __file__]
+    deps = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            [os.path.join(HERE, "..", "include", "haru.h"), __file__])
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
@@ -56,7 +57,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+    # the sweep kernels are one translation unit per (precision, class): build them all at once
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(24, os.cpu_count() or 1))) as ex:
         for obj, log in ex.map(one, sources()):
             objs.append(obj)
             if verbose and log:

@@ -58,6 +58,7 @@ haru::LaunchCfg haru_ctx::launch_cfg() const {
   lc.units_target = cfg.units_target;
   lc.int16_mode = cfg.int16_exact_share ? 2 : 1;
   lc.single_kernel = cfg.single_kernel ? 1 : 0;
+  lc.stack_short = cfg.stack_short > 0 ? 1 : (cfg.stack_short < 0 ? -1 : 0);
   lc.wait_ns = wait_ns(cfg);
   return lc;
 }

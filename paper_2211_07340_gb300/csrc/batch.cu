@@ -76,6 +76,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   pa.warps = lc.warps;
   pa.units_target = ws.units_target;
   pa.single = lc.single_kernel ? 1 : 0;
+  pa.stack = lc.stack_short > 0 || (lc.stack_short == 0 && nq >= static_cast<uint32_t>(ws.units_target)) ? 1 : 0;
   pa.nseg_cap = ws.nseg_cap;
   pa.items = ws.items;
   pa.groups = ws.groups;

@@ -31,7 +31,9 @@ struct Item {
 };
 
 // Queries of at most this many events are stacked two to a warp strip
-// (planner modes 0 and 1).
+// (planner modes 0 and 1) in batches large enough to fill the machine:
+// stacking doubles the rows per lane, which raises throughput but also the
+// time one strip takes, so small (latency-bound) batches stay unstacked.
 constexpr int kStackMax = 16 * 16;
 
 // Consecutive items with the same S swept over the same segment by one CTA,
@@ -139,6 +141,7 @@ struct PlanArgs {
   int warps;                // items per group
   int units_target;         // wanted work units (item x segment) in the batch
   int single;               // 1: every strip height in slot 0 (one kernel, one queue)
+  int stack;                // 1: stack queries of <= kStackMax events two to a strip (modes 0, 1)
   int nseg_cap;             // most segments per item (state storage is sized for it)
   Item *items;
   Group *groups;
@@ -167,7 +170,6 @@ cudaError_t launch_qstats(const float *events, const uint32_t *offsets, uint32_t
 cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s);
 size_t sdtw_smem_bytes(int tile_cols, int warps);
 int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps);
-int sdtw_class_of(int S);
 
 // Reference preparation.
 cudaError_t launch_ref_levels(const uint8_t *bases, size_t n, const float *model, int k, float *out,

@@ -106,6 +106,7 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   pa.warps = warps;
   pa.units_target = 1;
   pa.single = 0;
+  pa.stack = 0;  // at most HARU_NOALLOC_MAX_QUERIES queries: latency over throughput
   pa.nseg_cap = 1;
   pa.items = items;
   pa.groups = groups;

@@ -108,14 +108,14 @@ __device__ __forceinline__ int sdtw_class_dev(int S) { return S >= 13 ? 0 : (S >
 
 // Bucket key of query q: its strip height S (rows per lane), plus kMaxS + 1
 // if it is stacked (16 lanes, S = ceil(M / 16)); 0 for an invalid length.
-__device__ __forceinline__ int bucket_key(const uint32_t *off, uint32_t q, long N, int mode, int *status) {
+__device__ __forceinline__ int bucket_key(const uint32_t *off, uint32_t q, long N, int mode, int stack, int *status) {
   const uint32_t m = off[q + 1] - off[q];
   const long lim = N < HARU_MAX_QUERY ? N : HARU_MAX_QUERY;
   if (m < 1 || static_cast<long>(m) > lim) {
     if (status) report(status, HARU_EINVAL);
     return 0;
   }
-  if (mode != 2 && m <= static_cast<uint32_t>(kStackMax)) return static_cast<int>((m + 15) / 16) + kMaxS + 1;
+  if (stack && mode != 2 && m <= static_cast<uint32_t>(kStackMax)) return static_cast<int>((m + 15) / 16) + kMaxS + 1;
   return static_cast<int>((m + 31) / 32);
 }
 
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
   __syncwarp();
   for (uint32_t q0 = q_lo; q0 < q_hi; q0 += 32) {
     const uint32_t q = q0 + lane;
-    const int key = q < q_hi ? bucket_key(a.offsets, q, a.N, a.pair, status) : 0;
+    const int key = q < q_hi ? bucket_key(a.offsets, q, a.N, a.pair, a.stack, status) : 0;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     if (key && lane == __ffs(peers) - 1) wrun[warp][key] += __popc(peers);
     __syncwarp();
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
   const unsigned lt = (1u << lane) - 1u;
   for (uint32_t q0 = q_lo; q0 < q_hi; q0 += 32) {
     const uint32_t q = q0 + lane;
-    const int key = q < q_hi ? bucket_key(a.offsets, q, a.N, a.pair, nullptr) : 0;
+    const int key = q < q_hi ? bucket_key(a.offsets, q, a.N, a.pair, a.stack, nullptr) : 0;
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     if (key > kMaxS) {  // stacked: slots qa, qb | qc, qd (INT16) or qa | qc (FP32)
       const int b = key - kMaxS - 1;

@@ -1,0 +1,810 @@
+// The sDTW wavefront kernels (Eq. 1, Section 2.3; the pipelined oblique column
+// of Section 4.3 / Fig. 5, mapped onto warps).
+//
+// Layout of one warp's work. A query of M events is padded at the top to
+// 32 * S rows (S = ceil(M / 32)); lane l holds rows l*S .. l*S + S - 1 in
+// registers. Row i processes reference column t - i at step t, so every row
+// is one processing element of the paper's PE chain and the whole strip is
+// one oblique column: the S cells of a lane in one step are independent
+// (instruction-level parallelism S), a cell reads
+//   up   = row i-1 at step t-1,  diag = row i-1 at step t-2,  left = row i at step t-1,
+// and each step one value (the bottom row's cost) and the reference sample
+// it used cross from lane l-1 to lane l by __shfl_up_sync. Lane 0 injects
+// reference sample t and the free-start row gamma(0, .) = 0. A sweep is
+// N + 32*S - 1 steps, the paper's N + M - 1 (Section 4.3) for the padded
+// height. Pad rows sit above the query and hold exactly 0, the free-start
+// boundary row, so the last query row is always lane 31's last register.
+//
+// INT16 form: two queries share a warp, one per 16-bit half (DPX
+// __viaddmax_s16x2_relu for |q - r|, __vimin3_u16x2, and __viaddmin_u16x2 on
+// the rows that saturate at CAP); pad rows hold 0. FP32 form: one query per warp, 3-input min.f32,
+// pad rows have weight 0 in gamma = fma(|q - r|, w, min3).
+//
+// Segments. The steps of one query are cut into segments that run as
+// independent work units. Segment s > 0 starts V steps early from a fresh
+// state (as if the reference began there) and records its state (the last
+// two oblique columns) when it reaches its own first step B_s; segment s-1
+// records its exact state at the same step. The fix-up kernel compares the
+// two: equal states give identical computations from B_s on (the DP is a
+// deterministic function of that state and the reference), so the segment's
+// results stand; otherwise it recomputes the segment from the exact state.
+// The result is always the plain DP's.
+//
+// The reference streams through shared memory: every CTA sweeps a group of
+// warps (same S, same segment) over the same columns; tiles of T_S columns
+// are fetched by cp.async.bulk (TMA) into a two-slot ring guarded by
+// mbarriers. The warp that releases a slot last issues the copy of the tile
+// two ahead.
+//
+// The last-row minimum and its first column (Algorithm 1's final scan,
+// Algorithm 2's per-column compare) are tracked through a small per-warp
+// shared ring: lane 31 stores its bottom-row cost every step, and every
+// <= 32 steps each lane scans one stored value; a warp reduction keeps the
+// smallest cost, then the smallest column.
+//
+// Every wait is bounded by a global-timer deadline; on expiry the kernel
+// records HARU_ETIMEDOUT, waits (bounded) for its own copies in flight and
+// returns.
+
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "haru_internal.h"
+
+namespace haru {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of `bar` to complete, giving up at `deadline`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned long long deadline) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (now_ns() > deadline) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+// d = a * b + c on the integer multiply-add unit (keeps lane-0 fix-ups off
+// the half-rate pipe that the DPX min/max instructions use).
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Reference sample of step u of a chunk, read 4 (or 2) at a time: `ref` is
+// 16-byte (8-byte) aligned whenever U is a multiple of 4 (2).
+template <int U>
+struct RefWindow {
+  uint4 v4;
+  uint2 v2;
+  __device__ __forceinline__ uint32_t get(const uint32_t *ref, int u) {
+    if constexpr (U % 4 == 0) {
+      if (u % 4 == 0) v4 = reinterpret_cast<const uint4 *>(ref)[u / 4];
+      const int c = u % 4;
+      return c == 0 ? v4.x : (c == 1 ? v4.y : (c == 2 ? v4.z : v4.w));
+    } else if constexpr (U % 2 == 0) {
+      if (u % 2 == 0) v2 = reinterpret_cast<const uint2 *>(ref)[u / 2];
+      return (u % 2 == 0) ? v2.x : v2.y;
+    } else {
+      return ref[u];
+    }
+  }
+};
+
+template <int S>
+struct Geo {
+  static constexpr int U = (S % 2 == 0) ? S : 2 * S;    // steps per unrolled chunk (register renaming period)
+  static constexpr int F = (32 / U) > 0 ? (32 / U) : 1; // chunks per tracking flush
+};
+
+// ---------------------------------------------------------------- INT16 --
+// Pad rows carry the code -4095 in both Q and NQ: |q - r| is then taken as
+// relu(max(r + NQ, Q - r)) = relu(negative) = 0, so a pad row stays 0 (the
+// free-start row) without a per-row cap, and real rows (|q|, |r| <= 2047)
+// get max(r - q, q - r) unchanged.
+constexpr uint32_t kPadQ2 = 0xf001f001u;  // -4095 in both halves
+constexpr uint32_t kCap2 = (static_cast<uint32_t>(kCap) << 16) | static_cast<uint32_t>(kCap);
+
+// Sparse saturation. Costs are held as unsigned 16-bit halves and only rows
+// k = S-1, S-1-kCapRun, ... of each lane take min(CAP, .); the rows between
+// add without a cap (__vadd2 on the full-rate pipe instead of a DPX
+// instruction on the half-rate one). Every cell lies between min(CAP, exact)
+// and the exact cost, and a min3 is at most its `up` input, so the j-th
+// uncapped row after a capped one holds at most CAP + j * 4094. Runs are at
+// most kCapRun - 1 = 8 rows (also across lanes: row S-1 is capped), so every
+// value and every sum before a cap stays below 2^16 (28673 + 9 * 4094 =
+// 65519), and each capped row -- the query's last row among them -- equals
+// min(CAP, exact), the value of the all-saturating recurrence.
+constexpr int kCapRun = 9;
+
+template <int S>
+struct StripI16 {
+  uint32_t Q[S], NQ[S], G[2][S], Rr[S];
+  uint32_t gprev;
+
+  __device__ __forceinline__ void load(const uint32_t *img, int lane) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      Q[k] = img[k * 32 + lane];
+      NQ[k] = img[(S + k) * 32 + lane];
+    }
+  }
+  // Initial value of row k of this lane: CAP (infinity) for a real row, 0 for a pad row.
+  __device__ __forceinline__ uint32_t init(int k) const { return ~__vcmpeq2(Q[k], kPadQ2) & kCap2; }
+  // As if the reference began at the current step: every row at its initial
+  // value; the masked chunks hold rows that have not reached their first
+  // column at that value.
+  __device__ __forceinline__ void fresh() {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[0][k] = init(k);
+      G[1][k] = G[0][k];
+      Rr[k] = 0u;
+    }
+    gprev = 0u;
+  }
+  // Exact state before step t: G[1] = step t-1, G[0] = step t-2, and the
+  // reference samples the cells used at step t-1 (from the global image).
+  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane, uint32_t ng) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[1][k] = st[k * 32 + lane];
+      G[0][k] = st[(S + k) * 32 + lane];
+      Rr[(1 + k) % S] = gref[t - 1 - static_cast<long>(lane) * S - k];
+    }
+    const uint32_t g = __shfl_up_sync(kFull, G[0][S - 1], 1);
+    gprev = ng ? g : 0u;
+  }
+  __device__ __forceinline__ void save(uint32_t *st, int lane) const {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      st[k * 32 + lane] = G[1][k];
+      st[(S + k) * 32 + lane] = G[0][k];
+    }
+  }
+
+  template <bool MASK>
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+                                        uint32_t nr, bool tracked) {
+    constexpr int U = Geo<S>::U;
+    RefWindow<U> win;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = (S - (u % S)) % S;
+      const int a = (u + 1) & 1;
+      const int b = u & 1;
+      uint32_t gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
+      uint32_t rin = __shfl_up_sync(kFull, Rr[p], 1);
+      const uint32_t rv = win.get(ref, u);
+      gup = imad(gup, ng, 0u);                    // a stack's first lane: the free-start row, 0
+      rin = imad(rin, nr, imad(rv, 1u - nr, 0u));  // lane 0: reference sample t
+      Rr[p] = rin;
+#pragma unroll
+      for (int k = S - 1; k >= 0; --k) {
+        const uint32_t r = Rr[(p + k) % S];
+        const uint32_t d = __viaddmax_s16x2_relu(r, NQ[k], __vsub2(Q[k], r));  // |q - r| per half
+        const uint32_t up = k ? G[a][k - 1] : gup;
+        const uint32_t dg = k ? G[b][k - 1] : gprev;
+        const uint32_t m = __vimin3_u16x2(up, dg, G[a][k]);
+        uint32_t v = (S - 1 - k) % kCapRun == 0 ? __viaddmin_u16x2(d, m, kCap2) : __vadd2(m, d);
+        if (MASK) v = (trel + u - lane * S >= k) ? v : init(k);
+        G[b][k] = v;
+      }
+      gprev = gup;
+      if (tracked) ring[e0 + u] = G[b][S - 1];
+    }
+  }
+};
+
+struct TrackI16 {
+  int ba = 0x7fffffff, bb = 0x7fffffff;
+  long ca = -1, cb = -1;
+  __device__ __forceinline__ void add(uint32_t v, long c) {
+    const int va = static_cast<int>(v & 0xffffu);
+    const int vb = static_cast<int>(v >> 16);
+    if (va < ba) { ba = va; ca = c; }
+    if (vb < bb) { bb = vb; cb = c; }
+  }
+  __device__ __forceinline__ void reduce(int width) {  // over aligned groups of `width` lanes
+    for (int o = width >> 1; o > 0; o >>= 1) {
+      int oa = __shfl_xor_sync(kFull, ba, o), ob = __shfl_xor_sync(kFull, bb, o);
+      long pa = __shfl_xor_sync(kFull, ca, o), pb = __shfl_xor_sync(kFull, cb, o);
+      if (oa < ba || (oa == ba && static_cast<unsigned long>(pa) < static_cast<unsigned long>(ca))) { ba = oa; ca = pa; }
+      if (ob < bb || (ob == bb && static_cast<unsigned long>(pb) < static_cast<unsigned long>(cb))) { bb = ob; cb = pb; }
+    }
+  }
+  __device__ __forceinline__ void store(Best *b) const {
+    b->ia = ba; b->ib = bb; b->f = 0.0f; b->pad = 0; b->ca = ca; b->cb = cb;
+  }
+};
+
+// ----------------------------------------------------------------- FP32 --
+// CODES: the reference words are int16 codes (q | q << 16) and the query
+// samples are int16 codes held as floats: the exact-integer form of the
+// int16 arithmetic, run through the FP32 units (see FormOf below).
+template <int S, bool CODES>
+struct StripF32 {
+  float Q[S], W[S], G[2][S], Rr[S];
+  float gprev;
+
+  __device__ __forceinline__ static float ref_value(uint32_t w) {
+    if constexpr (CODES)
+      return __int2float_rn(static_cast<int>(static_cast<short>(w & 0xffffu)));
+    else
+      return __uint_as_float(w);
+  }
+
+  __device__ __forceinline__ void load(const uint32_t *img, int lane) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      Q[k] = __uint_as_float(img[k * 32 + lane]);
+      W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
+    }
+  }
+  __device__ __forceinline__ void fresh() {
+    const float kBig = 1.0e30f;  // stands for +inf; sums of these stay finite
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[0][k] = W[k] != 0.0f ? kBig : 0.0f;
+      G[1][k] = G[0][k];
+      Rr[k] = kBig;  // columns before the start: distance ~1e30 for real rows, weight 0 for pad rows
+    }
+    gprev = 0.0f;
+  }
+  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane, uint32_t ng) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[1][k] = __uint_as_float(st[k * 32 + lane]);
+      G[0][k] = __uint_as_float(st[(S + k) * 32 + lane]);
+      Rr[(1 + k) % S] = ref_value(gref[t - 1 - static_cast<long>(lane) * S - k]);
+    }
+    const float g = __shfl_up_sync(kFull, G[0][S - 1], 1);
+    gprev = ng ? g : 0.0f;
+  }
+  __device__ __forceinline__ void save(uint32_t *st, int lane) const {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      st[k * 32 + lane] = __float_as_uint(G[1][k]);
+      st[(S + k) * 32 + lane] = __float_as_uint(G[0][k]);
+    }
+  }
+
+  template <bool MASK>
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+                                        uint32_t nr, bool tracked) {
+    (void)trel;
+    constexpr int U = Geo<S>::U;
+    RefWindow<U> win;
+    float *fring = reinterpret_cast<float *>(ring);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = (S - (u % S)) % S;
+      const int a = (u + 1) & 1;
+      const int b = u & 1;
+      float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
+      float rin = __shfl_up_sync(kFull, Rr[p], 1);
+      const float rv = ref_value(win.get(ref, u));
+      gup = ng ? gup : 0.0f;  // a stack's first lane: the free-start row, 0
+      rin = nr ? rin : rv;    // lane 0: reference sample t
+      Rr[p] = rin;
+#pragma unroll
+      for (int k = S - 1; k >= 0; --k) {
+        const float r = Rr[(p + k) % S];
+        const float d = __fsub_rn(Q[k], r);
+        const float up = k ? G[a][k - 1] : gup;
+        const float dg = k ? G[b][k - 1] : gprev;
+        const float m = fmin3f(up, dg, G[a][k]);
+        G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
+      }
+      gprev = gup;
+      if (tracked) fring[e0 + u] = G[b][S - 1];
+    }
+  }
+};
+
+// CAPPED: last-row costs are compared as min(CAP, cost), the saturation of
+// the int16 form, so an exact-integer strip reports what a saturating one
+// would (saturating every cell equals saturating the exact result once).
+template <bool CAPPED>
+struct TrackF32 {
+  float best;
+  long col;
+  __device__ TrackF32() : best(__builtin_huge_valf()), col(-1) {}
+  __device__ __forceinline__ void add(uint32_t v, long c) {
+    float f = __uint_as_float(v);
+    if constexpr (CAPPED) f = fminf(f, static_cast<float>(kCap));
+    if (f < best) { best = f; col = c; }
+  }
+  __device__ __forceinline__ void reduce(int width) {  // over aligned groups of `width` lanes
+    for (int o = width >> 1; o > 0; o >>= 1) {
+      float ob = __shfl_xor_sync(kFull, best, o);
+      long oc = __shfl_xor_sync(kFull, col, o);
+      if (ob < best || (ob == best && static_cast<unsigned long>(oc) < static_cast<unsigned long>(col))) {
+        best = ob;
+        col = oc;
+      }
+    }
+  }
+  __device__ __forceinline__ void store(Best *b) const {
+    b->ia = 0; b->ib = 0; b->f = best; b->pad = 0; b->ca = col; b->cb = -1;
+  }
+};
+
+// Arithmetic forms of a strip: FP32 queries, int16 pairs (DPX), and int16
+// codes computed exactly in FP32. The last two give identical results; an
+// int16 batch runs both side by side so its cells use the half-rate DPX/min
+// pipe and the full-rate FMA pipe at once.
+constexpr int kFormF32 = 0, kFormI16 = 1, kFormExact = 2;
+
+template <int FORM, int S>
+struct FormOf;
+template <int S>
+struct FormOf<kFormI16, S> {
+  using Strip = StripI16<S>;
+  using Track = TrackI16;
+  static constexpr bool kMasked = true;
+};
+template <int S>
+struct FormOf<kFormF32, S> {
+  using Strip = StripF32<S, false>;
+  using Track = TrackF32<false>;
+  static constexpr bool kMasked = false;
+};
+template <int S>
+struct FormOf<kFormExact, S> {
+  using Strip = StripF32<S, true>;
+  using Track = TrackF32<true>;
+  static constexpr bool kMasked = false;
+};
+
+// ----------------------------------------------------------- tile sources --
+// Shared state of one CTA.
+struct Shared {
+  uint64_t full[2];
+  int cnt[2];
+  int uses[2];
+  int group;
+  int tile_base;
+  int abort;
+  int pad;
+};
+
+// Reference tiles streamed into shared memory by TMA (the sweep kernel).
+struct TileStream {
+  Shared *sh;
+  char *slots;                 // two slots of tile_cols words
+  const char *src;             // reference image
+  int tile_cols;               // T_S
+  int k_first;                 // first global tile of this group's steps
+  int K;                       // tiles in this group's sweep
+  int n_active;                // warps consuming this stream
+  unsigned long long wait_ns;  // longest single wait
+  int *status;
+
+  __device__ void issue(int k) {  // one thread
+    const int gk = sh->tile_base + k;
+    const int slot = gk & 1;
+    const unsigned bytes = static_cast<unsigned>(tile_cols) * 4u;
+    fence_proxy_async();
+    mbar_expect_tx(&sh->full[slot], bytes);
+    tma_load_1d(slots + static_cast<size_t>(slot) * tile_cols * 4,
+                src + static_cast<size_t>(k_first + k) * tile_cols * 4, bytes, &sh->full[slot]);
+    sh->uses[slot] += 1;
+  }
+  __device__ const uint32_t *acquire(int k) {  // whole warp
+    const int gk = sh->tile_base + k;
+    const int slot = gk & 1;
+    if (!mbar_wait_bounded(&sh->full[slot], (gk >> 1) & 1, now_ns() + wait_ns)) {
+      report(status, HARU_ETIMEDOUT);
+      sh->abort = 1;
+      return nullptr;
+    }
+    return reinterpret_cast<const uint32_t *>(slots + static_cast<size_t>(slot) * tile_cols * 4);
+  }
+  __device__ void release(int k) {  // lane 0 of a warp
+    const int gk = sh->tile_base + k;
+    const int slot = gk & 1;
+    __threadfence_block();
+    const int old = atomicAdd(&sh->cnt[slot], 1);
+    if (old == n_active - 1) {
+      sh->cnt[slot] = 0;
+      __threadfence_block();
+      if (k + 2 < K) issue(k + 2);
+    }
+  }
+};
+
+// The reference read straight from global memory (the fix-up kernel).
+struct GlobalTiles {
+  const uint32_t *img;
+  int tile_cols;
+  long k_first;
+  __device__ __forceinline__ const uint32_t *acquire(int k) {
+    return img + static_cast<size_t>(k_first + k) * tile_cols;
+  }
+  __device__ __forceinline__ void release(int) {}
+};
+
+// ------------------------------------------------------------ one unit --
+// Runs steps [t_start, t_end) of one strip (a query or a pair) and tracks
+// the last row over own steps [t_own, t_end). fresh: the strip starts from
+// the fresh state at t_start (masked prologue for the int16 form).
+// save_start / save_final: where to store the state before step t_own and
+// before step t_end (nullptr: not stored). stk: a stacked item (lanes 0..15
+// and 16..31 are two strips; each lane tracks its own stack's last row).
+// `ring` holds 128 words per warp: two flush buffers of 64, the upper
+// stack's (or the whole strip's) entries first, the lower stack's at +32.
+// Returns false on abort.
+template <int FORM, int S, class Src>
+__device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<FORM, S>::Track &tr, Src &src,
+                          int TS, long t_start, long t_own, long t_end, bool fresh, long N, uint32_t *save_start,
+                          uint32_t *save_final, uint32_t *ring, int lane, bool stk) {
+  constexpr int U = Geo<S>::U, F = Geo<S>::F;
+  constexpr bool kMasked = FormOf<FORM, S>::kMasked;
+  // ng: 0 on a lane that starts a stack from the free-start row; nr: 0 on
+  // lane 0, which injects the reference (it flows on through every lane)
+  const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u, nr = lane != 0 ? 1u : 0u;
+  const bool tracked = lane == 31 || (stk && lane == 15);
+  const int soff = stk && lane >= 16 ? 32 : 0;
+  const long last_row = (stk && lane < 16 ? 16L : 32L) * S - 1;
+  const int nscan = stk ? 2 : 1;
+  const long mask_end = fresh ? t_start + 32L * S : t_start;
+  const long k_first = t_start / TS;
+  const int K = static_cast<int>((t_end + TS - 1) / TS - k_first);
+  int fl = 0, buf = 0;
+  long tflush = t_start;
+  for (int k = 0; k < K; ++k) {
+    const uint32_t *tile = src.acquire(k);
+    if (!tile) return false;
+    const long tk0 = (k_first + k) * TS;
+    const long lo = tk0 > t_start ? tk0 : t_start;
+    const long hi = tk0 + TS < t_end ? tk0 + TS : t_end;
+    for (long t0 = lo; t0 < hi; t0 += U) {
+      if (save_start && t0 == t_own) st.save(save_start, lane);
+      uint32_t *rg = ring + buf * 64 + soff;
+      const uint32_t *ref = tile + (t0 - tk0);
+      if (kMasked && t0 < mask_end)
+        st.template chunk<true>(ref, static_cast<int>(t0 - t_start), lane, rg, fl * U, ng, nr, tracked);
+      else
+        st.template chunk<false>(ref, 0, lane, rg, fl * U, ng, nr, tracked);
+      if (++fl == F || t0 + U >= t_end) {
+        __syncwarp();
+        for (int r = 0; r < nscan; ++r) {  // entry j = step tflush + j of this lane's stack
+          const int j = stk ? (lane & 15) + 16 * r : lane;
+          if (j < fl * U) {
+            const long t = tflush + j;
+            const long c = t - last_row;
+            if (t >= t_own && c >= 0 && c < N) tr.add(rg[j], c);
+          }
+        }
+        tflush += static_cast<long>(fl) * U;
+        fl = 0;
+        buf ^= 1;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) src.release(k);
+  }
+  if (save_final) st.save(save_final, lane);
+  return true;
+}
+
+// Speculative sweep of one unit (item, segment) in the sweep kernel.
+template <int FORM, int S>
+__device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, int item, uint32_t *ring,
+                           int lane) {
+  typename FormOf<FORM, S>::Strip st;
+  typename FormOf<FORM, S>::Track tr;
+  st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
+  st.fresh();
+  long t_start, t_own, t_end;
+  seg_bounds(S, g.nseg, g.seg, A.N, &t_start, &t_own, &t_end);
+  uint32_t *ss = nullptr, *sf = nullptr;
+  const size_t unit = static_cast<size_t>(item) * A.nseg_cap + g.seg;
+  if (g.seg > 0) ss = A.states + (unit * 2 + 0) * kStateStride;
+  if (g.seg + 1 < g.nseg) sf = A.states + (unit * 2 + 1) * kStateStride;
+  const bool stk = A.items[item].stacked != 0;
+  const bool ok =
+      run_steps<FORM, S>(st, tr, ts, ts.tile_cols, t_start, t_own, t_end, true, A.N, ss, sf, ring, lane, stk);
+  tr.reduce(stk ? 16 : 32);
+  if (ok && lane == 0) tr.store(A.bests + unit);
+  if (ok && stk && lane == 16) tr.store(A.bests2 + unit);
+}
+
+template <int PREC, int S>
+__device__ __forceinline__ void sweep_any(const SdtwArgs &A, TileStream &ts, const Group &g, int item,
+                                          uint32_t *ring, int lane) {
+  if constexpr (PREC == HARU_FP32) {
+    sweep_unit<kFormF32, S>(A, ts, g, item, ring, lane);
+  } else {
+    if (A.items[item].kind == kItemExact)
+      sweep_unit<kFormExact, S>(A, ts, g, item, ring, lane);
+    else
+      sweep_unit<kFormI16, S>(A, ts, g, item, ring, lane);
+  }
+}
+
+// Strip heights of one kernel class: registers are allocated for the
+// tallest strip a kernel can meet, so short strips get their own kernels.
+template <int CLS>
+struct Cls;
+template <> struct Cls<0> { static constexpr int lo = 13, hi = 16; };
+template <> struct Cls<1> { static constexpr int lo = 9, hi = 12; };
+template <> struct Cls<2> { static constexpr int lo = 5, hi = 8; };
+template <> struct Cls<3> { static constexpr int lo = 1, hi = 4; };
+// One kernel for every strip height (a single longest-first queue), planned into slot 0.
+template <> struct Cls<4> { static constexpr int lo = 1, hi = 16; };
+template <int CLS> constexpr int slot_of() { return CLS == 4 ? 0 : CLS; }
+
+template <int PREC, int CLS, int S = Cls<CLS>::lo>
+__device__ __forceinline__ void dispatch_sweep(int s, const SdtwArgs &A, TileStream &ts, const Group &g, int item,
+                                               uint32_t *ring, int lane) {
+  if constexpr (S <= Cls<CLS>::hi) {
+    if (s == S)
+      sweep_any<PREC, S>(A, ts, g, item, ring, lane);
+    else
+      dispatch_sweep<PREC, CLS, S + 1>(s, A, ts, g, item, ring, lane);
+  }
+}
+
+// Two CTAs (16 warps) per SM for strips up to 12 rows per lane; kernels that
+// run strips of 13..16 rows need more registers than that allows without
+// spilling (a 168-register cap, for 12 warps per SM, measured ~20% slower).
+template <int PREC, int CLS>
+__global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kernel(SdtwArgs A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  Shared *sh = reinterpret_cast<Shared *>(smem);
+  uint32_t *rings = reinterpret_cast<uint32_t *>(smem + 128);
+  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * 128 * 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(&sh->full[0], 1);
+    mbar_init(&sh->full[1], 1);
+    sh->cnt[0] = sh->cnt[1] = 0;
+    sh->uses[0] = sh->uses[1] = 0;
+    sh->tile_base = 0;
+    sh->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int first = A.ints[kIntClassFirst + slot_of<CLS>()];
+  const int count = A.ints[kIntClassCount + slot_of<CLS>()];
+  int *queue = A.ints + kIntQueues + slot_of<CLS>();
+  for (;;) {
+    if (threadIdx.x == 0) sh->group = atomicAdd(queue, 1);
+    __syncthreads();
+    const int gi = sh->group;
+    if (gi >= count || sh->abort) break;
+    const Group grp = A.groups[first + gi];
+    const int S = grp.S;
+    const int TS = tile_width(S, A.tile_cols);
+    long t_start, t_own, t_end;
+    seg_bounds(S, grp.nseg, grp.seg, A.N, &t_start, &t_own, &t_end);
+    TileStream ts;
+    ts.sh = sh;
+    ts.slots = slots;
+    ts.src = reinterpret_cast<const char *>(A.ref_img);
+    ts.tile_cols = TS;
+    ts.k_first = static_cast<int>(t_start / TS);
+    ts.K = static_cast<int>((t_end + TS - 1) / TS - t_start / TS);
+    ts.n_active = grp.count;
+    ts.wait_ns = A.wait_ns;
+    ts.status = A.ints + kIntStatus;
+    if (threadIdx.x == 0) {
+      ts.issue(0);
+      if (ts.K > 1) ts.issue(1);
+    }
+    __syncthreads();
+    if (warp < grp.count) dispatch_sweep<PREC, CLS>(S, A, ts, grp, grp.first + warp, rings + warp * 128, lane);
+    __syncthreads();
+    if (threadIdx.x == 0) sh->tile_base += ts.K;
+  }
+  // On abort, wait (bounded) for this CTA's copies still in flight before exit.
+  __syncthreads();
+  if (threadIdx.x == 0 && sh->abort) {
+    const unsigned long long dl = now_ns() + A.wait_ns;
+    for (int s = 0; s < 2; ++s)
+      if (sh->uses[s] > 0) mbar_wait_bounded(&sh->full[s], (sh->uses[s] - 1) & 1, dl);
+  }
+}
+
+// --------------------------------------------------------------- fix-up --
+// One warp per item: verify every segment boundary, recompute segments whose
+// speculative start state differs from the exact one, combine the segments'
+// last-row minima (smallest cost, then smallest column) and write the
+// outputs.
+// Segment minima combine in segment order: the smaller cost wins, and on a
+// tie the earlier segment's (smaller) column stays.
+template <int FORM>
+__device__ __forceinline__ void combine(Best &b, const Best &o) {
+  if (FORM == kFormI16) {
+    if (o.ia < b.ia) { b.ia = o.ia; b.ca = o.ca; }
+    if (o.ib < b.ib) { b.ib = o.ib; b.cb = o.cb; }
+  } else {
+    if (o.f < b.f) { b.f = o.f; b.ca = o.ca; }
+  }
+}
+
+template <int FORM>
+__device__ __forceinline__ void write_out(const SdtwArgs &A, const Best &b, int qa, int qb) {
+  if (qa < 0) return;
+  if (FORM == kFormI16) {
+    A.out_cost[qa] = static_cast<float>(b.ia) * A.inv_scale;
+    A.out_col[qa] = b.ca;
+    if (qb >= 0) {
+      A.out_cost[qb] = static_cast<float>(b.ib) * A.inv_scale;
+      A.out_col[qb] = b.cb;
+    }
+  } else if (FORM == kFormExact) {
+    A.out_cost[qa] = b.f * A.inv_scale;
+    A.out_col[qa] = b.ca;
+  } else {
+    A.out_cost[qa] = b.f;
+    A.out_col[qa] = b.ca;
+  }
+}
+
+template <int FORM, int S>
+__device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane) {
+  const Item it = A.items[item];
+  const int nseg = it.nseg;
+  const bool stk = it.stacked != 0;
+  const size_t base = static_cast<size_t>(item) * A.nseg_cap;
+  Best b = A.bests[base];
+  Best b2 = stk ? A.bests2[base] : b;
+  if (nseg > 1) {
+    typename FormOf<FORM, S>::Strip st;
+    st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
+    const int TS = tile_width(S, A.tile_cols);
+    const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u;
+    for (int s = 1; s < nseg; ++s) {
+      const uint32_t *exact = A.states + ((base + s - 1) * 2 + 1) * kStateStride;
+      const uint32_t *spec = A.states + ((base + s) * 2 + 0) * kStateStride;
+      bool eq = true;
+      for (int k = 0; k < 2 * S; ++k) eq = eq && exact[k * 32 + lane] == spec[k * 32 + lane];
+      if (!__all_sync(kFull, eq)) {
+        long t_start, t_own, t_end;
+        seg_bounds(S, nseg, s, A.N, &t_start, &t_own, &t_end);
+        st.restore(exact, reinterpret_cast<const uint32_t *>(A.ref_img), t_own, lane, ng);
+        typename FormOf<FORM, S>::Track tr;
+        GlobalTiles src{reinterpret_cast<const uint32_t *>(A.ref_img), TS, t_own / TS};
+        uint32_t *sf = s + 1 < nseg ? A.states + ((base + s) * 2 + 1) * kStateStride : nullptr;
+        run_steps<FORM, S>(st, tr, src, TS, t_own, t_own, t_end, false, A.N, nullptr, sf, ring, lane, stk);
+        tr.reduce(stk ? 16 : 32);
+        if (lane == 0) {
+          tr.store(A.bests + base + s);
+          atomicAdd(A.ints + kIntFixups, 1);
+        }
+        if (stk && lane == 16) tr.store(A.bests2 + base + s);
+        __syncwarp();
+      }
+      combine<FORM>(b, A.bests[base + s]);
+      if (stk) combine<FORM>(b2, A.bests2[base + s]);
+    }
+  }
+  if (lane == 0) {
+    write_out<FORM>(A, b, it.qa, it.qb);
+    if (stk) write_out<FORM>(A, b2, it.qc, it.qd);
+  }
+}
+
+template <int PREC, int S>
+__device__ __forceinline__ void fixup_any(const SdtwArgs &A, int item, uint32_t *ring, int lane) {
+  if constexpr (PREC == HARU_FP32) {
+    fixup_item<kFormF32, S>(A, item, ring, lane);
+  } else {
+    if (A.items[item].kind == kItemExact)
+      fixup_item<kFormExact, S>(A, item, ring, lane);
+    else
+      fixup_item<kFormI16, S>(A, item, ring, lane);
+  }
+}
+
+template <int PREC, int CLS, int S = Cls<CLS>::lo>
+__device__ __forceinline__ void dispatch_fixup(int s, const SdtwArgs &A, int item, uint32_t *ring, int lane) {
+  if constexpr (S <= Cls<CLS>::hi) {
+    if (s == S)
+      fixup_any<PREC, S>(A, item, ring, lane);
+    else
+      dispatch_fixup<PREC, CLS, S + 1>(s, A, item, ring, lane);
+  }
+}
+
+constexpr int kFixWarps = 4;
+
+template <int PREC, int CLS>
+__global__ void __launch_bounds__(kFixWarps * 32) fixup_kernel(SdtwArgs A) {
+  __shared__ uint32_t rings[kFixWarps * 128];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int first = A.ints[kIntClassItemFirst + slot_of<CLS>()];
+  const int count = A.ints[kIntClassItemCount + slot_of<CLS>()];
+  const int i = blockIdx.x * kFixWarps + warp;
+  if (i >= count) return;
+  const int item = first + i;
+  dispatch_fixup<PREC, CLS>(A.items[item].S, A, item, rings + warp * 128, lane);
+}
+
+template <int PREC, int CLS>
+cudaError_t launch_sweep_cls(const SdtwArgs &a, int grid, cudaStream_t s) {
+  const size_t sm = sdtw_smem_bytes(a.tile_cols, a.warps);
+  cudaError_t e = cudaFuncSetAttribute(sdtw_kernel<PREC, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  sdtw_kernel<PREC, CLS><<<grid, a.warps * 32, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC, int CLS>
+cudaError_t launch_fixup_cls(const SdtwArgs &a, int fix_items, cudaStream_t s) {
+  if (fix_items <= 0) return cudaSuccess;
+  fixup_kernel<PREC, CLS><<<(fix_items + kFixWarps - 1) / kFixWarps, kFixWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC, int CLS>
+int occupancy_cls(int tile_cols, int warps) {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sdtw_kernel<PREC, CLS>, warps * 32,
+                                                sdtw_smem_bytes(tile_cols, warps));
+  return n;
+}
+
+}  // namespace
+}  // namespace haru
+
+// Define the entry points of the sweep kernel (launch, occupancy) or of the
+// segment fix-up kernel for precision P (0 FP32, 1 INT16) and strip-height
+// class C; one per translation unit, so the kernels compile in parallel.
+#define HARU_SDTW_SWEEP_INSTANCE(P, C)                                                         \
+  namespace haru {                                                                             \
+  cudaError_t sdtw_sweep_##P##_##C(const SdtwArgs &a, int grid, cudaStream_t s) {             \
+    return launch_sweep_cls<P, C>(a, grid, s);                                                 \
+  }                                                                                            \
+  int sdtw_occupancy_##P##_##C(int tile_cols, int warps) { return occupancy_cls<P, C>(tile_cols, warps); } \
+  }
+#define HARU_SDTW_FIXUP_INSTANCE(P, C)                                                         \
+  namespace haru {                                                                             \
+  cudaError_t sdtw_fixup_##P##_##C(const SdtwArgs &a, int fix_items, cudaStream_t s) {        \
+    return launch_fixup_cls<P, C>(a, fix_items, s);                                            \
+  }                                                                                            \
+  }

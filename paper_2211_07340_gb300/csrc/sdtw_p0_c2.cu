@@ -1,0 +1,4 @@
+// FP32 sweep kernel, strip-height class 2 (S 5..8).
+#include "sdtw_kernels.cuh"
+
+HARU_SDTW_SWEEP_INSTANCE(0, 2)

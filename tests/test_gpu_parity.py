@@ -68,8 +68,8 @@ def test_sars_32x250_both_forms(haru, sars):
     assert (np.abs(j32[on] - qs.truth_end[on]) <= 8).mean() >= 0.9
 
 
-@pytest.mark.parametrize("tile,warps", [(2048, 8), (4096, 4), (16384, 2)])
-def test_ragged_sizes_span_tiles(haru, tile, warps):
+@pytest.mark.parametrize("tile,warps,stack", [(2048, 8, 1), (4096, 4, -1), (16384, 2, 1), (4096, 8, -1)])
+def test_ragged_sizes_span_tiles(haru, tile, warps, stack):
     rng = np.random.default_rng(tile + warps)
     N = 9_001  # several tiles plus a ragged tail
     ref = synth.random_signal(N, seed=5)
@@ -78,7 +78,7 @@ def test_ragged_sizes_span_tiles(haru, tile, warps):
     off = offsets_of(lengths)
     # queries given as z-values (a 1-event query has no z-score of its own)
     ev = synth.random_signal(int(off[-1]), seed=6, scale=1.0, loc=0.0)
-    with haru.Context(tile_cols=tile, warps_per_cta=warps) as ctx:
+    with haru.Context(tile_cols=tile, warps_per_cta=warps, stack_short=stack) as ctx:
         ctx.ref_load(ref)
         c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off, raw=False)
         c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev, off, raw=False)
@@ -88,7 +88,7 @@ def test_ragged_sizes_span_tiles(haru, tile, warps):
     lengths = [m for m in lengths if m >= 2]
     off = offsets_of(lengths)
     ev = synth.random_signal(int(off[-1]), seed=7)
-    with haru.Context(tile_cols=tile, warps_per_cta=warps) as ctx:
+    with haru.Context(tile_cols=tile, warps_per_cta=warps, stack_short=stack) as ctx:
         ctx.ref_load(ref)
         c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off)
         c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev, off)
@@ -311,3 +311,28 @@ def test_int16_saturation_extremes(haru, units):
     o = compare_int16(c16, j16, ref, ev, off, normalize_ref=False, normalize_q=False)
     capped = o.icost >= oracle.cap()
     assert capped.sum() >= 10 and (~capped).sum() >= 10
+
+
+@pytest.mark.parametrize("units", [1, 4096])
+def test_stacked_strips_are_identical(haru, sars, units):
+    """Short queries stacked two to a warp strip (lanes 0-15 and 16-31) give
+    the unstacked results bit for bit, for both forms, with and without
+    reference segments; a sample matches the oracle."""
+    _, ref = sars
+    qs = synth.workload("sars_uneven_8192", nq=701).queries
+    out, items = {}, {}
+    for stack in (-1, 1):
+        with haru.Context(stack_short=stack, units_target=units) as ctx:
+            ctx.ref_load(ref)
+            out[stack] = [ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)]
+            items[stack] = ctx.last_stats()["items"]
+            out[stack].append(ctx.sdtw_batch(haru.HARU_FP32, qs.events, qs.offsets))
+            if units > 1:
+                assert ctx.last_stats()["max_segments"] > 1
+    assert items[1] < items[-1]  # four short queries per stacked int16 item, two per plain one
+    for p in range(2):
+        np.testing.assert_array_equal(out[1][p][0], out[-1][p][0])
+        np.testing.assert_array_equal(out[1][p][1], out[-1][p][1])
+    idx = np.flatnonzero(qs.lengths <= 256)[::23]
+    compare_int16(out[1][0][0], out[1][0][1], ref, qs.events, qs.offsets, idx=idx)
+    compare_fp32(out[1][1][0], out[1][1][1], ref, qs.events, qs.offsets, idx=idx)
