@@ -25,7 +25,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-PREC_F32, PREC_I16, PREC_F64 = 0, 1, 2
+PREC_F32, PREC_I16, PREC_F64, PREC_I32 = 0, 1, 2, 3  # PREC_I32: int16 inputs, 32-bit accumulation
 
 
 def build(force: bool = False) -> str:
@@ -63,6 +63,8 @@ def _load():
         lib.oracle_sdtw_roll_f32.restype = None
         lib.oracle_sdtw_roll_i16.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P]
         lib.oracle_sdtw_roll_i16.restype = None
+        lib.oracle_sdtw_roll_i32.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P]
+        lib.oracle_sdtw_roll_i32.restype = None
         lib.oracle_batch.argtypes = [ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int, P, P, ctypes.c_uint32,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
         lib.oracle_batch.restype = ctypes.c_int
@@ -151,6 +153,15 @@ def sdtw_roll_f32(x, y):
     return c.value, j.value
 
 
+def sdtw_roll_i32(x, y):
+    """int16 inputs, wide (exact) accumulation: the unsaturated integer DP."""
+    x = np.ascontiguousarray(x, dtype=np.int16)
+    y = np.ascontiguousarray(y, dtype=np.int16)
+    c, j = ctypes.c_int64(), ctypes.c_long()
+    _load().oracle_sdtw_roll_i32(_p(x), x.shape[0], _p(y), y.shape[0], ctypes.byref(c), ctypes.byref(j))
+    return c.value, j.value
+
+
 def sdtw_roll_i16(x, y):
     x = np.ascontiguousarray(x, dtype=np.int16)
     y = np.ascontiguousarray(y, dtype=np.int16)
@@ -166,7 +177,7 @@ class BatchResult:
 
 def batch(prec: int, ref, events, offsets, scale_log2: int = 6, normalize_ref: bool = True,
           normalize_q: bool = True, threads: int = 0) -> BatchResult:
-    """The whole path on the CPU: z-score, quantise (int16), Algorithm 2 per query."""
+    """The whole path on the CPU: z-score, quantise (integer forms), Algorithm 2 per query."""
     ref = np.ascontiguousarray(ref, dtype=np.float32)
     events = np.ascontiguousarray(events, dtype=np.float32)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
@@ -182,4 +193,4 @@ def batch(prec: int, ref, events, offsets, scale_log2: int = 6, normalize_ref: b
                              ctypes.byref(bad))
     if r != 0:
         raise ValueError(f"invalid input (query {bad.value})")
-    return BatchResult(cost, col, ru if prec == PREC_F64 else None, ic if prec == PREC_I16 else None)
+    return BatchResult(cost, col, ru if prec == PREC_F64 else None, ic if prec in (PREC_I16, PREC_I32) else None)

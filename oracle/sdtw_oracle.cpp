@@ -271,11 +271,41 @@ void oracle_sdtw_roll_i16(const int16_t *x, int M, const int16_t *y, long N, int
   *col = pos;
 }
 
+// int16 inputs with wide accumulation (the PE of Section 4.3: 16-bit
+// fixed-point samples, 32-bit cost registers): the exact integer DP, no
+// saturation. Accumulated in 64 bits here; for M <= 512 every value is below
+// 512 * 4094 < 2^31, so a 32-bit accumulator gives the same numbers.
+void oracle_sdtw_roll_i32(const int16_t *x, int M, const int16_t *y, long N, int64_t *cost, long *col) {
+  const int64_t kInf = (int64_t)1 << 60;
+  std::vector<int64_t> C((size_t)M + 1, kInf);
+  C[0] = 0;
+  int64_t score = kInf;
+  long pos = -1;
+  for (long j = 0; j < N; ++j) {
+    int64_t nw = C[0];
+    for (int i = 1; i <= M; ++i) {
+      int64_t w = C[i];
+      int64_t d = std::abs((int64_t)x[i - 1] - (int64_t)y[j]);
+      int64_t m = C[i - 1] < nw ? C[i - 1] : nw;
+      m = m < w ? m : w;
+      nw = w;
+      C[i] = m >= kInf ? kInf : d + m;
+    }
+    if (C[M] < score) {
+      score = C[M];
+      pos = j;
+    }
+  }
+  *cost = score;
+  *col = pos;
+}
+
 // ------------------------------------------------------------------ batch --
 // The whole path as the library exposes it: z-score the reference and each
 // query (when asked), quantise for the int16 form, run Algorithm 2 per query.
 // prec: 0 = FP32, 1 = int16 (saturating), 2 = FP64 (inputs are the FP32
-// z-values widened). cost is reported in z units (int16: integer / 2^k).
+// z-values widened), 3 = int16 inputs with 32-bit accumulation (no
+// saturation). cost is reported in z units (integer forms: integer / 2^k).
 // Queries are spread over `threads` worker threads (0 = hardware count).
 // Returns 0, or -1 on invalid input (first offending query in *bad).
 int oracle_batch(int prec, const float *ref, size_t N, int normalize_ref, const float *events,
@@ -290,7 +320,7 @@ int oracle_batch(int prec, const float *ref, size_t N, int normalize_ref, const 
   }
   std::vector<int16_t> rq;
   std::vector<double> rd;
-  if (prec == 1) {
+  if (prec == 1 || prec == 3) {
     rq.resize(N);
     oracle_quantise(rz.data(), N, scale_log2, rq.data());
   }
@@ -339,6 +369,13 @@ int oracle_batch(int prec, const float *ref, size_t N, int normalize_ref, const 
         oracle_sdtw_roll_i16(qq.data(), M, rq.data(), (long)N, &v, &c);
         cost[q] = (double)v / s;
         if (icost) icost[q] = v;
+      } else if (prec == 3) {
+        qq.resize((size_t)M);
+        oracle_quantise(qz.data(), (size_t)M, scale_log2, qq.data());
+        int64_t v;
+        oracle_sdtw_roll_i32(qq.data(), M, rq.data(), (long)N, &v, &c);
+        cost[q] = (double)v / s;
+        if (icost) icost[q] = (int32_t)v;
       } else {
         qd.resize((size_t)M);
         for (int i = 0; i < M; ++i) qd[(size_t)i] = (double)qz[(size_t)i];

@@ -62,6 +62,7 @@ def test_brute_force_all_forms(case):
     xi, yi = x.astype(np.int16), y.astype(np.int16)
     assert oracle.sdtw_full_i16(xi, yi) == (c, j)
     assert oracle.sdtw_roll_i16(xi, yi) == (c, j)
+    assert oracle.sdtw_roll_i32(xi, yi) == (c, j)
 
 
 def test_brute_force_continuous_values():
@@ -212,6 +213,34 @@ def test_int16_is_capped_exact_integer_dp():
     assert hit > 0
 
 
+def test_wide_accumulation_is_unsaturated():
+    """int16 inputs with 32-bit accumulation (Section 4.3's PE) equal the
+    brute-force minimum over every warping path even where that minimum is
+    above CAP (8 cells of |2047 - (-2047)| = 32,752 > 28,673), where the
+    saturating form reports CAP; and in general min(CAP, wide) = saturating."""
+    x = np.full(8, 2047, dtype=np.int16)
+    y = np.array([-2047] * 8, dtype=np.int16)
+    c, j = brute_force(list(x.astype(np.int64)), list(y.astype(np.int64)))
+    assert c == 8 * 4094 > oracle.cap()
+    assert oracle.sdtw_roll_i32(x, y) == (c, j)
+    assert oracle.sdtw_roll_i16(x, y) == (oracle.cap(), 0)
+    rng = np.random.default_rng(16)
+    for _ in range(6):
+        M, N = int(rng.integers(1, 8)), int(rng.integers(8, 9))
+        xi = rng.choice([-2047, 2047, 0, 1000], M).astype(np.int16)
+        yi = rng.choice([-2047, 2047, 5, -999], N).astype(np.int16)
+        assert oracle.sdtw_roll_i32(xi, yi) == brute_force(list(xi.astype(np.int64)), list(yi.astype(np.int64)))
+    for _ in range(10):
+        M, N = int(rng.integers(1, 60)), int(rng.integers(60, 300))
+        xi = rng.integers(-2047, 2048, size=M).astype(np.int16)
+        yi = rng.integers(-2047, 2048, size=N).astype(np.int16)
+        c32, j32 = oracle.sdtw_roll_i32(xi, yi)
+        c16, j16 = oracle.sdtw_roll_i16(xi, yi)
+        assert c16 == min(c32, oracle.cap())
+        if c32 < oracle.cap():
+            assert j16 == j32
+
+
 def test_int16_error_bound_vs_fp64():
     """Each quantised sample is within 0.5/s of its value, so every cell's
     distance moves by at most 1/s; any warping path has at most M + N - 1
@@ -269,10 +298,13 @@ def test_batch_composes_the_steps():
     b16 = oracle.batch(oracle.PREC_I16, ref, ev, off, scale_log2=5, threads=3)
     b32 = oracle.batch(oracle.PREC_F32, ref, ev, off, threads=1)
     b64 = oracle.batch(oracle.PREC_F64, ref, ev, off, threads=2)
+    bw = oracle.batch(oracle.PREC_I32, ref, ev, off, scale_log2=5, threads=2)
     for q in range(9):
         qz = oracle.zscore(ev[off[q]:off[q + 1]])
         ci, ji = oracle.sdtw_roll_i16(oracle.quantise(qz, 5), oracle.quantise(rz, 5))
         assert (b16.icost[q], b16.col[q]) == (ci, ji) and b16.cost[q] == ci / 32.0
+        cw, jw = oracle.sdtw_roll_i32(oracle.quantise(qz, 5), oracle.quantise(rz, 5))
+        assert (bw.icost[q], bw.col[q]) == (cw, jw) and bw.cost[q] == cw / 32.0
         assert (b32.cost[q], b32.col[q]) == oracle.sdtw_roll_f32(qz, rz)
         assert (b64.cost[q], b64.col[q]) == oracle.sdtw_roll_f64(qz.astype(np.float64), rz.astype(np.float64))[:2]
     with pytest.raises(ValueError):
