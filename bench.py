@@ -165,6 +165,57 @@ def cpu_baseline(ref, queries, target_s: float = 12.0, prec=None):
                       f"{dt:.1f} s"}
 
 
+def ref_sweep(haru, args, dev):
+    """Reference-length sweep: the same 512 x 250 query shape against the
+    SARS-CoV-2-sized (59,796 columns), RFC1-sized (257,820) and 5 Mb (~10M)
+    references, every form, with the oracle on the host cores beside each
+    (the paper's speed-up-versus-reference-length experiment)."""
+    import oracle
+    import torch
+    forms = [("int16", haru.HARU_INT16), ("fp32", haru.HARU_FP32), ("int16_acc32", haru.HARU_INT16_ACC32)]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    rows = []
+    for name, nq in (("sars_4096x250", 512), ("rfc1_512x250", None), ("long_512x250", None)):
+        w = synth.workload(name, nq=nq)
+        q = w.queries
+        with haru.Context(dev.index) as ctx:
+            ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
+            N = ctx.ref_length
+            cells = float(q.lengths.sum()) * N
+            ev_d = torch.from_numpy(q.events).to(dev)
+            off_d = torch.from_numpy(q.offsets.astype(np.int32)).to(dev)
+            cost_d = torch.empty(q.nq, dtype=torch.float32, device=dev)
+            col_d = torch.empty(q.nq, dtype=torch.int64, device=dev)
+            row = {"workload": name, "reference_len": N, "queries": q.nq, "cells": cells}
+            for fname, prec in forms:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                times = []
+                for rep in range(args.warmup + args.sweep_reps):
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                        e0.record(stream)
+                        ctx.sdtw_batch_device(prec, ev_d, off_d, cost_d, col_d, stream=stream.cuda_stream,
+                                              asynchronous=True)
+                        e1.record(stream)
+                    stream.synchronize()
+                    if ctx.last_status() != haru.HARU_OK:
+                        raise haru.HaruError(ctx.last_status(), "batch")
+                    if rep >= args.warmup:
+                        times.append(e0.elapsed_time(e1))
+                row[fname + "_gcups"] = cells / (statistics.median(times) / 1e3) / 1e9
+                row[fname + "_segments"] = ctx.last_stats()["max_segments"]
+        cpu = cpu_baseline(oracle.ref_levels(w.genome, w.model, w.k), q, target_s=args.sweep_cpu_s)
+        row["cpu_int16_gcups"] = cpu["value"]
+        row["cpu_sample"] = cpu["sample"]
+        row["int16_over_cpu"] = row["int16_gcups"] / cpu["value"]
+        rows.append(row)
+    return {"metric": "sDTW GCUPS vs reference length, 512 x 250 raw-event queries, 1 GB300", "unit": "GCUPS",
+            "data": "synthetic", "rows": rows, "reps": args.sweep_reps, "warmup": args.warmup,
+            "l2": "flushed between batches (512 MiB write)", "cpu_cores": os.cpu_count()}
+
+
 def pick_threshold(costs, on_target):
     """Decision threshold from a labelled held-out set: the cost cut with the
     fewest misclassified queries (accept iff cost <= T); among equally good
@@ -280,13 +331,19 @@ def main():
     ap.add_argument("--fixed-len", type=int, default=0, help="profiling: every query this many events")
     ap.add_argument("--single", type=int, default=-1, help="1: one sweep kernel, 0: four class kernels "
                     "(-1 = library default; the autotuner may change it)")
-    ap.add_argument("--forms", default="int16,fp32", help="forms to time: int16, int16exact, fp32")
+    ap.add_argument("--forms", default="int16,fp32,acc32",
+                    help="forms to time: int16, int16exact (exact-share option), fp32, acc32 (int16 inputs, "
+                         "32-bit accumulation)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the library defaults)")
     ap.add_argument("--workload", default=WORKLOAD, help="sars_uneven_8192 (default) or long_512x250")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="simulated flow-cell run (0 = skip)")
     ap.add_argument("--serve-warm", type=float, default=2.0, help="seconds of serving excluded from latency stats")
     ap.add_argument("--serve-channels", type=int, default=512)
+    ap.add_argument("--ref-sweep", action="store_true",
+                    help="reference-length sweep (59,796 / 257,820 / 9,999,990 columns) instead of the benchmark")
+    ap.add_argument("--sweep-reps", type=int, default=10)
+    ap.add_argument("--sweep-cpu-s", type=float, default=3.0, help="oracle seconds per reference in --ref-sweep")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -304,6 +361,10 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     haru.build_library()
+    if args.ref_sweep:
+        if rank == 0:
+            print(json.dumps(ref_sweep(haru, args, dev)), flush=True)
+        return
 
     # Weak scaling: every rank aligns its own batch (independent seeds).
     w = synth.workload(args.workload, seed=(101 if args.workload == WORKLOAD else 104) + 1000 * rank)
@@ -343,7 +404,8 @@ def main():
         sh = stream.cuda_stream
         ctx.configure(int16_exact_share=exact_share)
         if not args.no_tune:
-            key = "int16_exact_share" if exact_share else ("int16" if prec == haru.HARU_INT16 else "fp32")
+            key = ("int16_exact_share" if exact_share else
+                   {haru.HARU_INT16: "int16", haru.HARU_FP32: "fp32", haru.HARU_INT16_ACC32: "int16_acc32"}[prec])
             tuned[key] = ctx.autotune(prec, ev_d, off_d, raw=True, on_device=True)
         with torch.cuda.stream(stream):
             for _ in range(2):  # allocate the context workspace outside capture
@@ -402,12 +464,15 @@ def main():
     clocks = clocks32 = {}
     graphed = False
     msdpx = sweepdpx = nan
+    msw = sweepw = nan
     if "int16" in forms:
         ms16, sweep16, clocks, graphed = run_form(haru.HARU_INT16)
     if "int16exact" in forms:
         msdpx, sweepdpx, _, _ = run_form(haru.HARU_INT16, exact_share=1)
     if "fp32" in forms:
         ms32, sweep32, clocks32, _ = run_form(haru.HARU_FP32)
+    if "acc32" in forms:
+        msw, sweepw, _, _ = run_form(haru.HARU_INT16_ACC32)
     ctx.configure(int16_exact_share=0)
     if "int16" in tuned:
         ctx.configure(**tuned["int16"])
@@ -437,9 +502,9 @@ def main():
         e2e_ms = 1e3 * float(np.mean(e2e_s))
 
     if dist:
-        t = torch.tensor([ms16, e2e_ms, ms32], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms16, e2e_ms, ms32, msw], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms16, e2e_ms, ms32 = (float(x) for x in t.tolist())
+        ms16, e2e_ms, ms32, msw = (float(x) for x in t.tolist())
     total_cells = cells * world
     value = total_cells / (ms16 / 1e3) / 1e9
     value32 = total_cells / (ms32 / 1e3) / 1e9
@@ -488,6 +553,11 @@ def main():
                                "sweep_gcups": cells / (sweepdpx / 1e3) / 1e9,
                                "note": "int16 with two thirds of the warps on exact-integer FP32 strips"}
                               if msdpx == msdpx else None),
+        "int16_acc32": ({"value": total_cells / (msw / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": msw,
+                         "sweep_gcups": cells / (sweepw / 1e3) / 1e9,
+                         "note": "int16 inputs with 32-bit accumulation (Section 4.3's PE): exact integer costs, "
+                                 "computed exactly in FP32, one query per strip"}
+                        if msw == msw else None),
         "int16_over_fp32": value / value32 if value32 == value32 else None,
         "prep_ms_per_step": ms16 - sweep16,
         "e2e": {"value": e2e_value, "unit": "GCUPS", "ms_per_step": e2e_ms,

@@ -14,12 +14,16 @@
  * indices into the reference as loaded (forward strand first when built by
  * haru_ref_build).
  *
- * Two arithmetic forms:
+ * Three arithmetic forms:
  *   HARU_FP32  plain float: delta = |x - y| rounded once, sums rounded once.
  *   HARU_INT16 the paper's fixed-point idea (Sections 4.1 and 4.3): samples
  *              are quantised to q = clamp(round_half_even(z * 2^k), -2047,
  *              2047) and costs saturate at HARU_INT16_CAP, which also stands
  *              for infinity; the reported cost is the integer cost / 2^k.
+ *   HARU_INT16_ACC32 the same quantised samples with wide (32-bit)
+ *              accumulation, the PE of Section 4.3: the exact integer cost,
+ *              never saturated (every cost of a query of <= 512 events is
+ *              below 2^31), reported as integer / 2^k. Batch calls only.
  *
  * Conventions for every entry point:
  *   - return 0 (HARU_OK) or a negative HARU_E* code; nothing aborts or traps;
@@ -51,6 +55,7 @@ extern "C" {
 
 #define HARU_FP32 0
 #define HARU_INT16 1
+#define HARU_INT16_ACC32 2
 
 #define HARU_INT16_QMAX 2047
 #define HARU_INT16_CAP 28673 /* 32767 - 2 * HARU_INT16_QMAX */
@@ -140,7 +145,7 @@ int haru_ref_read(haru_ctx *ctx, float *z, int16_t *q, size_t n);
 /* Align a batch of queries against the loaded reference (the hot path).
  * events[offsets[q] .. offsets[q+1]) are query q's events, float32;
  * offsets has nq + 1 entries, offsets[0] = 0, non-decreasing.
- * precision: HARU_FP32 or HARU_INT16.
+ * precision: HARU_FP32, HARU_INT16 or HARU_INT16_ACC32.
  * out_cost[q]: the minimum last-row cost (float; int16: integer cost / 2^k,
  *   exact). out_col[q]: its first (smallest) 0-based reference column.
  * flags: HARU_ON_DEVICE (device pointers, work ordered on `stream`, a

@@ -29,6 +29,7 @@ HARU_ETIMEDOUT = -5
 HARU_ECUDA = -6
 HARU_FP32 = 0
 HARU_INT16 = 1
+HARU_INT16_ACC32 = 2  # int16 inputs, wide (32-bit) accumulation: the exact integer cost
 HARU_ON_DEVICE = 1
 HARU_RAW = 2
 HARU_ASYNC = 4

@@ -81,7 +81,7 @@ int ctx_reference(haru_ctx *ctx, int precision, const void **img, long *N, int *
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->sticky) return ctx->sticky;
   if (ctx->N == 0) return HARU_ENOREF;
-  *img = precision == HARU_INT16 ? static_cast<const void *>(ctx->img16) : static_cast<const void *>(ctx->img32);
+  *img = precision != HARU_FP32 ? static_cast<const void *>(ctx->img16) : static_cast<const void *>(ctx->img32);
   *N = static_cast<long>(ctx->N);
   *scale_log2 = ctx->scale_log2;
   *device = ctx->device;
@@ -330,7 +330,7 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   if (!ctx) return HARU_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->sticky) return ctx->sticky;
-  if (precision != HARU_FP32 && precision != HARU_INT16) return HARU_EINVAL;
+  if (precision != HARU_FP32 && precision != HARU_INT16 && precision != HARU_INT16_ACC32) return HARU_EINVAL;
   if (ctx->N == 0) return HARU_ENOREF;
   if (nq == 0) return HARU_OK;
   if (!events || !offsets || !out_cost || !out_col) return HARU_EINVAL;

@@ -30,7 +30,8 @@ cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCf
   // Work units: enough (query x reference segment) units to keep every SM
   // busy to the end; nseg_cap bounds the segments per item for storage.
   const int units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * lc.warps;
-  const size_t items_min = mode == 0 ? nq : (mode == 1 ? (static_cast<size_t>(nq) + 1) / 2 : (3 * static_cast<size_t>(nq)) / 4);
+  const size_t items_min = (mode == 0 || mode == 3) ? nq
+                           : (mode == 1 ? (static_cast<size_t>(nq) + 1) / 2 : (3 * static_cast<size_t>(nq)) / 4);
   int nseg_cap = static_cast<int>(
       std::min<size_t>(kMaxSeg, (static_cast<size_t>(units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
   if (nseg_cap < 1) nseg_cap = 1;
@@ -99,7 +100,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   if ((e = launch_pack(ka, static_cast<uint32_t>(ws.max_items), s)) != cudaSuccess) return e;
 
   SdtwArgs sa;
-  sa.ref_img = precision == HARU_INT16 ? static_cast<const void *>(ref.img16) : static_cast<const void *>(ref.img32);
+  sa.ref_img = precision != HARU_FP32 ? static_cast<const void *>(ref.img16) : static_cast<const void *>(ref.img32);
   sa.N = ref.N;
   sa.img = ws.img;
   sa.items = ws.items;
@@ -121,7 +122,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   // streams are given, else one after the other on s; each is persistent
   // over its own part of the group list, then verifies its segments and
   // writes its queries' results.
-  if (lc.single_kernel) {
+  if (lc.single_kernel || precision == HARU_INT16_ACC32) {  // the wide form has the single kernel only
     int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, kClassAll, lc.tile, lc.warps);
     if (per_sm < 1) per_sm = 1;
     const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));

@@ -43,15 +43,17 @@ struct LaunchCfg {
   unsigned long long wait_ns = 2000000000ull;
 };
 
-// Planner mode of a batch: 0 FP32, 1 int16 pairs, 2 int16 pairs + exact strips.
+// Planner mode of a batch: 0 FP32, 1 int16 pairs, 2 int16 pairs + exact
+// strips, 3 int16 inputs with wide accumulation (one exact strip per query).
 inline int plan_mode(int precision, const LaunchCfg &lc) {
+  if (precision == HARU_INT16_ACC32) return 3;
   return precision == HARU_INT16 ? (lc.int16_mode == 1 ? 1 : 2) : 0;
 }
 
 // Most items a batch of nq queries can make in `mode` (per-bucket rounding
 // included: each strip height has a plain and a stacked bucket).
 inline size_t items_bound(int mode, size_t nq) {
-  if (mode == 0) return nq + kMaxS;
+  if (mode == 0 || mode == 3) return nq + kMaxS;
   if (mode == 1) return (nq + 1) / 2 + 2 * kMaxS;
   return (3 * nq + 3) / 4 + 2 * kMaxS;
 }

@@ -1,0 +1,4 @@
+// INT16_ACC32 (int16 inputs, wide accumulation) segment fix-up kernel, every strip height (1..16).
+#include "sdtw_kernels.cuh"
+
+HARU_SDTW_FIXUP_INSTANCE(2, 4)

@@ -137,7 +137,8 @@ struct PlanArgs {
   const uint32_t *offsets;  // nq + 1
   uint32_t nq;
   long N;
-  int pair;                 // 0: FP32 singles; 1: INT16 pairs; 2: INT16 pairs and exact-FP32 singles (1:2 warps)
+  int pair;                 // 0: FP32 singles; 1: INT16 pairs; 2: INT16 pairs and exact-FP32 singles (1:2 warps);
+                            // 3: exact-integer singles, unsaturated (HARU_INT16_ACC32)
   int warps;                // items per group
   int units_target;         // wanted work units (item x segment) in the batch
   int single;               // 1: every strip height in slot 0 (one kernel, one queue)

@@ -122,9 +122,12 @@ __device__ __forceinline__ int bucket_key(const uint32_t *off, uint32_t q, long 
 // Items of a bucket of n queries. Mode 2 (int16 split over both pipes)
 // repeats the pattern [pair, exact, exact] over runs of four queries, so a
 // group's warps mix the DPX pairs and the exact-FP32 singles 1:2.
-__device__ __forceinline__ int stacked_items(int mode, int n) { return mode == 0 ? (n + 1) / 2 : (n + 3) / 4; }
+// Modes 0 (FP32) and 3 (int16 inputs, wide accumulation) make one item per
+// query (two per stacked item); modes 1 and 2 pair int16 queries.
+__device__ __forceinline__ bool singles(int mode) { return mode == 0 || mode == 3; }
+__device__ __forceinline__ int stacked_items(int mode, int n) { return singles(mode) ? (n + 1) / 2 : (n + 3) / 4; }
 __device__ __forceinline__ int bucket_items(int mode, int n) {
-  if (mode == 0) return n;
+  if (singles(mode)) return n;
   if (mode == 1) return (n + 1) / 2;
   const int r = n % 4;
   return 3 * (n / 4) + (r == 0 ? 0 : (r == 3 ? 2 : 1));
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
   for (int i = tid; i < n_items; i += blockDim.x) {
     Item it;
     it.qa = -1; it.qb = -1; it.S = 0; it.nseg = 1;
-    it.kind = a.pair == 0 ? kItemF32 : kItemPair;
+    it.kind = a.pair == 0 ? kItemF32 : (a.pair == 3 ? kItemExact : kItemPair);
     it.qc = -1; it.qd = -1; it.stacked = 0;
     a.items[i] = it;
   }
@@ -238,8 +241,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     if (key > kMaxS) {  // stacked: slots qa, qb | qc, qd (INT16) or qa | qc (FP32)
       const int b = key - kMaxS - 1;
       const int pos = wrun[warp][key] + __popc(peers & lt);
-      const int per = a.pair == 0 ? 2 : 4;
-      const int slot = a.pair == 0 ? 2 * (pos % 2) : pos % 4;
+      const int per = singles(a.pair) ? 2 : 4;
+      const int slot = singles(a.pair) ? 2 * (pos % 2) : pos % 4;
       Item *it = &a.items[sbase[b] + pos / per];
       if (slot == 0) { it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b]; it->stacked = 1; }
       else if (slot == 1) it->qb = static_cast<int>(q);
@@ -263,7 +266,8 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         }
       } else {
         Item it;
-        it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b]; it.kind = kItemF32;
+        it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b];
+        it.kind = a.pair == 3 ? kItemExact : kItemF32;
         it.qc = -1; it.qd = -1; it.stacked = 0;
         a.items[ibase[b] + pos] = it;
       }

@@ -22,6 +22,7 @@ HARU_SDTW_DECLARE(1, 1)
 HARU_SDTW_DECLARE(1, 2)
 HARU_SDTW_DECLARE(1, 3)
 HARU_SDTW_DECLARE(1, 4)
+HARU_SDTW_DECLARE(2, 4)
 
 namespace {
 #define HARU_SDTW_BOTH(P, C)                                                               \
@@ -36,6 +37,10 @@ cudaError_t launch_p1(int cls, const SdtwArgs &a, int grid, int fix_items, cudaS
     case 4: HARU_SDTW_BOTH(1, 4)
     default: HARU_SDTW_BOTH(1, 3)
   }
+}
+cudaError_t launch_p2(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {  // single kernel only
+  cudaError_t e;
+  HARU_SDTW_BOTH(2, 4)
 }
 cudaError_t launch_p0(int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   cudaError_t e;
@@ -54,6 +59,7 @@ size_t sdtw_smem_bytes(int tile_cols, int warps) {
 }
 
 int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
+  if (precision == HARU_INT16_ACC32) return sdtw_occupancy_2_4(tile_cols, warps);
   if (precision == HARU_INT16) {
     switch (cls) {
       case 0: return sdtw_occupancy_1_0(tile_cols, warps);
@@ -75,6 +81,7 @@ int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
 // The sweep kernel of the class, then its segment fix-up kernel (which also
 // writes the outputs), stream-ordered.
 cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
+  if (precision == HARU_INT16_ACC32) return launch_p2(a, grid, fix_items, s);
   return precision == HARU_INT16 ? launch_p1(cls, a, grid, fix_items, s) : launch_p0(cls, a, grid, fix_items, s);
 }
 

@@ -370,11 +370,13 @@ struct TrackF32 {
   }
 };
 
-// Arithmetic forms of a strip: FP32 queries, int16 pairs (DPX), and int16
-// codes computed exactly in FP32. The last two give identical results; an
-// int16 batch runs both side by side so its cells use the half-rate DPX/min
-// pipe and the full-rate FMA pipe at once.
-constexpr int kFormF32 = 0, kFormI16 = 1, kFormExact = 2;
+// Arithmetic forms of a strip: FP32 queries, int16 pairs (DPX), int16
+// codes computed exactly in FP32 and saturated like the int16 form (an int16
+// batch may run both side by side, to use the half-rate DPX/min pipe and the
+// full-rate FMA pipe at once), and int16 codes computed exactly without
+// saturation: wide accumulation (every cost of a query of <= 512 events is
+// an integer below 512 * 4094 < 2^24, so FP32 holds it exactly).
+constexpr int kFormF32 = 0, kFormI16 = 1, kFormExact = 2, kFormExactWide = 3;
 
 template <int FORM, int S>
 struct FormOf;
@@ -394,6 +396,12 @@ template <int S>
 struct FormOf<kFormExact, S> {
   using Strip = StripF32<S, true>;
   using Track = TrackF32<true>;
+  static constexpr bool kMasked = false;
+};
+template <int S>
+struct FormOf<kFormExactWide, S> {
+  using Strip = StripF32<S, true>;
+  using Track = TrackF32<false>;
   static constexpr bool kMasked = false;
 };
 
@@ -556,6 +564,8 @@ __device__ __forceinline__ void sweep_any(const SdtwArgs &A, TileStream &ts, con
                                           uint32_t *ring, int lane) {
   if constexpr (PREC == HARU_FP32) {
     sweep_unit<kFormF32, S>(A, ts, g, item, ring, lane);
+  } else if constexpr (PREC == HARU_INT16_ACC32) {
+    sweep_unit<kFormExactWide, S>(A, ts, g, item, ring, lane);
   } else {
     if (A.items[item].kind == kItemExact)
       sweep_unit<kFormExact, S>(A, ts, g, item, ring, lane);
@@ -675,7 +685,7 @@ __device__ __forceinline__ void write_out(const SdtwArgs &A, const Best &b, int 
       A.out_cost[qb] = static_cast<float>(b.ib) * A.inv_scale;
       A.out_col[qb] = b.cb;
     }
-  } else if (FORM == kFormExact) {
+  } else if (FORM == kFormExact || FORM == kFormExactWide) {
     A.out_cost[qa] = b.f * A.inv_scale;
     A.out_col[qa] = b.ca;
   } else {
@@ -732,6 +742,8 @@ template <int PREC, int S>
 __device__ __forceinline__ void fixup_any(const SdtwArgs &A, int item, uint32_t *ring, int lane) {
   if constexpr (PREC == HARU_FP32) {
     fixup_item<kFormF32, S>(A, item, ring, lane);
+  } else if constexpr (PREC == HARU_INT16_ACC32) {
+    fixup_item<kFormExactWide, S>(A, item, ring, lane);
   } else {
     if (A.items[item].kind == kItemExact)
       fixup_item<kFormExact, S>(A, item, ring, lane);

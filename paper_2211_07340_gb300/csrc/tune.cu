@@ -18,7 +18,8 @@
 extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets,
                              uint32_t nq, uint32_t flags, haru_config *chosen) {
   using namespace haru;
-  if (!ctx || (precision != HARU_FP32 && precision != HARU_INT16) || nq == 0 || !events || !offsets)
+  if (!ctx || (precision != HARU_FP32 && precision != HARU_INT16 && precision != HARU_INT16_ACC32) || nq == 0 ||
+      !events || !offsets)
     return HARU_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->sticky) return ctx->sticky;
@@ -71,6 +72,7 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
   LaunchCfg best = base;
   for (int one : single_c)
   for (int w : warps_c)
+    if (one || precision != HARU_INT16_ACC32)  // the wide form has the single kernel only
     for (int t : tiles_c)
       for (int u : units_c) {
         if (e != cudaSuccess) break;

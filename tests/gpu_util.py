@@ -5,15 +5,16 @@ import oracle
 
 
 def compare_int16(cost, col, ref_levels, events, offsets, scale_log2=6, normalize_ref=True, idx=None,
-                  normalize_q=True):
-    """Bit-exact check of the int16 form against the oracle on queries idx."""
-    from synth import Queries  # noqa: F401
+                  normalize_q=True, prec=None):
+    """Bit-exact check of an integer form (default the saturating int16 one;
+    prec=oracle.PREC_I32 for wide accumulation) against the oracle on queries idx."""
+    prec = oracle.PREC_I16 if prec is None else prec
     q = idx if idx is not None else np.arange(offsets.shape[0] - 1)
     sub_ev, sub_off = _subset(events, offsets, q)
-    o = oracle.batch(oracle.PREC_I16, ref_levels, sub_ev, sub_off, scale_log2=scale_log2,
+    o = oracle.batch(prec, ref_levels, sub_ev, sub_off, scale_log2=scale_log2,
                      normalize_ref=normalize_ref, normalize_q=normalize_q)
-    np.testing.assert_array_equal(col[q], o.col, err_msg="int16 end column")
-    np.testing.assert_array_equal(cost[q].astype(np.float64), o.cost, err_msg="int16 cost")
+    np.testing.assert_array_equal(col[q], o.col, err_msg="integer form end column")
+    np.testing.assert_array_equal(cost[q].astype(np.float64), o.cost, err_msg="integer form cost")
     return o
 
 

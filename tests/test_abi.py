@@ -2,6 +2,7 @@
 include/haru.h declares (no GPU work: nothing here launches a kernel)."""
 import ctypes
 import os
+import re
 import subprocess
 
 import pytest
@@ -53,3 +54,27 @@ def test_header_constants_match_binding():
     for name in ("HARU_INT16_QMAX", "HARU_INT16_CAP", "HARU_MAX_QUERY", "HARU_RAW", "HARU_ON_DEVICE"):
         assert f"#define {name} " in txt
     assert haru.HARU_INT16_CAP == 32767 - 2 * haru.HARU_INT16_QMAX
+    # every numeric #define the binding re-exports has the header's value
+    seen = 0
+    for name, val in re.findall(r"^#define (HARU_[A-Z0-9_]+) \(?(-?\d+)u?\)?", txt, re.M):
+        if hasattr(haru, name):
+            assert getattr(haru, name) == int(val), name
+            seen += 1
+    assert seen >= 12
+    assert (haru.HARU_FP32, haru.HARU_INT16, haru.HARU_INT16_ACC32) == (0, 1, 2)
+
+
+def _struct_fields(txt, name):
+    body = re.search(r"typedef struct \{([^{}]*)\} " + name + ";", txt).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return [re.findall(r"(\w+)\s*(?:\[\d+\])?$", d.strip())[0] for d in body.split(";") if d.strip()]
+
+
+@pytest.mark.parametrize("cname,pyname", [("haru_config", "haru_config"), ("haru_result", "haru_result"),
+                                          ("haru_batch_stats", "haru_batch_stats"),
+                                          ("haru_stream_stats", "haru_stream_stats")])
+def test_struct_layouts_match_header(cname, pyname):
+    """The ctypes mirrors list the header's fields in the header's order."""
+    txt = open(haru.HEADER).read()
+    fields = [f[0] for f in getattr(haru, pyname)._fields_]
+    assert fields == _struct_fields(txt, cname)

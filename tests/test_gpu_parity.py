@@ -336,3 +336,40 @@ def test_stacked_strips_are_identical(haru, sars, units):
     idx = np.flatnonzero(qs.lengths <= 256)[::23]
     compare_int16(out[1][0][0], out[1][0][1], ref, qs.events, qs.offsets, idx=idx)
     compare_fp32(out[1][1][0], out[1][1][1], ref, qs.events, qs.offsets, idx=idx)
+
+
+@pytest.mark.parametrize("stack,units", [(-1, 1), (1, 1), (1, 4096), (-1, 4096)])
+def test_wide_accumulation_form(haru, sars, stack, units):
+    """int16 inputs with wide accumulation (Section 4.3's PE): bit-exact to the
+    oracle's unsaturated integer DP, equal to the saturating int16 form
+    wherever the exact cost is below CAP, identical with and without stacking
+    and reference segments."""
+    _, ref = sars
+    qs = synth.workload("sars_uneven_8192", nq=257).queries
+    with haru.Context(stack_short=stack, units_target=units) as ctx:
+        ctx.ref_load(ref)
+        cw, jw = ctx.sdtw_batch(haru.HARU_INT16_ACC32, qs.events, qs.offsets)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
+    o = compare_int16(cw, jw, ref, qs.events, qs.offsets, prec=oracle.PREC_I32)
+    below = o.icost < oracle.cap()
+    np.testing.assert_array_equal(c16[below], cw[below])
+    np.testing.assert_array_equal(j16[below], jw[below])
+    np.testing.assert_array_equal(c16[~below], oracle.cap() / 64.0)
+
+
+def test_wide_accumulation_above_cap(haru):
+    """Costs far above CAP are reported exactly by the wide form: queries at
+    +2047 against a reference at -2047 with a short run of zeros cost
+    M * 2047 (a vertical path in the first zero column), 34,799 and more."""
+    N = 5000
+    ref = np.full(N, -40.0)
+    ref[2000:2010] = 0.0
+    lens = [512, 480, 300, 100, 17]
+    ev = np.full(sum(lens), 40.0, dtype=np.float32)
+    off = offsets_of(lens)
+    with haru.Context() as ctx:
+        ctx.ref_load(ref, normalize=False)
+        cw, jw = ctx.sdtw_batch(haru.HARU_INT16_ACC32, ev, off, raw=False)
+    o = compare_int16(cw, jw, ref, ev, off, normalize_ref=False, normalize_q=False, prec=oracle.PREC_I32)
+    np.testing.assert_array_equal(o.icost, np.array(lens) * 2047)
+    np.testing.assert_array_equal(jw, 2000)
