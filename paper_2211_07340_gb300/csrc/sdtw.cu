@@ -55,7 +55,8 @@ cudaError_t launch_p0(int cls, const SdtwArgs &a, int grid, int fix_items, cudaS
 }  // namespace
 
 size_t sdtw_smem_bytes(int tile_cols, int warps) {
-  return 128 + static_cast<size_t>(warps) * 128 * 4 + 2 * static_cast<size_t>(tile_cols) * 4;
+  // Shared header, per-warp tracking rings, 32 zero words, two tile slots
+  return 128 + static_cast<size_t>(warps) * 128 * 4 + 32 * 4 + 2 * static_cast<size_t>(tile_cols) * 4;
 }
 
 int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {

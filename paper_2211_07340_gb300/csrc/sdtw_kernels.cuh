@@ -216,8 +216,8 @@ struct StripI16 {
       uint32_t gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
       uint32_t rin = __shfl_up_sync(kFull, Rr[p], 1);
       const uint32_t rv = win.get(ref, u);
-      gup = imad(gup, ng, 0u);                    // a stack's first lane: the free-start row, 0
-      rin = imad(rin, nr, imad(rv, 1u - nr, 0u));  // lane 0: reference sample t
+      gup = imad(gup, ng, 0u);  // a stack's first lane: the free-start row, 0
+      rin = imad(rin, nr, rv);  // lane 0: reference sample t (other lanes read zeros)
       Rr[p] = rin;
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
@@ -421,6 +421,7 @@ struct Shared {
 struct TileStream {
   Shared *sh;
   char *slots;                 // two slots of tile_cols words
+  const uint32_t *zero_words;  // kZeroWords zero words in shared memory
   const char *src;             // reference image
   int tile_cols;               // T_S
   int k_first;                 // first global tile of this group's steps
@@ -449,6 +450,7 @@ struct TileStream {
     }
     return reinterpret_cast<const uint32_t *>(slots + static_cast<size_t>(slot) * tile_cols * 4);
   }
+  __device__ __forceinline__ const uint32_t *zeros() const { return zero_words; }
   __device__ void release(int k) {  // lane 0 of a warp
     const int gk = sh->tile_base + k;
     const int slot = gk & 1;
@@ -462,6 +464,12 @@ struct TileStream {
   }
 };
 
+// Words of zeros that lanes other than lane 0 read in place of the
+// reference window (only lane 0 injects reference samples), so the
+// injection is one multiply-add: rin * (lane != 0) + sample-or-zero.
+constexpr int kZeroWords = 32;
+__device__ __align__(16) const uint32_t kGlobalZeros[kZeroWords] = {0};
+
 // The reference read straight from global memory (the fix-up kernel).
 struct GlobalTiles {
   const uint32_t *img;
@@ -470,6 +478,7 @@ struct GlobalTiles {
   __device__ __forceinline__ const uint32_t *acquire(int k) {
     return img + static_cast<size_t>(k_first + k) * tile_cols;
   }
+  __device__ __forceinline__ const uint32_t *zeros() const { return kGlobalZeros; }
   __device__ __forceinline__ void release(int) {}
 };
 
@@ -501,21 +510,30 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
   const int K = static_cast<int>((t_end + TS - 1) / TS - k_first);
   int fl = 0, buf = 0;
   long tflush = t_start;
+  const uint32_t *zw = src.zeros();
   for (int k = 0; k < K; ++k) {
     const uint32_t *tile = src.acquire(k);
     if (!tile) return false;
+    // This tile's steps [lo, hi), walked in 32-bit offsets from lo.
     const long tk0 = (k_first + k) * TS;
     const long lo = tk0 > t_start ? tk0 : t_start;
     const long hi = tk0 + TS < t_end ? tk0 + TS : t_end;
-    for (long t0 = lo; t0 < hi; t0 += U) {
-      if (save_start && t0 == t_own) st.save(save_start, lane);
+    const int n = static_cast<int>(hi - lo);
+    const int own_at = (save_start && t_own >= lo && t_own < hi) ? static_cast<int>(t_own - lo) : -1;
+    const long mrem = mask_end - lo;
+    const int mask_n = !kMasked || mrem <= 0 ? 0 : (mrem >= n ? n : static_cast<int>(mrem));
+    const bool last_tile = t_end <= tk0 + TS;
+    const int trel0 = static_cast<int>(lo - t_start);
+    const uint32_t *tref = tile + (lo - tk0);
+    for (int o = 0; o < n; o += U) {
+      if (o == own_at) st.save(save_start, lane);
       uint32_t *rg = ring + buf * 64 + soff;
-      const uint32_t *ref = tile + (t0 - tk0);
-      if (kMasked && t0 < mask_end)
-        st.template chunk<true>(ref, static_cast<int>(t0 - t_start), lane, rg, fl * U, ng, nr, tracked);
+      const uint32_t *ref = nr ? zw : tref + o;
+      if (kMasked && o < mask_n)
+        st.template chunk<true>(ref, trel0 + o, lane, rg, fl * U, ng, nr, tracked);
       else
         st.template chunk<false>(ref, 0, lane, rg, fl * U, ng, nr, tracked);
-      if (++fl == F || t0 + U >= t_end) {
+      if (++fl == F || (last_tile && o + U >= n)) {
         __syncwarp();
         for (int r = 0; r < nscan; ++r) {  // entry j = step tflush + j of this lane's stack
           const int j = stk ? (lane & 15) + 16 * r : lane;
@@ -604,8 +622,11 @@ template <int PREC, int CLS>
 __global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kernel(SdtwArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared *sh = reinterpret_cast<Shared *>(smem);
+  // layout: Shared (128 B) | per-warp tracking rings (128 words each) | zero words | two tile slots
   uint32_t *rings = reinterpret_cast<uint32_t *>(smem + 128);
-  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * 128 * 4);
+  uint32_t *zero_words = reinterpret_cast<uint32_t *>(smem + 128 + A.warps * 128 * 4);
+  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * 128 * 4 + kZeroWords * 4);
+  if (threadIdx.x < kZeroWords) zero_words[threadIdx.x] = 0u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(&sh->full[0], 1);
@@ -633,6 +654,7 @@ __global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kern
     TileStream ts;
     ts.sh = sh;
     ts.slots = slots;
+    ts.zero_words = zero_words;
     ts.src = reinterpret_cast<const char *>(A.ref_img);
     ts.tile_cols = TS;
     ts.k_first = static_cast<int>(t_start / TS);
