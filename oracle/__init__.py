@@ -66,7 +66,11 @@ def _load():
         lib.oracle_sdtw_roll_i32.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P]
         lib.oracle_sdtw_roll_i32.restype = None
         lib.oracle_batch.argtypes = [ctypes.c_int, P, ctypes.c_size_t, ctypes.c_int, P, P, ctypes.c_uint32,
-                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
+        lib.oracle_sdtw_span_f32.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P, P]
+        lib.oracle_sdtw_span_f32.restype = None
+        lib.oracle_sdtw_span_i32.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P, P]
+        lib.oracle_sdtw_span_i32.restype = None
         lib.oracle_batch.restype = ctypes.c_int
         lib.oracle_cap.restype = ctypes.c_int
         lib.oracle_qmax.restype = ctypes.c_int
@@ -170,13 +174,33 @@ def sdtw_roll_i16(x, y):
     return c.value, j.value
 
 
+def sdtw_span_f32(x, y):
+    """FP32 DP carrying each path's start column: (cost, end column, start column)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    c, j, s = ctypes.c_float(), ctypes.c_long(), ctypes.c_long()
+    _load().oracle_sdtw_span_f32(_p(x), x.shape[0], _p(y), y.shape[0], ctypes.byref(c), ctypes.byref(j),
+                                 ctypes.byref(s))
+    return c.value, j.value, s.value
+
+
+def sdtw_span_i32(x, y):
+    """Wide-accumulation integer DP carrying each path's start column."""
+    x = np.ascontiguousarray(x, dtype=np.int16)
+    y = np.ascontiguousarray(y, dtype=np.int16)
+    c, j, s = ctypes.c_int64(), ctypes.c_long(), ctypes.c_long()
+    _load().oracle_sdtw_span_i32(_p(x), x.shape[0], _p(y), y.shape[0], ctypes.byref(c), ctypes.byref(j),
+                                 ctypes.byref(s))
+    return c.value, j.value, s.value
+
+
 class BatchResult:
-    def __init__(self, cost, col, runner_up, icost):
-        self.cost, self.col, self.runner_up, self.icost = cost, col, runner_up, icost
+    def __init__(self, cost, col, runner_up, icost, start=None):
+        self.cost, self.col, self.runner_up, self.icost, self.start = cost, col, runner_up, icost, start
 
 
 def batch(prec: int, ref, events, offsets, scale_log2: int = 6, normalize_ref: bool = True,
-          normalize_q: bool = True, threads: int = 0) -> BatchResult:
+          normalize_q: bool = True, threads: int = 0, start: bool = False) -> BatchResult:
     """The whole path on the CPU: z-score, quantise (integer forms), Algorithm 2 per query."""
     ref = np.ascontiguousarray(ref, dtype=np.float32)
     events = np.ascontiguousarray(events, dtype=np.float32)
@@ -186,11 +210,15 @@ def batch(prec: int, ref, events, offsets, scale_log2: int = 6, normalize_ref: b
     col = np.empty(nq, dtype=np.int64)
     ru = np.empty(nq, dtype=np.float64)
     ic = np.zeros(nq, dtype=np.int32)
+    if start and prec not in (PREC_F32, PREC_I32):
+        raise ValueError("start columns: FP32 and wide-accumulation forms only")
+    st = np.full(nq, -1, dtype=np.int64) if start else None
     bad = ctypes.c_long(-1)
     ev = events if events.shape[0] else np.zeros(1, np.float32)
     r = _load().oracle_batch(int(prec), _p(ref), ref.shape[0], int(normalize_ref), _p(ev), _p(offsets), nq,
                              int(normalize_q), int(scale_log2), int(threads), _p(cost), _p(col), _p(ru), _p(ic),
-                             ctypes.byref(bad))
+                             _p(st) if start else None, ctypes.byref(bad))
     if r != 0:
         raise ValueError(f"invalid input (query {bad.value})")
-    return BatchResult(cost, col, ru if prec == PREC_F64 else None, ic if prec in (PREC_I16, PREC_I32) else None)
+    return BatchResult(cost, col, ru if prec == PREC_F64 else None, ic if prec in (PREC_I16, PREC_I32) else None,
+                       st)

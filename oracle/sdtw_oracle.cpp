@@ -40,6 +40,7 @@
 #include <cstring>
 #include <limits>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -300,17 +301,79 @@ void oracle_sdtw_roll_i32(const int16_t *x, int M, const int16_t *y, long N, int
   *col = pos;
 }
 
+// Start column of the alignment (the paper drops backtracking; this carries
+// the start forward instead). Every cell keeps the start of the predecessor
+// that gives its minimum: the up neighbour if it is a minimum, else the
+// diagonal one if it is, else the left one (a fixed preference on equal
+// costs); a path that enters row 1 at column j starts at j. The cost and the
+// end column are those of the plain DP. T: float (FP32 form) or int64_t
+// (int16 inputs, wide accumulation).
+}  // extern "C"
+
+template <class T, class D>
+static void roll_span(const D *x, int M, const D *y, long N, T inf, T *cost, long *col, long *start) {
+  std::vector<T> C((size_t)M + 1, inf);
+  std::vector<long> P((size_t)M + 1, -1);
+  C[0] = 0;
+  T score = inf;
+  long pos = -1, spos = -1;
+  for (long j = 0; j < N; ++j) {
+    T nw = C[0];
+    long nws = j;
+    for (int i = 1; i <= M; ++i) {
+      const T w = C[i];
+      const long ws = P[i];
+      // up: row i-1 of this column; diagonal: row i-1 of the previous one
+      // (row 0 on both: cost 0, and the path starts here, at column j)
+      T mc = i == 1 ? T(0) : C[i - 1];
+      long ms = i == 1 ? j : P[i - 1];
+      const T dc = i == 1 ? T(0) : nw;
+      const long ds = i == 1 ? j : nws;
+      if (dc < mc) { mc = dc; ms = ds; }
+      if (w < mc) { mc = w; ms = ws; }
+      T d;
+      if constexpr (std::is_same<T, float>::value) d = std::fabs(x[i - 1] - y[j]);
+      else d = std::abs((T)x[i - 1] - (T)y[j]);
+      nw = w;
+      nws = ws;
+      C[i] = mc >= inf ? inf : d + mc;
+      P[i] = ms;
+    }
+    if (C[M] < score) {
+      score = C[M];
+      pos = j;
+      spos = P[M];
+    }
+  }
+  *cost = score;
+  *col = pos;
+  *start = spos;
+}
+
+extern "C" {
+
+void oracle_sdtw_span_f32(const float *x, int M, const float *y, long N, float *cost, long *col, long *start) {
+  roll_span<float, float>(x, M, y, N, std::numeric_limits<float>::infinity(), cost, col, start);
+}
+
+void oracle_sdtw_span_i32(const int16_t *x, int M, const int16_t *y, long N, int64_t *cost, long *col,
+                          long *start) {
+  roll_span<int64_t, int16_t>(x, M, y, N, (int64_t)1 << 60, cost, col, start);
+}
+
 // ------------------------------------------------------------------ batch --
 // The whole path as the library exposes it: z-score the reference and each
 // query (when asked), quantise for the int16 form, run Algorithm 2 per query.
 // prec: 0 = FP32, 1 = int16 (saturating), 2 = FP64 (inputs are the FP32
 // z-values widened), 3 = int16 inputs with 32-bit accumulation (no
 // saturation). cost is reported in z units (integer forms: integer / 2^k).
+// start (optional, FP32 and the wide form): the alignment's start column
+// (roll_span); the cost and column are the same as without it.
 // Queries are spread over `threads` worker threads (0 = hardware count).
 // Returns 0, or -1 on invalid input (first offending query in *bad).
 int oracle_batch(int prec, const float *ref, size_t N, int normalize_ref, const float *events,
                  const uint32_t *offsets, uint32_t nq, int normalize_q, int scale_log2, int threads,
-                 double *cost, int64_t *col, double *runner_up, int32_t *icost, long *bad) {
+                 double *cost, int64_t *col, double *runner_up, int32_t *icost, int64_t *start, long *bad) {
   if (N == 0) return -1;
   std::vector<float> rz(N);
   if (normalize_ref) {
@@ -358,7 +421,13 @@ int oracle_batch(int prec, const float *ref, size_t N, int normalize_ref, const 
         std::memcpy(qz.data(), ev, (size_t)M * sizeof(float));
       }
       long c = -1;
-      if (prec == 0) {
+      if (prec == 0 && start) {
+        float f;
+        long st;
+        oracle_sdtw_span_f32(qz.data(), M, rz.data(), (long)N, &f, &c, &st);
+        cost[q] = (double)f;
+        start[q] = (int64_t)st;
+      } else if (prec == 0) {
         float f;
         oracle_sdtw_roll_f32(qz.data(), M, rz.data(), (long)N, &f, &c);
         cost[q] = (double)f;
@@ -373,7 +442,13 @@ int oracle_batch(int prec, const float *ref, size_t N, int normalize_ref, const 
         qq.resize((size_t)M);
         oracle_quantise(qz.data(), (size_t)M, scale_log2, qq.data());
         int64_t v;
-        oracle_sdtw_roll_i32(qq.data(), M, rq.data(), (long)N, &v, &c);
+        if (start) {
+          long st;
+          oracle_sdtw_span_i32(qq.data(), M, rq.data(), (long)N, &v, &c, &st);
+          start[q] = (int64_t)st;
+        } else {
+          oracle_sdtw_roll_i32(qq.data(), M, rq.data(), (long)N, &v, &c);
+        }
         cost[q] = (double)v / s;
         if (icost) icost[q] = (int32_t)v;
       } else {

@@ -241,6 +241,59 @@ def test_wide_accumulation_is_unsaturated():
             assert j16 == j32
 
 
+# ------------------------------------------------------- start column --
+def traceback_start(x, y):
+    """Independent pin for the start column: the whole cost matrix in float64
+    (numpy, Eq. 1), then a traceback from the first minimum of the last row
+    that steps to the up neighbour if it is a minimum predecessor, else the
+    diagonal one, else the left one; the path starts where it enters row 1."""
+    M, N = len(x), len(y)
+    g = np.full((M + 1, N + 1), np.inf)
+    g[0, :] = 0.0
+    for i in range(1, M + 1):
+        for j in range(1, N + 1):
+            g[i, j] = abs(x[i - 1] - y[j - 1]) + min(g[i - 1, j], g[i - 1, j - 1], g[i, j - 1])
+    j = int(np.argmin(g[M, 1:])) + 1
+    cost, end = g[M, j], j - 1
+    i = M
+    while i > 1:
+        up, dg, lf = g[i - 1, j], g[i - 1, j - 1], g[i, j - 1]
+        m = min(up, dg, lf)
+        if up == m:
+            i -= 1
+        elif dg == m:
+            i, j = i - 1, j - 1
+        else:
+            j -= 1
+    return cost, end, j - 1
+
+
+def test_start_column_matches_traceback():
+    rng = np.random.default_rng(17)
+    cases = [(rng.integers(0, 4, int(rng.integers(1, 7))), rng.integers(0, 4, 7)) for _ in range(40)]
+    cases += [(rng.integers(-2047, 2048, int(rng.integers(1, 30))), rng.integers(-2047, 2048, 80)) for _ in range(20)]
+    for x, y in cases:
+        if len(x) > len(y):
+            continue
+        c, e, st = traceback_start(list(x.astype(np.float64)), list(y.astype(np.float64)))
+        assert oracle.sdtw_span_i32(x.astype(np.int16), y.astype(np.int16)) == (c, e, st)
+        assert oracle.sdtw_span_f32(x.astype(np.float32), y.astype(np.float32)) == (c, e, st)
+        # cost and end column are the plain DP's; the start lies on an optimal path (brute force, small cases)
+        assert oracle.sdtw_roll_i32(x.astype(np.int16), y.astype(np.int16)) == (c, e)
+        if len(y) <= 7:
+            bc, bj = brute_force(list(x.astype(np.float64)), list(y.astype(np.float64)))
+            assert (bc, bj) == (c, e) and 0 <= st <= e
+
+
+def test_start_column_of_planted_copies():
+    rng = np.random.default_rng(18)
+    y = rng.normal(size=3000).astype(np.float32)
+    for s0, m, rep in ((0, 50, 1), (1234, 80, 1), (2900, 100, 1), (700, 60, 3)):
+        x = np.repeat(y[s0:s0 + m], rep)  # a dwelled copy: vertical steps cost 0
+        c, e, st = oracle.sdtw_span_f32(x, y)
+        assert (c, e, st) == (0.0, s0 + m - 1, s0)
+
+
 def test_int16_error_bound_vs_fp64():
     """Each quantised sample is within 0.5/s of its value, so every cell's
     distance moves by at most 1/s; any warping path has at most M + N - 1
@@ -299,12 +352,17 @@ def test_batch_composes_the_steps():
     b32 = oracle.batch(oracle.PREC_F32, ref, ev, off, threads=1)
     b64 = oracle.batch(oracle.PREC_F64, ref, ev, off, threads=2)
     bw = oracle.batch(oracle.PREC_I32, ref, ev, off, scale_log2=5, threads=2)
+    bws = oracle.batch(oracle.PREC_I32, ref, ev, off, scale_log2=5, threads=2, start=True)
+    b32s = oracle.batch(oracle.PREC_F32, ref, ev, off, threads=2, start=True)
     for q in range(9):
         qz = oracle.zscore(ev[off[q]:off[q + 1]])
         ci, ji = oracle.sdtw_roll_i16(oracle.quantise(qz, 5), oracle.quantise(rz, 5))
         assert (b16.icost[q], b16.col[q]) == (ci, ji) and b16.cost[q] == ci / 32.0
         cw, jw = oracle.sdtw_roll_i32(oracle.quantise(qz, 5), oracle.quantise(rz, 5))
         assert (bw.icost[q], bw.col[q]) == (cw, jw) and bw.cost[q] == cw / 32.0
+        assert (bws.icost[q], bws.col[q], bws.start[q]) == oracle.sdtw_span_i32(oracle.quantise(qz, 5),
+                                                                               oracle.quantise(rz, 5))
+        assert (b32s.cost[q], b32s.col[q], b32s.start[q]) == oracle.sdtw_span_f32(qz, rz)
         assert (b32.cost[q], b32.col[q]) == oracle.sdtw_roll_f32(qz, rz)
         assert (b64.cost[q], b64.col[q]) == oracle.sdtw_roll_f64(qz.astype(np.float64), rz.astype(np.float64))[:2]
     with pytest.raises(ValueError):
