@@ -157,6 +157,22 @@ int haru_ref_read(haru_ctx *ctx, float *z, int16_t *q, size_t n);
 int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
                     float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);
 
+/* haru_sdtw_batch that also reports where each alignment starts: out_start[q]
+ * (int64, nq) is the 0-based reference column at which the chosen warping
+ * path of query q enters its first row, so the query maps to reference
+ * columns [out_start[q], out_col[q]]. The paper drops backtracking
+ * (Section 4.3); here the start column is carried forward through the DP:
+ * every cell takes the start of its up neighbour if that is a minimum
+ * predecessor, else of its diagonal one, else of its left one (a fixed
+ * preference where costs tie). Costs and end columns equal haru_sdtw_batch's.
+ * precision: HARU_FP32 or HARU_INT16_ACC32 (the packed int16 form has no room
+ * for a start column per cell). Layout, flags, ownership and errors as in
+ * haru_sdtw_batch; out_start is a host pointer, or a device pointer with
+ * HARU_ON_DEVICE. About 2-3x the time of haru_sdtw_batch (more work per
+ * cell), and each query sweeps the reference in one piece. */
+int haru_sdtw_batch_span(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
+                         float *out_cost, int64_t *out_col, int64_t *out_start, uintptr_t stream, uint32_t flags);
+
 /* ---- Serving: continuous batching of Read Until decisions -----------------
  * A persistent request loop inside the context (a worker thread) takes the
  * event chunks of reads as a flow cell delivers them, keeps each admitted

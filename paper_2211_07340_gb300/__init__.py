@@ -99,6 +99,9 @@ _SIGS = {
     "haru_sdtw_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.c_uint32]),
+    "haru_sdtw_batch_span": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_size_t, ctypes.c_uint32]),
     "haru_last_status": (ctypes.c_int, [ctypes.c_void_p]),
     "haru_last_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_batch_stats)]),
     "haru_stream_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
@@ -250,6 +253,21 @@ class Context:
         check(self.sdtw_batch_raw(precision, ev, offsets, nq, cost, col, 0, HARU_RAW if raw else 0),
               "haru_sdtw_batch")
         return cost[:nq], col[:nq]
+
+    def sdtw_batch_span(self, precision: int, events, offsets, raw: bool = True):
+        """haru_sdtw_batch_span with host arrays: (cost float32[nq], end col int64[nq],
+        start col int64[nq]); precision HARU_FP32 or HARU_INT16_ACC32."""
+        events = np.ascontiguousarray(events, dtype=np.float32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+        nq = offsets.shape[0] - 1
+        cost = np.empty(max(nq, 1), dtype=np.float32)
+        col = np.empty(max(nq, 1), dtype=np.int64)
+        start = np.empty(max(nq, 1), dtype=np.int64)
+        ev = events if events.shape[0] else np.zeros(1, np.float32)
+        check(int(lib().haru_sdtw_batch_span(self._h, int(precision), _ptr(ev), _ptr(offsets), int(nq), _ptr(cost),
+                                             _ptr(col), _ptr(start), 0, HARU_RAW if raw else 0)),
+              "haru_sdtw_batch_span")
+        return cost[:nq], col[:nq], start[:nq]
 
     def sdtw_batch_device(self, precision: int, events, offsets, out_cost, out_col, stream: int = 0,
                           raw: bool = True, asynchronous: bool = False, profile: bool = False):

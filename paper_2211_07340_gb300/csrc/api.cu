@@ -191,7 +191,7 @@ void haru_destroy(haru_ctx *ctx) {
   }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   void *ptrs[] = {ctx->ref_z,    ctx->img16,     ctx->img32,  ctx->stats, ctx->partials,
-                  ctx->d_events, ctx->d_offsets, ctx->d_cost, ctx->d_col};
+                  ctx->d_events, ctx->d_offsets, ctx->d_cost, ctx->d_col, ctx->d_start};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   haru::ws_free(ctx->ws);
@@ -325,15 +325,19 @@ int haru_ref_read(haru_ctx *ctx, float *z, int16_t *q, size_t n) {
   return HARU_OK;
 }
 
-int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
-                    float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags) {
-  if (!ctx) return HARU_EINVAL;
+namespace {
+
+// The batch path shared by haru_sdtw_batch and haru_sdtw_batch_span;
+// `precision` is the kernels' (kPrecF32Span / kPrecWideSpan when out_start
+// is wanted).
+int batch_call(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
+               float *out_cost, int64_t *out_col, int64_t *out_start, uintptr_t stream, uint32_t flags) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->sticky) return ctx->sticky;
-  if (precision != HARU_FP32 && precision != HARU_INT16 && precision != HARU_INT16_ACC32) return HARU_EINVAL;
   if (ctx->N == 0) return HARU_ENOREF;
   if (nq == 0) return HARU_OK;
-  if (!events || !offsets || !out_cost || !out_col) return HARU_EINVAL;
+  const bool span = haru::prec_span(precision);
+  if (!events || !offsets || !out_cost || !out_col || (span && !out_start)) return HARU_EINVAL;
   const bool on_dev = flags & HARU_ON_DEVICE;
   const bool async = (flags & HARU_ASYNC) && on_dev;
   const int raw = (flags & HARU_RAW) ? 1 : 0;
@@ -344,6 +348,7 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   const float *d_ev = events;
   float *d_cost = out_cost;
   int64_t *d_col = out_col;
+  int64_t *d_start = out_start;
   if (!on_dev) {
     // Host inputs: validate on the host, then stage on the device.
     const long lim = std::min<long>((long)ctx->N, HARU_MAX_QUERY);
@@ -356,13 +361,14 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
     const size_t ne = offsets[nq];
     HARU_CUDA(grow(&ctx->d_events, &ctx->cap_events, ne));
     if (ctx->cap_q < (size_t)nq + 1) {
-      size_t c0 = 0, c1 = 0, c2 = 0;
-      cudaFree(ctx->d_offsets); cudaFree(ctx->d_cost); cudaFree(ctx->d_col);
-      ctx->d_offsets = nullptr; ctx->d_cost = nullptr; ctx->d_col = nullptr;
+      size_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+      cudaFree(ctx->d_offsets); cudaFree(ctx->d_cost); cudaFree(ctx->d_col); cudaFree(ctx->d_start);
+      ctx->d_offsets = nullptr; ctx->d_cost = nullptr; ctx->d_col = nullptr; ctx->d_start = nullptr;
       ctx->cap_q = 0;
       HARU_CUDA(grow(&ctx->d_offsets, &c0, (size_t)nq + 1));
       HARU_CUDA(grow(&ctx->d_cost, &c1, (size_t)nq + 1));
       HARU_CUDA(grow(&ctx->d_col, &c2, (size_t)nq + 1));
+      HARU_CUDA(grow(&ctx->d_start, &c3, (size_t)nq + 1));
       ctx->cap_q = (size_t)nq + 1;
     }
     HARU_CUDA(cudaMemcpyAsync(ctx->d_events, events, ne * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -372,12 +378,13 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
     d_ev = ctx->d_events;
     d_cost = ctx->d_cost;
     d_col = ctx->d_col;
+    d_start = span ? ctx->d_start : nullptr;
   }
   const haru::LaunchCfg lc = ctx->launch_cfg();
   HARU_CUDA(haru::ws_reserve(ctx->ws, precision, nq, lc));
   const bool prof = flags & HARU_PROFILE;
   HARU_CUDA(haru::ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, d_cost, d_col, lc, s,
-                             &ctx->fj, prof ? ctx->ev[0] : nullptr, prof ? ctx->ev[1] : nullptr));
+                             &ctx->fj, prof ? ctx->ev[0] : nullptr, prof ? ctx->ev[1] : nullptr, d_start));
   if (prof) {
     HARU_CUDA(haru::record_event(ctx->ev[2], s));
     ctx->profiled = true;
@@ -390,12 +397,31 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
   if (!on_dev) {
     HARU_CUDA(cudaMemcpyAsync(out_cost, d_cost, (size_t)nq * sizeof(float), cudaMemcpyDeviceToHost, s));
     HARU_CUDA(cudaMemcpyAsync(out_col, d_col, (size_t)nq * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (span)
+      HARU_CUDA(cudaMemcpyAsync(out_start, d_start, (size_t)nq * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   }
   int st = 0;
   HARU_CUDA(cudaMemcpyAsync(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost, s));
   HARU_CUDA(cudaStreamSynchronize(s));
   ctx->last_status = st;
   return st;
+}
+
+}  // namespace
+
+int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
+                    float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags) {
+  if (!ctx) return HARU_EINVAL;
+  if (precision != HARU_FP32 && precision != HARU_INT16 && precision != HARU_INT16_ACC32) return HARU_EINVAL;
+  return batch_call(ctx, precision, events, offsets, nq, out_cost, out_col, nullptr, stream, flags);
+}
+
+int haru_sdtw_batch_span(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
+                         float *out_cost, int64_t *out_col, int64_t *out_start, uintptr_t stream, uint32_t flags) {
+  if (!ctx) return HARU_EINVAL;
+  if (precision != HARU_FP32 && precision != HARU_INT16_ACC32) return HARU_EINVAL;
+  return batch_call(ctx, precision == HARU_FP32 ? haru::kPrecF32Span : haru::kPrecWideSpan, events, offsets, nq,
+                    out_cost, out_col, out_start, stream, flags);
 }
 
 int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep) {

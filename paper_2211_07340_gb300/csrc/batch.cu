@@ -34,7 +34,7 @@ cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCf
                            : (mode == 1 ? (static_cast<size_t>(nq) + 1) / 2 : (3 * static_cast<size_t>(nq)) / 4);
   int nseg_cap = static_cast<int>(
       std::min<size_t>(kMaxSeg, (static_cast<size_t>(units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
-  if (nseg_cap < 1) nseg_cap = 1;
+  if (nseg_cap < 1 || prec_span(precision)) nseg_cap = 1;  // start-column forms sweep unsegmented
   cudaError_t e = cudaSuccess;
   size_t c = ws.ints ? static_cast<size_t>(kIntWords) : 0;
   if ((e = grow(&ws.ints, &c, kIntWords)) != cudaSuccess) return e;
@@ -65,7 +65,7 @@ cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCf
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
                        const LaunchCfg &lc, cudaStream_t s, const ForkJoin *fj, cudaEvent_t ev_prep,
-                       cudaEvent_t ev_sweep) {
+                       cudaEvent_t ev_sweep, int64_t *d_start) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.ints, 0, kIntWords * sizeof(int), s)) != cudaSuccess) return e;
   if (ev_prep && (e = record_event(ev_prep, s)) != cudaSuccess) return e;
@@ -100,7 +100,8 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   if ((e = launch_pack(ka, static_cast<uint32_t>(ws.max_items), s)) != cudaSuccess) return e;
 
   SdtwArgs sa;
-  sa.ref_img = precision != HARU_FP32 ? static_cast<const void *>(ref.img16) : static_cast<const void *>(ref.img32);
+  const bool fp_ref = precision == HARU_FP32 || precision == kPrecF32Span;
+  sa.ref_img = fp_ref ? static_cast<const void *>(ref.img32) : static_cast<const void *>(ref.img16);
   sa.N = ref.N;
   sa.img = ws.img;
   sa.items = ws.items;
@@ -109,6 +110,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   sa.states = ws.states;
   sa.bests = ws.bests;
   sa.bests2 = ws.bests + ws.max_items * static_cast<size_t>(ws.nseg_cap);
+  sa.out_start = d_start;
   sa.nseg_cap = ws.nseg_cap;
   sa.out_cost = d_cost;
   sa.out_col = d_col;
@@ -122,7 +124,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   // streams are given, else one after the other on s; each is persistent
   // over its own part of the group list, then verifies its segments and
   // writes its queries' results.
-  if (lc.single_kernel || precision == HARU_INT16_ACC32) {  // the wide form has the single kernel only
+  if (lc.single_kernel || precision == HARU_INT16_ACC32 || prec_span(precision)) {  // these have the single kernel only
     int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, kClassAll, lc.tile, lc.warps);
     if (per_sm < 1) per_sm = 1;
     const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));

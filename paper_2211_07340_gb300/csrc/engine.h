@@ -46,7 +46,8 @@ struct LaunchCfg {
 // Planner mode of a batch: 0 FP32, 1 int16 pairs, 2 int16 pairs + exact
 // strips, 3 int16 inputs with wide accumulation (one exact strip per query).
 inline int plan_mode(int precision, const LaunchCfg &lc) {
-  if (precision == HARU_INT16_ACC32) return 3;
+  if (precision == HARU_INT16_ACC32 || precision == kPrecWideSpan) return 3;
+  if (precision == kPrecF32Span) return 0;
   return precision == HARU_INT16 ? (lc.int16_mode == 1 ? 1 : 2) : 0;
 }
 
@@ -105,7 +106,7 @@ struct ForkJoin {
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
                        const LaunchCfg &lc, cudaStream_t s, const ForkJoin *fj, cudaEvent_t ev_prep,
-                       cudaEvent_t ev_sweep);
+                       cudaEvent_t ev_sweep, int64_t *d_start = nullptr);
 
 // Record `e` on `s`; inside a stream capture, as an external event node so
 // its time can be read after every replay.
@@ -142,6 +143,7 @@ struct haru_ctx {
   uint32_t *d_offsets = nullptr;
   float *d_cost = nullptr;
   int64_t *d_col = nullptr;
+  int64_t *d_start = nullptr;
   size_t cap_q = 0;
   haru::ForkJoin fj;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // HARU_PROFILE

@@ -70,6 +70,14 @@ constexpr int kCap = HARU_INT16_CAP;
 constexpr int kMaxTile = 16384;
 constexpr long kRefPad = 32 * kMaxS + kMaxTile + 64;
 
+// Internal precisions of the sweep kernels beyond the public HARU_FP32,
+// HARU_INT16 and HARU_INT16_ACC32: the FP32 and wide forms that also carry
+// each alignment's start column (haru_sdtw_batch_span).
+constexpr int kPrecF32Span = 3, kPrecWideSpan = 4;
+__host__ __device__ constexpr bool prec_span(int p) { return p == kPrecF32Span || p == kPrecWideSpan; }
+// Tracking-ring words per warp: costs (and start columns, +128, for the span forms).
+__host__ __device__ constexpr int ring_words(int p) { return prec_span(p) ? 256 : 128; }
+
 // Strip-height classes, tallest first: S in 13..16, 9..12, 5..8, 1..4; kernel
 // class 4 covers 1..16 in one kernel (single queue, planned into slot 0).
 constexpr int kClasses = 4;
@@ -123,6 +131,7 @@ struct SdtwArgs {
   uint32_t *states;        // [item][nseg_cap][2] saved states (start, final), kStateStride words each
   Best *bests;             // [item][nseg_cap]: the strip's (upper stack's) last-row minimum
   Best *bests2;            // [item][nseg_cap]: the lower stack's, for stacked items
+  int64_t *out_start;      // span forms: the alignment start column per query
   int nseg_cap;
   float *out_cost;
   int64_t *out_col;
@@ -169,7 +178,7 @@ cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s);
 cudaError_t launch_qstats(const float *events, const uint32_t *offsets, uint32_t nq, double *qstats, int *status,
                           cudaStream_t s);
 cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s);
-size_t sdtw_smem_bytes(int tile_cols, int warps);
+size_t sdtw_smem_bytes(int precision, int tile_cols, int warps);
 int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps);
 
 // Reference preparation.

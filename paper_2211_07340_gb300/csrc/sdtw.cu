@@ -23,6 +23,8 @@ HARU_SDTW_DECLARE(1, 2)
 HARU_SDTW_DECLARE(1, 3)
 HARU_SDTW_DECLARE(1, 4)
 HARU_SDTW_DECLARE(2, 4)
+HARU_SDTW_DECLARE(3, 4)
+HARU_SDTW_DECLARE(4, 4)
 
 namespace {
 #define HARU_SDTW_BOTH(P, C)                                                               \
@@ -38,9 +40,18 @@ cudaError_t launch_p1(int cls, const SdtwArgs &a, int grid, int fix_items, cudaS
     default: HARU_SDTW_BOTH(1, 3)
   }
 }
-cudaError_t launch_p2(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {  // single kernel only
+// The wide form and the start-column forms have the single kernel only.
+cudaError_t launch_p2(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   cudaError_t e;
   HARU_SDTW_BOTH(2, 4)
+}
+cudaError_t launch_p3(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
+  cudaError_t e;
+  HARU_SDTW_BOTH(3, 4)
+}
+cudaError_t launch_p4(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
+  cudaError_t e;
+  HARU_SDTW_BOTH(4, 4)
 }
 cudaError_t launch_p0(int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   cudaError_t e;
@@ -54,13 +65,16 @@ cudaError_t launch_p0(int cls, const SdtwArgs &a, int grid, int fix_items, cudaS
 }
 }  // namespace
 
-size_t sdtw_smem_bytes(int tile_cols, int warps) {
+size_t sdtw_smem_bytes(int precision, int tile_cols, int warps) {
   // Shared header, per-warp tracking rings, 32 zero words, two tile slots
-  return 128 + static_cast<size_t>(warps) * 128 * 4 + 32 * 4 + 2 * static_cast<size_t>(tile_cols) * 4;
+  return 128 + static_cast<size_t>(warps) * ring_words(precision) * 4 + 32 * 4 +
+         2 * static_cast<size_t>(tile_cols) * 4;
 }
 
 int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
   if (precision == HARU_INT16_ACC32) return sdtw_occupancy_2_4(tile_cols, warps);
+  if (precision == kPrecF32Span) return sdtw_occupancy_3_4(tile_cols, warps);
+  if (precision == kPrecWideSpan) return sdtw_occupancy_4_4(tile_cols, warps);
   if (precision == HARU_INT16) {
     switch (cls) {
       case 0: return sdtw_occupancy_1_0(tile_cols, warps);
@@ -83,6 +97,8 @@ int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
 // writes the outputs), stream-ordered.
 cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   if (precision == HARU_INT16_ACC32) return launch_p2(a, grid, fix_items, s);
+  if (precision == kPrecF32Span) return launch_p3(a, grid, fix_items, s);
+  if (precision == kPrecWideSpan) return launch_p4(a, grid, fix_items, s);
   return precision == HARU_INT16 ? launch_p1(cls, a, grid, fix_items, s) : launch_p0(cls, a, grid, fix_items, s);
 }
 

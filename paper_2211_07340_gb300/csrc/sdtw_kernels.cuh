@@ -174,7 +174,7 @@ struct StripI16 {
   // As if the reference began at the current step: every row at its initial
   // value; the masked chunks hold rows that have not reached their first
   // column at that value.
-  __device__ __forceinline__ void fresh() {
+  __device__ __forceinline__ void fresh(long, int) {
 #pragma unroll
     for (int k = 0; k < S; ++k) {
       G[0][k] = init(k);
@@ -205,7 +205,7 @@ struct StripI16 {
 
   template <bool MASK>
   __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
-                                        uint32_t nr, bool tracked) {
+                                        uint32_t nr, bool tracked, int, int) {
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
 #pragma unroll
@@ -239,7 +239,8 @@ struct StripI16 {
 struct TrackI16 {
   int ba = 0x7fffffff, bb = 0x7fffffff;
   long ca = -1, cb = -1;
-  __device__ __forceinline__ void add(uint32_t v, long c) {
+  __device__ __forceinline__ void add(const uint32_t *rg, int j, long c) {
+    const uint32_t v = rg[j];
     const int va = static_cast<int>(v & 0xffffu);
     const int vb = static_cast<int>(v >> 16);
     if (va < ba) { ba = va; ca = c; }
@@ -281,7 +282,7 @@ struct StripF32 {
       W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
     }
   }
-  __device__ __forceinline__ void fresh() {
+  __device__ __forceinline__ void fresh(long, int) {
     const float kBig = 1.0e30f;  // stands for +inf; sums of these stay finite
 #pragma unroll
     for (int k = 0; k < S; ++k) {
@@ -311,7 +312,7 @@ struct StripF32 {
 
   template <bool MASK>
   __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
-                                        uint32_t nr, bool tracked) {
+                                        uint32_t nr, bool tracked, int, int) {
     (void)trel;
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
@@ -350,8 +351,8 @@ struct TrackF32 {
   float best;
   long col;
   __device__ TrackF32() : best(__builtin_huge_valf()), col(-1) {}
-  __device__ __forceinline__ void add(uint32_t v, long c) {
-    float f = __uint_as_float(v);
+  __device__ __forceinline__ void add(const uint32_t *rg, int j, long c) {
+    float f = __uint_as_float(rg[j]);
     if constexpr (CAPPED) f = fminf(f, static_cast<float>(kCap));
     if (f < best) { best = f; col = c; }
   }
@@ -370,6 +371,147 @@ struct TrackF32 {
   }
 };
 
+// ------------------------------------------------------ start columns --
+// The FP32 strip that also carries each cell's alignment start column: a
+// cell takes the start of its up neighbour if that is a minimum
+// predecessor, else of its diagonal one if that is, else of its left one.
+// Pad rows (weight 0, cost 0) take their up neighbour's start on the cost
+// tie, so they pass down "my own column" from the row injected above the
+// first lane of a stack (the row above row i processed column t - i at
+// step t - 1); the first real row therefore starts its paths at its own
+// column, like the free-start row of Eq. 1. CODES as for StripF32.
+template <int S, bool CODES>
+struct StripF32Span {
+  float Q[S], W[S], G[2][S], Rr[S];
+  int P[2][S];
+  float gprev;
+  int pprev;
+
+  __device__ __forceinline__ static float ref_value(uint32_t w) {
+    if constexpr (CODES)
+      return __int2float_rn(static_cast<int>(static_cast<short>(w & 0xffffu)));
+    else
+      return __uint_as_float(w);
+  }
+  __device__ __forceinline__ void load(const uint32_t *img, int lane) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      Q[k] = __uint_as_float(img[k * 32 + lane]);
+      W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
+    }
+  }
+  // Before step t_start: row i = lane * S + k held its column t_start - 1 - i
+  // (and t_start - 2 - i one step earlier) as the start of a pad row's path.
+  __device__ __forceinline__ void fresh(long t_start, int lane) {
+    const float kBig = 1.0e30f;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[0][k] = W[k] != 0.0f ? kBig : 0.0f;
+      G[1][k] = G[0][k];
+      Rr[k] = kBig;
+      const int i = lane * S + k;
+      P[1][k] = static_cast<int>(t_start) - 1 - i;
+      P[0][k] = static_cast<int>(t_start) - 2 - i;
+    }
+    gprev = 0.0f;
+    pprev = static_cast<int>(t_start) - 1 - lane * S;  // the row above row 0 at step t_start - 2
+  }
+  // States hold G (2S rows of 32 words) then P (2S rows).
+  __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane, uint32_t ng) {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      G[1][k] = __uint_as_float(st[k * 32 + lane]);
+      G[0][k] = __uint_as_float(st[(S + k) * 32 + lane]);
+      P[1][k] = static_cast<int>(st[(2 * S + k) * 32 + lane]);
+      P[0][k] = static_cast<int>(st[(3 * S + k) * 32 + lane]);
+      Rr[(1 + k) % S] = ref_value(gref[t - 1 - static_cast<long>(lane) * S - k]);
+    }
+    const float g = __shfl_up_sync(kFull, G[0][S - 1], 1);
+    const int pg = __shfl_up_sync(kFull, P[0][S - 1], 1);
+    gprev = ng ? g : 0.0f;
+    pprev = ng ? pg : static_cast<int>(t) - 1 - lane * S;
+  }
+  __device__ __forceinline__ void save(uint32_t *st, int lane) const {
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      st[k * 32 + lane] = __float_as_uint(G[1][k]);
+      st[(S + k) * 32 + lane] = __float_as_uint(G[0][k]);
+      st[(2 * S + k) * 32 + lane] = static_cast<uint32_t>(P[1][k]);
+      st[(3 * S + k) * 32 + lane] = static_cast<uint32_t>(P[0][k]);
+    }
+  }
+
+  // t0: the absolute step of the chunk's first step; top: the first row of
+  // this lane's stack (0, or 16 * S in the lower stack). The ring's start
+  // columns sit 128 words after the costs.
+  template <bool MASK>
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+                                        uint32_t nr, bool tracked, int t0, int top) {
+    (void)trel;
+    constexpr int U = Geo<S>::U;
+    RefWindow<U> win;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int p = (S - (u % S)) % S;
+      const int a = (u + 1) & 1;
+      const int b = u & 1;
+      float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
+      int pup = __shfl_up_sync(kFull, P[a][S - 1], 1);
+      float rin = __shfl_up_sync(kFull, Rr[p], 1);
+      const float rv = ref_value(win.get(ref, u));
+      gup = ng ? gup : 0.0f;             // a stack's first lane: the free-start row, 0 ...
+      pup = ng ? pup : t0 + u - top;      // ... whose row processed column t - top at step t - 1
+      rin = nr ? rin : rv;                // lane 0: reference sample t
+      Rr[p] = rin;
+#pragma unroll
+      for (int k = S - 1; k >= 0; --k) {
+        const float r = Rr[(p + k) % S];
+        const float d = __fsub_rn(Q[k], r);
+        float m = k ? G[a][k - 1] : gup;
+        int pm = k ? P[a][k - 1] : pup;
+        const float dg = k ? G[b][k - 1] : gprev;
+        const int pd = k ? P[b][k - 1] : pprev;
+        if (dg < m) { m = dg; pm = pd; }
+        if (G[a][k] < m) { m = G[a][k]; pm = P[a][k]; }
+        G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
+        P[b][k] = pm;
+      }
+      gprev = gup;
+      pprev = pup;
+      if (tracked) {
+        ring[e0 + u] = __float_as_uint(G[b][S - 1]);
+        ring[128 + e0 + u] = static_cast<uint32_t>(P[b][S - 1]);
+      }
+    }
+  }
+};
+
+struct TrackF32Span {
+  float best;
+  long col;
+  int start;
+  __device__ TrackF32Span() : best(__builtin_huge_valf()), col(-1), start(-1) {}
+  __device__ __forceinline__ void add(const uint32_t *rg, int j, long c) {
+    const float f = __uint_as_float(rg[j]);
+    if (f < best) { best = f; col = c; start = static_cast<int>(rg[128 + j]); }
+  }
+  __device__ __forceinline__ void reduce(int width) {  // over aligned groups of `width` lanes
+    for (int o = width >> 1; o > 0; o >>= 1) {
+      float ob = __shfl_xor_sync(kFull, best, o);
+      long oc = __shfl_xor_sync(kFull, col, o);
+      int os = __shfl_xor_sync(kFull, start, o);
+      if (ob < best || (ob == best && static_cast<unsigned long>(oc) < static_cast<unsigned long>(col))) {
+        best = ob;
+        col = oc;
+        start = os;
+      }
+    }
+  }
+  __device__ __forceinline__ void store(Best *b) const {
+    b->ia = 0; b->ib = 0; b->f = best; b->pad = 0; b->ca = col; b->cb = start;
+  }
+};
+
 // Arithmetic forms of a strip: FP32 queries, int16 pairs (DPX), int16
 // codes computed exactly in FP32 and saturated like the int16 form (an int16
 // batch may run both side by side, to use the half-rate DPX/min pipe and the
@@ -377,6 +519,8 @@ struct TrackF32 {
 // saturation: wide accumulation (every cost of a query of <= 512 events is
 // an integer below 512 * 4094 < 2^24, so FP32 holds it exactly).
 constexpr int kFormF32 = 0, kFormI16 = 1, kFormExact = 2, kFormExactWide = 3;
+// and the FP32 and wide forms carrying the start column
+constexpr int kFormF32Span = 4, kFormWideSpan = 5;
 
 template <int FORM, int S>
 struct FormOf;
@@ -402,6 +546,18 @@ template <int S>
 struct FormOf<kFormExactWide, S> {
   using Strip = StripF32<S, true>;
   using Track = TrackF32<false>;
+  static constexpr bool kMasked = false;
+};
+template <int S>
+struct FormOf<kFormF32Span, S> {
+  using Strip = StripF32Span<S, false>;
+  using Track = TrackF32Span;
+  static constexpr bool kMasked = false;
+};
+template <int S>
+struct FormOf<kFormWideSpan, S> {
+  using Strip = StripF32Span<S, true>;
+  using Track = TrackF32Span;
   static constexpr bool kMasked = false;
 };
 
@@ -489,8 +645,9 @@ struct GlobalTiles {
 // save_start / save_final: where to store the state before step t_own and
 // before step t_end (nullptr: not stored). stk: a stacked item (lanes 0..15
 // and 16..31 are two strips; each lane tracks its own stack's last row).
-// `ring` holds 128 words per warp: two flush buffers of 64, the upper
-// stack's (or the whole strip's) entries first, the lower stack's at +32.
+// `ring` holds kRingWords words per warp: two flush buffers of 64, the upper
+// stack's (or the whole strip's) entries first, the lower stack's at +32;
+// forms that carry start columns keep them 128 words further on.
 // Returns false on abort.
 template <int FORM, int S, class Src>
 __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<FORM, S>::Track &tr, Src &src,
@@ -503,6 +660,7 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
   const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u, nr = lane != 0 ? 1u : 0u;
   const bool tracked = lane == 31 || (stk && lane == 15);
   const int soff = stk && lane >= 16 ? 32 : 0;
+  const int top = stk && lane >= 16 ? 16 * S : 0;  // first row of this lane's stack
   const long last_row = (stk && lane < 16 ? 16L : 32L) * S - 1;
   const int nscan = stk ? 2 : 1;
   const long mask_end = fresh ? t_start + 32L * S : t_start;
@@ -529,10 +687,11 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
       if (o == own_at) st.save(save_start, lane);
       uint32_t *rg = ring + buf * 64 + soff;
       const uint32_t *ref = nr ? zw : tref + o;
+      const int tabs = static_cast<int>(lo) + o;
       if (kMasked && o < mask_n)
-        st.template chunk<true>(ref, trel0 + o, lane, rg, fl * U, ng, nr, tracked);
+        st.template chunk<true>(ref, trel0 + o, lane, rg, fl * U, ng, nr, tracked, tabs, top);
       else
-        st.template chunk<false>(ref, 0, lane, rg, fl * U, ng, nr, tracked);
+        st.template chunk<false>(ref, 0, lane, rg, fl * U, ng, nr, tracked, tabs, top);
       if (++fl == F || (last_tile && o + U >= n)) {
         __syncwarp();
         for (int r = 0; r < nscan; ++r) {  // entry j = step tflush + j of this lane's stack
@@ -540,7 +699,7 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
           if (j < fl * U) {
             const long t = tflush + j;
             const long c = t - last_row;
-            if (t >= t_own && c >= 0 && c < N) tr.add(rg[j], c);
+            if (t >= t_own && c >= 0 && c < N) tr.add(rg, j, c);
           }
         }
         tflush += static_cast<long>(fl) * U;
@@ -562,9 +721,9 @@ __device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, in
   typename FormOf<FORM, S>::Strip st;
   typename FormOf<FORM, S>::Track tr;
   st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
-  st.fresh();
   long t_start, t_own, t_end;
   seg_bounds(S, g.nseg, g.seg, A.N, &t_start, &t_own, &t_end);
+  st.fresh(t_start, lane);
   uint32_t *ss = nullptr, *sf = nullptr;
   const size_t unit = static_cast<size_t>(item) * A.nseg_cap + g.seg;
   if (g.seg > 0) ss = A.states + (unit * 2 + 0) * kStateStride;
@@ -584,6 +743,10 @@ __device__ __forceinline__ void sweep_any(const SdtwArgs &A, TileStream &ts, con
     sweep_unit<kFormF32, S>(A, ts, g, item, ring, lane);
   } else if constexpr (PREC == HARU_INT16_ACC32) {
     sweep_unit<kFormExactWide, S>(A, ts, g, item, ring, lane);
+  } else if constexpr (PREC == kPrecF32Span) {
+    sweep_unit<kFormF32Span, S>(A, ts, g, item, ring, lane);
+  } else if constexpr (PREC == kPrecWideSpan) {
+    sweep_unit<kFormWideSpan, S>(A, ts, g, item, ring, lane);
   } else {
     if (A.items[item].kind == kItemExact)
       sweep_unit<kFormExact, S>(A, ts, g, item, ring, lane);
@@ -622,10 +785,11 @@ template <int PREC, int CLS>
 __global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kernel(SdtwArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared *sh = reinterpret_cast<Shared *>(smem);
-  // layout: Shared (128 B) | per-warp tracking rings (128 words each) | zero words | two tile slots
+  // layout: Shared (128 B) | per-warp tracking rings | zero words | two tile slots
   uint32_t *rings = reinterpret_cast<uint32_t *>(smem + 128);
-  uint32_t *zero_words = reinterpret_cast<uint32_t *>(smem + 128 + A.warps * 128 * 4);
-  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * 128 * 4 + kZeroWords * 4);
+  constexpr int kRing = ring_words(PREC);
+  uint32_t *zero_words = reinterpret_cast<uint32_t *>(smem + 128 + A.warps * kRing * 4);
+  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * kRing * 4 + kZeroWords * 4);
   if (threadIdx.x < kZeroWords) zero_words[threadIdx.x] = 0u;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -667,7 +831,7 @@ __global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kern
       if (ts.K > 1) ts.issue(1);
     }
     __syncthreads();
-    if (warp < grp.count) dispatch_sweep<PREC, CLS>(S, A, ts, grp, grp.first + warp, rings + warp * 128, lane);
+    if (warp < grp.count) dispatch_sweep<PREC, CLS>(S, A, ts, grp, grp.first + warp, rings + warp * kRing, lane);
     __syncthreads();
     if (threadIdx.x == 0) sh->tile_base += ts.K;
   }
@@ -693,7 +857,7 @@ __device__ __forceinline__ void combine(Best &b, const Best &o) {
     if (o.ia < b.ia) { b.ia = o.ia; b.ca = o.ca; }
     if (o.ib < b.ib) { b.ib = o.ib; b.cb = o.cb; }
   } else {
-    if (o.f < b.f) { b.f = o.f; b.ca = o.ca; }
+    if (o.f < b.f) { b.f = o.f; b.ca = o.ca; b.cb = o.cb; }  // cb: the start column of the span forms
   }
 }
 
@@ -707,13 +871,14 @@ __device__ __forceinline__ void write_out(const SdtwArgs &A, const Best &b, int 
       A.out_cost[qb] = static_cast<float>(b.ib) * A.inv_scale;
       A.out_col[qb] = b.cb;
     }
-  } else if (FORM == kFormExact || FORM == kFormExactWide) {
+  } else if (FORM == kFormExact || FORM == kFormExactWide || FORM == kFormWideSpan) {
     A.out_cost[qa] = b.f * A.inv_scale;
     A.out_col[qa] = b.ca;
   } else {
     A.out_cost[qa] = b.f;
     A.out_col[qa] = b.ca;
   }
+  if (FORM == kFormF32Span || FORM == kFormWideSpan) A.out_start[qa] = b.cb;
 }
 
 template <int FORM, int S>
@@ -766,6 +931,10 @@ __device__ __forceinline__ void fixup_any(const SdtwArgs &A, int item, uint32_t 
     fixup_item<kFormF32, S>(A, item, ring, lane);
   } else if constexpr (PREC == HARU_INT16_ACC32) {
     fixup_item<kFormExactWide, S>(A, item, ring, lane);
+  } else if constexpr (PREC == kPrecF32Span) {
+    fixup_item<kFormF32Span, S>(A, item, ring, lane);
+  } else if constexpr (PREC == kPrecWideSpan) {
+    fixup_item<kFormWideSpan, S>(A, item, ring, lane);
   } else {
     if (A.items[item].kind == kItemExact)
       fixup_item<kFormExact, S>(A, item, ring, lane);
@@ -788,19 +957,19 @@ constexpr int kFixWarps = 4;
 
 template <int PREC, int CLS>
 __global__ void __launch_bounds__(kFixWarps * 32) fixup_kernel(SdtwArgs A) {
-  __shared__ uint32_t rings[kFixWarps * 128];
+  __shared__ uint32_t rings[kFixWarps * ring_words(PREC)];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int first = A.ints[kIntClassItemFirst + slot_of<CLS>()];
   const int count = A.ints[kIntClassItemCount + slot_of<CLS>()];
   const int i = blockIdx.x * kFixWarps + warp;
   if (i >= count) return;
   const int item = first + i;
-  dispatch_fixup<PREC, CLS>(A.items[item].S, A, item, rings + warp * 128, lane);
+  dispatch_fixup<PREC, CLS>(A.items[item].S, A, item, rings + warp * ring_words(PREC), lane);
 }
 
 template <int PREC, int CLS>
 cudaError_t launch_sweep_cls(const SdtwArgs &a, int grid, cudaStream_t s) {
-  const size_t sm = sdtw_smem_bytes(a.tile_cols, a.warps);
+  const size_t sm = sdtw_smem_bytes(PREC, a.tile_cols, a.warps);
   cudaError_t e = cudaFuncSetAttribute(sdtw_kernel<PREC, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm));
   if (e != cudaSuccess) return e;
@@ -819,7 +988,7 @@ template <int PREC, int CLS>
 int occupancy_cls(int tile_cols, int warps) {
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sdtw_kernel<PREC, CLS>, warps * 32,
-                                                sdtw_smem_bytes(tile_cols, warps));
+                                                sdtw_smem_bytes(PREC, tile_cols, warps));
   return n;
 }
 

@@ -373,3 +373,50 @@ def test_wide_accumulation_above_cap(haru):
     o = compare_int16(cw, jw, ref, ev, off, normalize_ref=False, normalize_q=False, prec=oracle.PREC_I32)
     np.testing.assert_array_equal(o.icost, np.array(lens) * 2047)
     np.testing.assert_array_equal(jw, 2000)
+
+
+@pytest.mark.parametrize("stack", [-1, 1])
+def test_start_columns(haru, sars, stack):
+    """haru_sdtw_batch_span: costs and end columns equal haru_sdtw_batch's;
+    start columns equal the oracle's (FP32 and wide accumulation), stacked
+    and not, over ragged lengths."""
+    _, ref = sars
+    qs = synth.workload("sars_uneven_8192", nq=199).queries
+    rng = np.random.default_rng(41)
+    lengths = [1, 2, 31, 32, 33, 100, 255, 256, 257, 511, 512] + list(rng.integers(1, 513, size=12))
+    off = offsets_of(lengths)
+    ev = synth.random_signal(int(off[-1]), seed=42, scale=1.0, loc=0.0)
+    with haru.Context(stack_short=stack) as ctx:
+        ctx.ref_load(ref)
+        for prec, oprec in ((haru.HARU_FP32, oracle.PREC_F32), (haru.HARU_INT16_ACC32, oracle.PREC_I32)):
+            c, j = ctx.sdtw_batch(prec, qs.events, qs.offsets)
+            cs, js, ss = ctx.sdtw_batch_span(prec, qs.events, qs.offsets)
+            np.testing.assert_array_equal(cs, c)
+            np.testing.assert_array_equal(js, j)
+            o = oracle.batch(oprec, ref, qs.events, qs.offsets, start=True)
+            np.testing.assert_array_equal(ss, o.start)
+            assert ((ss >= 0) & (ss <= js)).all()
+            cs, js, ss = ctx.sdtw_batch_span(prec, ev, off, raw=False)
+            o = oracle.batch(oprec, ref, ev, off, normalize_q=False, start=True)
+            np.testing.assert_array_equal(js, o.col)
+            np.testing.assert_array_equal(ss, o.start)
+        with pytest.raises(haru.HaruError):
+            ctx.sdtw_batch_span(haru.HARU_INT16, qs.events, qs.offsets)
+
+
+def test_start_columns_of_planted_copies(haru):
+    N = 6000
+    ref = synth.random_signal(N, seed=43, scale=1.0, loc=0.0)
+    starts = [0, 1, 777, 2500, N - 300, 4000]
+    lens = [300, 250, 129, 32, 300, 60]
+    parts = [ref[s:s + m] for s, m in zip(starts, lens)]
+    parts[-1] = np.repeat(parts[-1], 2)  # dwelled: every sample twice
+    lens[-1] *= 2
+    ev = np.concatenate(parts).astype(np.float32)
+    off = offsets_of(lens)
+    with haru.Context() as ctx:
+        ctx.ref_load(ref, normalize=False)
+        c, j, st = ctx.sdtw_batch_span(haru.HARU_FP32, ev, off, raw=False)
+    np.testing.assert_array_equal(c, 0.0)
+    np.testing.assert_array_equal(st, starts)
+    np.testing.assert_array_equal(j, [s + m - 1 for s, m in zip(starts, [300, 250, 129, 32, 300, 60])])
