@@ -331,9 +331,9 @@ def main():
     ap.add_argument("--fixed-len", type=int, default=0, help="profiling: every query this many events")
     ap.add_argument("--single", type=int, default=-1, help="1: one sweep kernel, 0: four class kernels "
                     "(-1 = library default; the autotuner may change it)")
-    ap.add_argument("--forms", default="int16,fp32,acc32",
+    ap.add_argument("--forms", default="int16,fp32,acc32,span",
                     help="forms to time: int16, int16exact (exact-share option), fp32, acc32 (int16 inputs, "
-                         "32-bit accumulation)")
+                         "32-bit accumulation), span (FP32 with alignment start columns)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the library defaults)")
     ap.add_argument("--workload", default=WORKLOAD, help="sars_uneven_8192 (default) or long_512x250")
@@ -473,6 +473,29 @@ def main():
         ms32, sweep32, clocks32, _ = run_form(haru.HARU_FP32)
     if "acc32" in forms:
         msw, sweepw, _, _ = run_form(haru.HARU_INT16_ACC32)
+    span_ms = nan
+    if "span" in forms:  # FP32 with start columns, default launch shape, direct launches
+        d = haru.default_config()
+        ctx.configure(warps_per_cta=args.warps or d.warps_per_cta, tile_cols=args.tile or d.tile_cols,
+                      units_target=args.units or d.units_target)
+        start_d = torch.empty(q.nq, dtype=torch.int64, device=dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        times = []
+        for rep in range(args.warmup + max(3, args.steps // 4)):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0.record(stream)
+                ctx.sdtw_batch_span_device(haru.HARU_FP32, ev_d, off_d, cost_d, col_d, start_d,
+                                           stream=stream.cuda_stream, asynchronous=True)
+                e1.record(stream)
+            stream.synchronize()
+            if rep >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        if ctx.last_status() != haru.HARU_OK:
+            raise haru.HaruError(ctx.last_status(), "span batch")
+        span_ms = float(np.mean(times))
+        launches.append(5 * len(times))  # plan, statistics, pack, sweep, fix-up
     ctx.configure(int16_exact_share=0)
     if "int16" in tuned:
         ctx.configure(**tuned["int16"])
@@ -500,11 +523,12 @@ def main():
             e2e_step()
         e2e_s = [e2e_step() for _ in range(args.steps)]
         e2e_ms = 1e3 * float(np.mean(e2e_s))
+        launches.append(kernels_per_step() * args.steps)
 
     if dist:
-        t = torch.tensor([ms16, e2e_ms, ms32, msw], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms16, e2e_ms, ms32, msw, span_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms16, e2e_ms, ms32, msw = (float(x) for x in t.tolist())
+        ms16, e2e_ms, ms32, msw, span_ms = (float(x) for x in t.tolist())
     total_cells = cells * world
     value = total_cells / (ms16 / 1e3) / 1e9
     value32 = total_cells / (ms32 / 1e3) / 1e9
@@ -558,6 +582,10 @@ def main():
                          "note": "int16 inputs with 32-bit accumulation (Section 4.3's PE): exact integer costs, "
                                  "computed exactly in FP32, one query per strip"}
                         if msw == msw else None),
+        "fp32_start_columns": ({"value": total_cells / (span_ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": span_ms,
+                                "note": "FP32 with each alignment's start column (haru_sdtw_batch_span): "
+                                        "direct launches, default launch shape, unsegmented"}
+                               if span_ms == span_ms else None),
         "int16_over_fp32": value / value32 if value32 == value32 else None,
         "prep_ms_per_step": ms16 - sweep16,
         "e2e": {"value": e2e_value, "unit": "GCUPS", "ms_per_step": e2e_ms,

@@ -90,8 +90,9 @@ typedef struct {
   int stack_short;          /* queries of at most 256 events stacked two to a warp strip (lanes 0-15
                                and 16-31), doubling the rows each lane sweeps: more throughput, but
                                each strip takes longer. 0 (default) = in batches of at least
-                               units_target queries (or 4 x SMs x warps_per_cta when that is 0);
-                               1 = always; -1 = never */
+                               units_target queries (or 4 x SMs x warps_per_cta when that is 0),
+                               or whose stacked items cut into reference segments still make that
+                               many work units (long references); 1 = always; -1 = never */
   int int16_exact_share;    /* int16 batches: 0 (default) = every warp runs packed DPX query pairs;
                                1 = two of every three warps compute their query exactly on the int16
                                codes in FP32 instead (identical results: saturating every cell equals

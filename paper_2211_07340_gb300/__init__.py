@@ -269,6 +269,15 @@ class Context:
               "haru_sdtw_batch_span")
         return cost[:nq], col[:nq], start[:nq]
 
+    def sdtw_batch_span_device(self, precision: int, events, offsets, out_cost, out_col, out_start,
+                               stream: int = 0, raw: bool = True, asynchronous: bool = False):
+        """haru_sdtw_batch_span on device tensors (torch), ordered on `stream`."""
+        nq = int(offsets.shape[0]) - 1
+        flags = HARU_ON_DEVICE | (HARU_RAW if raw else 0) | (HARU_ASYNC if asynchronous else 0)
+        return check(int(lib().haru_sdtw_batch_span(self._h, int(precision), _ptr(events), _ptr(offsets), nq,
+                                                    _ptr(out_cost), _ptr(out_col), _ptr(out_start), int(stream),
+                                                    flags)), "haru_sdtw_batch_span")
+
     def sdtw_batch_device(self, precision: int, events, offsets, out_cost, out_col, stream: int = 0,
                           raw: bool = True, asynchronous: bool = False, profile: bool = False):
         """Device tensors in and out (torch), ordered on `stream` (a cudaStream_t as int)."""

@@ -449,7 +449,7 @@ int haru_last_stats(haru_ctx *ctx, haru_batch_stats *out) {
   out->items = (uint32_t)w[haru::kIntItems];
   out->groups = (uint32_t)w[haru::kIntGroups];
   out->fixups = (uint32_t)w[haru::kIntFixups];
-  out->max_segments = (uint32_t)ctx->ws.nseg_cap;
+  out->max_segments = (uint32_t)w[haru::kIntMaxSeg];
   return HARU_OK;
 }
 

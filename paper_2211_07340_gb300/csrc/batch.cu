@@ -30,8 +30,10 @@ cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCf
   // Work units: enough (query x reference segment) units to keep every SM
   // busy to the end; nseg_cap bounds the segments per item for storage.
   const int units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * lc.warps;
-  const size_t items_min = (mode == 0 || mode == 3) ? nq
-                           : (mode == 1 ? (static_cast<size_t>(nq) + 1) / 2 : (3 * static_cast<size_t>(nq)) / 4);
+  // Fewest items the batch can make (stacked: four int16 or two other
+  // queries per item); the segment cap is sized for that case.
+  const size_t items_min = (mode == 0 || mode == 3) ? (static_cast<size_t>(nq) + 1) / 2
+                           : (mode == 1 ? (static_cast<size_t>(nq) + 3) / 4 : (3 * static_cast<size_t>(nq)) / 4);
   int nseg_cap = static_cast<int>(
       std::min<size_t>(kMaxSeg, (static_cast<size_t>(units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
   if (nseg_cap < 1 || prec_span(precision)) nseg_cap = 1;  // start-column forms sweep unsegmented
@@ -77,7 +79,14 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   pa.warps = lc.warps;
   pa.units_target = ws.units_target;
   pa.single = lc.single_kernel ? 1 : 0;
-  pa.stack = lc.stack_short > 0 || (lc.stack_short == 0 && nq >= static_cast<uint32_t>(ws.units_target)) ? 1 : 0;
+  // Auto stacking: when the batch alone fills the unit target, or when its
+  // stacked items (up to four queries each) cut into reference segments
+  // (at most 64, each at least 8,192 steps: four warm-ups of a 16-row strip)
+  // still do; small batches on short references stay unstacked for latency.
+  const long seg_room = std::min<long>(kMaxSeg, ref.N / 8192);
+  const bool fills = nq >= static_cast<uint32_t>(ws.units_target) ||
+                     static_cast<long>(nq) * seg_room >= 4L * ws.units_target;
+  pa.stack = lc.stack_short > 0 || (lc.stack_short == 0 && fills) ? 1 : 0;
   pa.nseg_cap = ws.nseg_cap;
   pa.items = ws.items;
   pa.groups = ws.groups;

@@ -85,7 +85,8 @@ constexpr int kClassAll = 4;
 
 // Layout of the small integer block every batch uses (status and counters).
 constexpr int kIntStatus = 0, kIntGroups = 1, kIntItems = 2, kIntFixups = 3, kIntQueues = 4, kIntClassFirst = 8,
-              kIntClassCount = 12, kIntClassItemFirst = 16, kIntClassItemCount = 20, kIntWords = 24;
+              kIntClassCount = 12, kIntClassItemFirst = 16, kIntClassItemCount = 20, kIntMaxSeg = 24,
+              kIntWords = 25;
 
 __host__ __device__ inline int steps_per_chunk(int S) { return (S % 2 == 0) ? S : 2 * S; }
 

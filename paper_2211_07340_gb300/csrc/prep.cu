@@ -206,6 +206,10 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
       a.ints[kIntClassItemCount + c] = icnt;
     }
     a.ints[kIntGroups] = g;
+    int most = 0;
+    for (int S = 1; S <= kMaxS; ++S)
+      if (icount[S] > 0 && nseg_of[S] > most) most = nseg_of[S];
+    a.ints[kIntMaxSeg] = most;
   }
   __syncthreads();
   // Groups of each bucket, segment-major: (seg, first item), in parallel.
