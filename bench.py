@@ -138,7 +138,8 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "sm_min_mhz": min(sm) if sm else None,
+                "below_1000_mhz": sum(1 for x in sm if x < 1000.0)}
 
 
 def cpu_baseline(ref, queries, target_s: float = 12.0, prec=None):
@@ -251,7 +252,16 @@ def run_serving(haru, args, local, w, threshold):
     th = threading.Thread(target=poller, daemon=True)
     th.start()
     t_start = time.monotonic_ns()
-    late = synth.replay(chunks, lambda c, t: ctx.stream_submit(c.read_id, c.channel, c.events, t, c.last))
+    # The arrival time is read before the Python submit call: keep the
+    # collector from pausing the replay thread between the two.
+    import gc
+    gc.collect()
+    gc.disable()
+    try:
+        with ClockSampler(local) as clk:
+            late = synth.replay(chunks, lambda c, t: ctx.stream_submit(c.read_id, c.channel, c.events, t, c.last))
+    finally:
+        gc.enable()
     deadline = time.monotonic() + 30
     while len(results) < q.nq and time.monotonic() < deadline:
         time.sleep(0.01)
@@ -261,7 +271,9 @@ def run_serving(haru, args, local, w, threshold):
     st = ctx.stream_stats()
     ctx.close()
     warm_ns = t_start + int(args.serve_warm * 1e9)
-    lat = np.array([(r.t_done_ns - r.t_arrival_ns) / 1e6 for r in results if r.t_arrival_ns >= warm_ns])
+    kept = [r for r in results if r.t_arrival_ns >= warm_ns]
+    lat = np.array([(r.t_done_ns - r.t_arrival_ns) / 1e6 for r in kept])
+    lib_lat = np.array([(r.t_done_ns - r.t_received_ns) / 1e6 for r in kept])
     dec = {r.read_id: r.decision for r in results}
     acc = float(np.mean([dec.get(i, 0) == int(q.on_target[i]) for i in range(q.nq)])) if q.nq else None
     N = 2 * (synth.SARS_COV_2_BASES - 5)
@@ -270,11 +282,17 @@ def run_serving(haru, args, local, w, threshold):
             "decided": len(results), "precision": "int16", "threshold_z": threshold,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "p999_ms": float(np.percentile(lat, 99.9)) if lat.size else None,
             "max_ms": float(lat.max()) if lat.size else None, "latency_samples": int(lat.size),
+            "over_10ms": int(np.sum(lat > 10.0)),
+            "library_p50_ms": float(np.percentile(lib_lat, 50)) if lib_lat.size else None,
+            "library_p99_ms": float(np.percentile(lib_lat, 99)) if lib_lat.size else None,
+            "library_max_ms": float(lib_lat.max()) if lib_lat.size else None,
             "decisions_per_s": len(results) / span, "gcups": len(results) * 250 * N / span / 1e9,
             "accept_eject_accuracy_vs_truth": acc, "batches": st["batches"], "max_batch": st["max_batch"],
-            "max_concurrent_batches": st["max_concurrent"], "late_chunks": late,
-            "latency_clock": "chunk delivery that completes the prefix -> decision available (CLOCK_MONOTONIC)"}
+            "max_concurrent_batches": st["max_concurrent"], "late_chunks": late, "clocks": clk.summary(),
+            "latency_clock": "chunk delivery that completes the prefix -> decision available (CLOCK_MONOTONIC); "
+                             "library_*: the library's receipt of that chunk -> decision available"}
 
 
 def run_reference(args, rank: int):

@@ -195,6 +195,8 @@ typedef struct {
   uint32_t pad;
   uint64_t t_arrival_ns;  /* as submitted with the chunk that completed the prefix */
   uint64_t t_done_ns;     /* when the decision was ready (CLOCK_MONOTONIC ns) */
+  uint64_t t_received_ns; /* when the library received that chunk (CLOCK_MONOTONIC ns): t_done_ns -
+                             t_received_ns is the library's own share of the latency */
 } haru_result;
 
 /* Append a chunk of raw event currents (host pointer, n floats) to read

@@ -74,7 +74,7 @@ class haru_result(ctypes.Structure):
     _fields_ = [("read_id", ctypes.c_uint64), ("channel", ctypes.c_uint32), ("decision", ctypes.c_int32),
                 ("cost", ctypes.c_float), ("status", ctypes.c_int32), ("end_col", ctypes.c_int64),
                 ("events", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("t_arrival_ns", ctypes.c_uint64),
-                ("t_done_ns", ctypes.c_uint64)]
+                ("t_done_ns", ctypes.c_uint64), ("t_received_ns", ctypes.c_uint64)]
 
 
 class haru_stream_stats(ctypes.Structure):

@@ -24,19 +24,35 @@ void ws_free(Workspace &ws) {
   ws = Workspace();
 }
 
-cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCfg &lc) {
+namespace {
+
+// Buffer sizes one batch of nq queries needs.
+struct WsNeeds {
+  size_t max_items, units, qstats, states;
+  int nseg_cap, units_target;
+};
+
+WsNeeds ws_needs(int precision, uint32_t nq, const LaunchCfg &lc) {
+  WsNeeds w;
   const int mode = plan_mode(precision, lc);
-  const size_t max_items = items_bound(mode, nq);
+  w.max_items = items_bound(mode, nq);
   // Work units: enough (query x reference segment) units to keep every SM
   // busy to the end; nseg_cap bounds the segments per item for storage.
-  const int units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * lc.warps;
+  w.units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * lc.warps;
   // Fewest items the batch can make (stacked: four int16 or two other
   // queries per item); the segment cap is sized for that case.
   const size_t items_min = (mode == 0 || mode == 3) ? (static_cast<size_t>(nq) + 1) / 2
                            : (mode == 1 ? (static_cast<size_t>(nq) + 3) / 4 : (3 * static_cast<size_t>(nq)) / 4);
-  int nseg_cap = static_cast<int>(
-      std::min<size_t>(kMaxSeg, (static_cast<size_t>(units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
-  if (nseg_cap < 1 || prec_span(precision)) nseg_cap = 1;  // start-column forms sweep unsegmented
+  w.nseg_cap = static_cast<int>(std::min<size_t>(
+      kMaxSeg, (static_cast<size_t>(w.units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
+  if (w.nseg_cap < 1 || prec_span(precision)) w.nseg_cap = 1;  // start-column forms sweep unsegmented
+  w.units = w.max_items * static_cast<size_t>(w.nseg_cap);
+  w.qstats = 2 * static_cast<size_t>(nq);
+  w.states = w.nseg_cap > 1 ? w.units * 2 * kStateStride : 0;
+  return w;
+}
+
+cudaError_t ws_alloc(Workspace &ws, size_t max_items, size_t units, size_t qstats, size_t states) {
   cudaError_t e = cudaSuccess;
   size_t c = ws.ints ? static_cast<size_t>(kIntWords) : 0;
   if ((e = grow(&ws.ints, &c, kIntWords)) != cudaSuccess) return e;
@@ -54,14 +70,34 @@ cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCf
     if ((e = grow(&ws.img, &c2, max_items * kImgStride)) != cudaSuccess) return e;
     ws.cap_items = max_items;
   }
-  const size_t units = max_items * static_cast<size_t>(nseg_cap);
   if ((e = grow(&ws.bests, &ws.cap_bests, 2 * units)) != cudaSuccess) return e;
-  if ((e = grow(&ws.qstats, &ws.cap_qstats, 2 * static_cast<size_t>(nq))) != cudaSuccess) return e;
-  if (nseg_cap > 1 && (e = grow(&ws.states, &ws.cap_states, units * 2 * kStateStride)) != cudaSuccess) return e;
-  ws.max_items = max_items;
-  ws.nseg_cap = nseg_cap;
-  ws.units_target = units_target;
+  if ((e = grow(&ws.qstats, &ws.cap_qstats, qstats)) != cudaSuccess) return e;
+  if (states > 0 && (e = grow(&ws.states, &ws.cap_states, states)) != cudaSuccess) return e;
   return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCfg &lc) {
+  const WsNeeds w = ws_needs(precision, nq, lc);
+  cudaError_t e = ws_alloc(ws, w.max_items, w.units, w.qstats, w.states);
+  if (e != cudaSuccess) return e;
+  ws.max_items = w.max_items;
+  ws.nseg_cap = w.nseg_cap;
+  ws.units_target = w.units_target;
+  return cudaSuccess;
+}
+
+cudaError_t ws_reserve_upto(Workspace &ws, int precision, uint32_t max_nq, const LaunchCfg &lc) {
+  size_t items = 0, units = 0, qstats = 0, states = 0;
+  for (uint32_t n = 1; n <= max_nq; ++n) {  // sizing arithmetic only; one allocation per buffer
+    const WsNeeds w = ws_needs(precision, n, lc);
+    items = std::max(items, w.max_items);
+    units = std::max(units, w.units);
+    qstats = std::max(qstats, w.qstats);
+    states = std::max(states, w.states);
+  }
+  return ws_alloc(ws, items, units, qstats, states);
 }
 
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,

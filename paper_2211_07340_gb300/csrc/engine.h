@@ -89,6 +89,9 @@ struct Workspace {
 
 // Size `ws` for a batch of nq queries (allocates only when it must grow).
 cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCfg &lc);
+// Size `ws` for every batch of 1..max_nq queries at once, so that later
+// ws_reserve calls for such batches never allocate.
+cudaError_t ws_reserve_upto(Workspace &ws, int precision, uint32_t max_nq, const LaunchCfg &lc);
 void ws_free(Workspace &ws);
 
 // Streams/events to run the class kernels side by side (optional).

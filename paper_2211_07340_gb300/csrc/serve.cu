@@ -90,6 +90,7 @@ class Server {
     bool bad = false;            // non-finite event seen
     float lo = 0.0f, hi = 0.0f;  // range of the accepted events (a flat prefix has no z-score)
     uint64_t t_arrival = 0;
+    uint64_t t_received = 0;
   };
   struct BatchCtx {
     Workspace ws;
@@ -196,8 +197,7 @@ int Server::start() {
     if (e == cudaSuccess) e = cudaMallocHost(&b.h_status, sizeof(int));
     // size the workspace for every batch size up to max_batch (segments per
     // item grow as batches shrink) so the loop never allocates
-    for (uint32_t n = static_cast<uint32_t>(max_batch_); n >= 1 && e == cudaSuccess; n = n / 2)
-      e = ws_reserve(b.ws, precision_, n, lc_);
+    if (e == cudaSuccess) e = ws_reserve_upto(b.ws, precision_, static_cast<uint32_t>(max_batch_), lc_);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -282,6 +282,7 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
   if (r.total >= static_cast<uint32_t>(prefix_) || last) {
     r.complete = true;
     r.t_arrival = t_arrival;
+    r.t_received = now_ns();
     if (r.bad || r.total < 2 || !(r.hi > r.lo) || r.total > static_cast<uint32_t>(ref_.N)) {
       // no z-score or no alignment for this prefix: decided (eject) without the GPU
       haru_result o;
@@ -293,6 +294,7 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
       o.end_col = -1;
       o.t_arrival_ns = t_arrival;
       o.t_done_ns = now_ns();
+      o.t_received_ns = r.t_received;
       host_events_ -= r.host.size();
       if (r.slot >= 0) free_slots_.push_back(r.slot);
       auto qi = std::find(admit_q_.begin(), admit_q_.end(), r.id);
@@ -483,6 +485,7 @@ int Server::turn_complete() {
         o.decision = (st == HARU_OK && o.cost <= thr) ? 1 : 0;
         o.t_arrival_ns = r.t_arrival;
         o.t_done_ns = t;
+        o.t_received_ns = r.t_received;
         free_slots_.push_back(r.slot);
         reads_.erase(it);
       }
