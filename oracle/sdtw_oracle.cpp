@@ -18,7 +18,7 @@
 //     followed by those of the reverse complement; z-score normalisation of
 //     the reference and of every query; fixed-point scaling by a power of two.
 //
-// Readings where the paper is silent (each also listed in the design doc):
+// Readings where the paper is silent:
 //   * z-score: population standard deviation; mean and variance accumulated in
 //     double, in blocks of 4096 consecutive samples summed in index order, the
 //     block sums added in index order; z = (float)((x - mean) / sigma);
