@@ -291,6 +291,15 @@ def run_serving(haru, args, local, w, threshold):
             "decisions_per_s": len(results) / span, "gcups": len(results) * 250 * N / span / 1e9,
             "accept_eject_accuracy_vs_truth": acc, "batches": st["batches"], "max_batch": st["max_batch"],
             "max_concurrent_batches": st["max_concurrent"], "late_chunks": late, "clocks": clk.summary(),
+            "stages": {"max_upload_ms": st["max_upload_ns"] / 1e6, "max_queue_ms": st["max_queue_ns"] / 1e6,
+                       "max_gpu_ms": st["max_gpu_ns"] / 1e6, "over_10ms_upload": st["slow_upload"],
+                       "over_10ms_queue": st["slow_queue"], "over_10ms_gpu": st["slow_gpu"],
+                       "max_upload_sync_ms": st["max_upload_sync_ns"] / 1e6,
+                       "max_worker_turn_gap_ms": st["max_turn_gap_ns"] / 1e6,
+                       "worst_turn_ms": {k: st["worst_turn_" + k + "_ns"] / 1e6
+                                         for k in ("complete", "upload", "launch", "wait")},
+                       "worst_turn_switches": {"voluntary": st["worst_turn_voluntary_switches"],
+                                               "involuntary": st["worst_turn_involuntary_switches"]}},
             "latency_clock": "chunk delivery that completes the prefix -> decision available (CLOCK_MONOTONIC); "
                              "library_*: the library's receipt of that chunk -> decision available"}
 

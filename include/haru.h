@@ -98,6 +98,9 @@ typedef struct {
                                codes in FP32 instead (identical results: saturating every cell equals
                                saturating the exact cost once), to load the FMA pipe as well as the
                                half-rate min/DPX pipe. Measured slower on GB300; kept as an option. */
+  int serve_spin_us;        /* serving: microseconds the worker keeps polling after its last piece of
+                               work before it sleeps (a sleeping thread can be woken late on a busy
+                               host); 0 = 2000, negative = never poll idle */
 } haru_config;
 
 /* Fill *cfg with defaults. Returns HARU_OK, or HARU_EINVAL if cfg is NULL. */
@@ -203,9 +206,12 @@ typedef struct {
  * read_id on channel. t_arrival_ns is the caller's CLOCK_MONOTONIC time of
  * delivery (it starts the decision-latency clock when this chunk completes
  * the prefix). last_chunk = 1 ends the read: a shorter prefix is decided as
- * is. Chunks after the prefix is complete are ignored. The first call starts
- * the serving thread. Errors: HARU_EINVAL, HARU_ENOREF, HARU_EBUSY (too many
- * events waiting on the host: poll, then retry), HARU_ECUDA. */
+ * is. Chunks after the prefix is complete are ignored. The call copies the
+ * events and hands them to the serving thread without waiting on it (a
+ * lock-free list), so a submitter is never held up by the serving loop and
+ * vice versa. The first call starts the serving thread. Errors: HARU_EINVAL,
+ * HARU_ENOREF, HARU_ENOMEM, HARU_EBUSY (too many events waiting on the host:
+ * poll, then retry), HARU_ECUDA. */
 int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const float *events, uint32_t n,
                        uint64_t t_arrival_ns, int last_chunk);
 
@@ -223,6 +229,21 @@ typedef struct {
   uint64_t max_batch;         /* largest batch launched */
   uint64_t max_concurrent;    /* most batches on the GPU at once */
   uint64_t slots;             /* device slots the budget allows */
+  /* where decided reads spent their time (for latency diagnosis), per stage
+   * the longest time seen and how many reads took over 10 ms there:
+   * upload = the completing chunk received -> all events on the device and
+   * the read queued; queue = queued -> launched in a batch; gpu = launched
+   * -> the batch's completion seen by the worker */
+  uint64_t max_upload_ns, max_queue_ns, max_gpu_ns;
+  uint64_t slow_upload, slow_queue, slow_gpu;
+  /* the longest wait for an upload transfer to finish, and the longest gap
+   * between two turns of the worker loop */
+  uint64_t max_upload_sync_ns, max_turn_gap_ns;
+  /* the slowest turn: time in its complete / upload / launch / idle-wait
+   * parts, and the worker thread's voluntary and involuntary context
+   * switches during it (Linux; 0 elsewhere) */
+  uint64_t worst_turn_complete_ns, worst_turn_upload_ns, worst_turn_launch_ns, worst_turn_wait_ns;
+  uint64_t worst_turn_voluntary_switches, worst_turn_involuntary_switches;
 } haru_stream_stats;
 int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
 

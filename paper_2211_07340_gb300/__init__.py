@@ -62,6 +62,7 @@ class haru_config(ctypes.Structure):
         ("single_kernel", ctypes.c_int),
         ("stack_short", ctypes.c_int),
         ("int16_exact_share", ctypes.c_int),
+        ("serve_spin_us", ctypes.c_int),
     ]
 
 
@@ -80,7 +81,12 @@ class haru_result(ctypes.Structure):
 class haru_stream_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("reads_submitted", "reads_decided", "reads_waiting",
                                                "reads_in_flight", "batches", "max_batch", "max_concurrent",
-                                               "slots")]
+                                               "slots", "max_upload_ns", "max_queue_ns", "max_gpu_ns",
+                                               "slow_upload", "slow_queue", "slow_gpu", "max_upload_sync_ns",
+                                               "max_turn_gap_ns", "worst_turn_complete_ns", "worst_turn_upload_ns",
+                                               "worst_turn_launch_ns", "worst_turn_wait_ns",
+                                               "worst_turn_voluntary_switches",
+                                               "worst_turn_involuntary_switches")]
 
 
 _lib = None

@@ -20,10 +20,13 @@
 // and polls events without blocking.
 
 #include <cuda_runtime.h>
+#include <sys/resource.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 
@@ -31,6 +34,20 @@
 
 namespace haru {
 namespace {
+
+// Voluntary and involuntary context switches of the calling thread so far.
+void thread_switches(long *vol, long *invol) {
+#ifdef RUSAGE_THREAD
+  struct rusage ru;
+  if (getrusage(RUSAGE_THREAD, &ru) == 0) {
+    *vol = ru.ru_nvcsw;
+    *invol = ru.ru_nivcsw;
+    return;
+  }
+#endif
+  *vol = 0;
+  *invol = 0;
+}
 
 uint64_t now_ns() {
   return static_cast<uint64_t>(
@@ -91,6 +108,8 @@ class Server {
     float lo = 0.0f, hi = 0.0f;  // range of the accepted events (a flat prefix has no z-score)
     uint64_t t_arrival = 0;
     uint64_t t_received = 0;
+    uint64_t t_queued = 0;
+    uint64_t t_launched = 0;
   };
   struct BatchCtx {
     Workspace ws;
@@ -110,7 +129,21 @@ class Server {
     bool busy = false;
   };
 
+  // A chunk handed over by submit (events copied), on the intake list.
+  struct Chunk {
+    Chunk *next;
+    uint64_t read_id;
+    uint64_t t_arrival;
+    uint64_t t_received;
+    uint32_t channel;
+    uint32_t n;
+    int last;
+    float ev[1];  // n events (allocated past the struct)
+  };
+
   void worker();
+  void drain_intake();
+  void take_chunk(const Chunk *c);
   int turn_upload();
   int turn_launch();
   int turn_complete();
@@ -119,13 +152,17 @@ class Server {
   haru_ctx *ctx_;
   std::thread thread_;
   std::atomic<bool> run_{false};
-  std::mutex mu_;                       // reads_, pending chunks, admission queue
+  std::mutex mu_;                       // reads_ and the queues (the worker; stats() reads them)
   std::condition_variable cv_work_;
+  // submit pushes chunks here without a lock (newest first); the worker
+  // takes the whole list each turn, so neither side ever waits for the other
+  std::atomic<Chunk *> intake_{nullptr};
+  std::atomic<size_t> intake_events_{0};
   std::unordered_map<uint64_t, Read> reads_;
   std::deque<uint64_t> admit_q_;        // reads waiting for a slot
   std::deque<uint64_t> ready_q_;        // admitted reads with complete prefix, uploaded
   std::vector<int> free_slots_;
-  size_t host_events_ = 0;              // events held on the host
+  std::atomic<size_t> host_events_{0};  // events held on the host (taken from the intake)
   std::mutex out_mu_;
   std::condition_variable cv_out_;
   std::deque<haru_result> done_q_;
@@ -153,6 +190,15 @@ class Server {
 
   // stats
   std::atomic<uint64_t> n_submitted_{0}, n_decided_{0}, n_batches_{0}, max_batch_seen_{0}, max_conc_{0};
+  // per-stage latency diagnosis (worker thread writes, stats() reads)
+  std::atomic<uint64_t> max_stage_[3] = {{0}, {0}, {0}}, slow_stage_[3] = {{0}, {0}, {0}};
+  std::atomic<uint64_t> max_sync_{0}, max_gap_{0};
+  uint64_t spin_ns_ = 0;  // keep polling this long after the last piece of work
+  std::atomic<uint64_t> worst_[6] = {{0}, {0}, {0}, {0}, {0}, {0}};  // parts of the slowest turn
+  void note_stage(int k, uint64_t dt) {
+    if (dt > max_stage_[k]) max_stage_[k] = dt;
+    if (dt > 10000000ull) slow_stage_[k]++;
+  }
 };
 
 int Server::start() {
@@ -161,6 +207,7 @@ int Server::start() {
   if (prefix_ < 1 || prefix_ > HARU_MAX_QUERY) return HARU_EINVAL;
   slot_len_ = (prefix_ + 31) / 32 * 32;
   max_batch_ = c.serve_max_batch ? static_cast<int>(c.serve_max_batch) : 1024;
+  spin_ns_ = c.serve_spin_us < 0 ? 0 : 1000ull * static_cast<uint64_t>(c.serve_spin_us ? c.serve_spin_us : 2000);
   precision_ = c.serve_precision == HARU_FP32 ? HARU_FP32 : HARU_INT16;
   threshold_ = c.threshold;
   const size_t budget = c.serve_budget_bytes ? c.serve_budget_bytes : (64u << 20);
@@ -215,6 +262,11 @@ void Server::stop() {
     cv_work_.notify_all();
     if (thread_.joinable()) thread_.join();
   }
+  for (Chunk *c = intake_.exchange(nullptr); c;) {  // chunks never taken
+    Chunk *nx = c->next;
+    std::free(c);
+    c = nx;
+  }
   cudaSetDevice(ctx_->device);
   for (auto &b : batches_) {
     if (b.stream) cudaStreamSynchronize(b.stream);
@@ -255,20 +307,61 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
     if (error_ != HARU_OK) return error_;
   }
   if (n > 0 && !ev) return HARU_EINVAL;
+  if (intake_events_.load() + host_events_.load() + n > stage_cap_ * 4) return HARU_EBUSY;
+  Chunk *c = static_cast<Chunk *>(std::malloc(offsetof(Chunk, ev) + sizeof(float) * std::max<uint32_t>(n, 1)));
+  if (!c) return HARU_ENOMEM;
+  c->read_id = read_id;
+  c->t_arrival = t_arrival;
+  c->channel = channel;
+  c->n = n;
+  c->last = last;
+  if (n) std::memcpy(c->ev, ev, sizeof(float) * n);
+  intake_events_ += n;
+  c->t_received = now_ns();
+  Chunk *head = intake_.load(std::memory_order_relaxed);
+  do {
+    c->next = head;
+  } while (!intake_.compare_exchange_weak(head, c, std::memory_order_release, std::memory_order_relaxed));
+  cv_work_.notify_one();
+  return HARU_OK;
+}
+
+// Worker: take every chunk submitted so far, in submission order.
+void Server::drain_intake() {
+  Chunk *list = intake_.exchange(nullptr, std::memory_order_acquire);
+  if (!list) return;
+  Chunk *ord = nullptr;
+  while (list) {
+    Chunk *nx = list->next;
+    list->next = ord;
+    ord = list;
+    list = nx;
+  }
   std::lock_guard<std::mutex> lk(mu_);
-  if (host_events_ + n > stage_cap_ * 4) return HARU_EBUSY;
-  auto it = reads_.find(read_id);
+  while (ord) {
+    Chunk *nx = ord->next;
+    take_chunk(ord);
+    intake_events_ -= ord->n;
+    std::free(ord);
+    ord = nx;
+  }
+}
+
+// Worker, under mu_: append a chunk's events to its read (up to the prefix).
+void Server::take_chunk(const Chunk *c) {
+  auto it = reads_.find(c->read_id);
   if (it == reads_.end()) {
     Read r;
-    r.id = read_id;
-    r.channel = channel;
-    it = reads_.emplace(read_id, std::move(r)).first;
-    admit_q_.push_back(read_id);
+    r.id = c->read_id;
+    r.channel = c->channel;
+    it = reads_.emplace(c->read_id, std::move(r)).first;
+    admit_q_.push_back(c->read_id);
     n_submitted_++;
   }
   Read &r = it->second;
-  if (r.complete) return HARU_OK;  // later chunks of a decided prefix are not needed
-  const uint32_t take = std::min<uint32_t>(n, static_cast<uint32_t>(prefix_) - r.total);
+  if (r.complete) return;  // later chunks of a decided prefix are not needed
+  const float *ev = c->ev;
+  const uint32_t take = std::min<uint32_t>(c->n, static_cast<uint32_t>(prefix_) - r.total);
   for (uint32_t i = 0; i < take; ++i) {
     const float x = ev[i];
     if (!std::isfinite(x)) r.bad = true;
@@ -279,10 +372,10 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
   r.host.insert(r.host.end(), ev, ev + take);
   host_events_ += take;
   r.total += take;
-  if (r.total >= static_cast<uint32_t>(prefix_) || last) {
+  if (r.total >= static_cast<uint32_t>(prefix_) || c->last) {
     r.complete = true;
-    r.t_arrival = t_arrival;
-    r.t_received = now_ns();
+    r.t_arrival = c->t_arrival;
+    r.t_received = c->t_received;
     if (r.bad || r.total < 2 || !(r.hi > r.lo) || r.total > static_cast<uint32_t>(ref_.N)) {
       // no z-score or no alignment for this prefix: decided (eject) without the GPU
       haru_result o;
@@ -292,7 +385,7 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
       o.status = HARU_EINVAL;
       o.events = r.total;
       o.end_col = -1;
-      o.t_arrival_ns = t_arrival;
+      o.t_arrival_ns = r.t_arrival;
       o.t_done_ns = now_ns();
       o.t_received_ns = r.t_received;
       host_events_ -= r.host.size();
@@ -306,11 +399,8 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
       }
       n_decided_++;
       cv_out_.notify_all();
-      return HARU_OK;
     }
   }
-  cv_work_.notify_one();
-  return HARU_OK;
 }
 
 int Server::poll(haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us) {
@@ -336,6 +426,20 @@ void Server::stats(haru_stream_stats *out) {
   out->batches = n_batches_;
   out->max_batch = max_batch_seen_;
   out->max_concurrent = max_conc_;
+  out->max_upload_ns = max_stage_[0];
+  out->max_queue_ns = max_stage_[1];
+  out->max_gpu_ns = max_stage_[2];
+  out->slow_upload = slow_stage_[0];
+  out->slow_queue = slow_stage_[1];
+  out->slow_gpu = slow_stage_[2];
+  out->max_upload_sync_ns = max_sync_;
+  out->max_turn_gap_ns = max_gap_;
+  out->worst_turn_complete_ns = worst_[0];
+  out->worst_turn_upload_ns = worst_[1];
+  out->worst_turn_launch_ns = worst_[2];
+  out->worst_turn_wait_ns = worst_[3];
+  out->worst_turn_voluntary_switches = worst_[4];
+  out->worst_turn_involuntary_switches = worst_[5];
   out->slots = static_cast<uint64_t>(nslots_);
   std::lock_guard<std::mutex> lk(mu_);
   out->reads_waiting = admit_q_.size();
@@ -348,6 +452,7 @@ void Server::stats(haru_stream_stats *out) {
 // Admit waiting reads to free slots and copy every host-held event of an
 // admitted read to its slot (one staged transfer and one scatter kernel).
 int Server::turn_upload() {
+  drain_intake();
   std::vector<CopyOp> ops;
   size_t staged = 0;
   std::vector<uint64_t> finished;
@@ -394,15 +499,26 @@ int Server::turn_upload() {
     }
     // the staging buffers are reused next turn: wait for this transfer
     if (e == cudaSuccess) e = cudaEventRecord(up_done_, up_stream_);
-    if (e == cudaSuccess) e = cudaEventSynchronize(up_done_);
+    // Poll for the transfer (a few tens of microseconds) rather than block
+    // in the driver; bounded by the context's wait limit.
+    const uint64_t ts = now_ns();
+    if (e == cudaSuccess) {
+      while ((e = cudaEventQuery(up_done_)) == cudaErrorNotReady) {
+        if (now_ns() - ts > lc_.wait_ns) return HARU_ETIMEDOUT;
+      }
+    }
+    const uint64_t dts = now_ns() - ts;
+    if (dts > max_sync_) max_sync_ = dts;
     if (e != cudaSuccess) return HARU_ECUDA;
   }
   if (!finished.empty()) {
     std::lock_guard<std::mutex> lk(mu_);
+    const uint64_t tq = now_ns();
     for (uint64_t id : finished) {
       Read &r = reads_[id];
       if (!r.queued) {
         r.queued = true;
+        r.t_queued = tq;
         ready_q_.push_back(id);
       }
     }
@@ -420,9 +536,11 @@ int Server::turn_launch() {
       if (ready_q_.empty()) return HARU_OK;
       b.reads.clear();
       b.h_off[0] = 0;
+      const uint64_t tl = now_ns();
       while (!ready_q_.empty() && n < static_cast<uint32_t>(max_batch_)) {
         Read &r = reads_[ready_q_.front()];
         ready_q_.pop_front();
+        r.t_launched = tl;
         b.reads.push_back(r.id);
         b.h_slot[n] = static_cast<uint32_t>(r.slot);
         b.h_off[n + 1] = b.h_off[n] + r.total;
@@ -486,6 +604,9 @@ int Server::turn_complete() {
         o.t_arrival_ns = r.t_arrival;
         o.t_done_ns = t;
         o.t_received_ns = r.t_received;
+        note_stage(0, r.t_queued - r.t_received);
+        note_stage(1, r.t_launched - r.t_queued);
+        note_stage(2, t - r.t_launched);
         free_slots_.push_back(r.slot);
         reads_.erase(it);
       }
@@ -506,20 +627,48 @@ void Server::worker() {
     fail(HARU_ECUDA);
     return;
   }
+  uint64_t t_prev = now_ns();
+  long vcs0 = 0, ics0 = 0;
+  thread_switches(&vcs0, &ics0);
+  uint64_t part[4] = {0, 0, 0, 0};
+  uint64_t t_work = now_ns();  // last turn that had work
   while (run_) {
+    const uint64_t t_turn = now_ns();
+    long vcs = 0, ics = 0;
+    thread_switches(&vcs, &ics);
+    if (t_turn - t_prev > max_gap_) {  // the previous turn was the slowest so far
+      max_gap_ = t_turn - t_prev;
+      for (int k = 0; k < 4; ++k) worst_[k] = part[k];
+      worst_[4] = static_cast<uint64_t>(vcs - vcs0);
+      worst_[5] = static_cast<uint64_t>(ics - ics0);
+    }
+    t_prev = t_turn;
+    vcs0 = vcs;
+    ics0 = ics;
     int rc = turn_complete();
+    const uint64_t t1 = now_ns();
     if (rc == HARU_OK) rc = turn_upload();
+    const uint64_t t2 = now_ns();
     if (rc == HARU_OK) rc = turn_launch();
+    const uint64_t t3 = now_ns();
     if (rc != HARU_OK) {
       fail(rc);
       return;
     }
-    std::unique_lock<std::mutex> lk(mu_);
-    bool busy = false;
-    for (auto &b : batches_) busy = busy || b.busy;
-    const bool work = !ready_q_.empty() || host_events_ > 0;
-    if (!work)
-      cv_work_.wait_for(lk, std::chrono::microseconds(busy ? 50 : 200));
+    {
+      std::unique_lock<std::mutex> lk(mu_);
+      bool busy = false;
+      for (auto &b : batches_) busy = busy || b.busy;
+      const bool work = !ready_q_.empty() || host_events_ > 0 || intake_.load() != nullptr;
+      if (work || busy || !reads_.empty()) t_work = t3;
+      // poll (no sleep) while reads are in progress or within the spin window
+      if (!work && t3 - t_work >= spin_ns_)
+        cv_work_.wait_for(lk, std::chrono::microseconds(busy ? 50 : 200));
+    }
+    part[0] = t1 - t_turn;
+    part[1] = t2 - t1;
+    part[2] = t3 - t2;
+    part[3] = now_ns() - t3;
   }
 }
 

@@ -67,7 +67,11 @@ def test_header_constants_match_binding():
 def _struct_fields(txt, name):
     body = re.search(r"typedef struct \{([^{}]*)\} " + name + ";", txt).group(1)
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    return [re.findall(r"(\w+)\s*(?:\[\d+\])?$", d.strip())[0] for d in body.split(";") if d.strip()]
+    names = []
+    for decl in (d.strip() for d in body.split(";") if d.strip()):
+        # "type a" or "type a, b, c": every declarator's name, in order
+        names += [re.findall(r"(\w+)\s*(?:\[\d+\])?$", part.strip())[0] for part in decl.split(",")]
+    return names
 
 
 @pytest.mark.parametrize("cname,pyname", [("haru_config", "haru_config"), ("haru_result", "haru_result"),
