@@ -238,8 +238,9 @@ def test_autotuner_keeps_results(haru, sars):
     qs = synth.workload("sars_uneven_8192", nq=600).queries
     with haru.Context() as ctx:
         ctx.ref_load(ref)
-        before = [ctx.sdtw_batch(p, qs.events, qs.offsets) for p in (haru.HARU_INT16, haru.HARU_FP32)]
-        for i, p in enumerate((haru.HARU_INT16, haru.HARU_FP32)):
+        forms = (haru.HARU_INT16, haru.HARU_FP32, haru.HARU_INT16_ACC32)
+        before = [ctx.sdtw_batch(p, qs.events, qs.offsets) for p in forms]
+        for i, p in enumerate(forms):
             chosen = ctx.autotune(p, qs.events, qs.offsets)
             assert chosen["warps_per_cta"] in (4, 8) and chosen["tile_cols"] in (2048, 4096, 8192, 16384)
             c, j = ctx.sdtw_batch(p, qs.events, qs.offsets)

@@ -104,3 +104,24 @@ def test_flat_and_short_reads_are_rejected_alone(haru, ref):
         assert got[2].status == haru.HARU_EINVAL
         assert got[3].status == 0
         assert ctx.stream_poll(16, 1000) == []  # nothing pending: times out empty
+
+
+def test_stage_counters_and_idle_sleeping_worker(haru, ref):
+    """With serve_spin_us < 0 the worker sleeps between turns; decisions
+    still come back, and the per-stage counters account for them."""
+    q = synth.flowcell_schedule(4, 3.0, seed=9)[1]
+    with haru.Context(serve_spin_us=-1) as ctx:
+        ctx.ref_load(ref)
+        t = time.monotonic_ns()
+        for i in range(min(q.nq, 6)):
+            assert ctx.stream_submit(100 + i, i, q.query(i), t, True) == 0
+        got = {}
+        deadline = time.monotonic() + 10
+        while len(got) < min(q.nq, 6) and time.monotonic() < deadline:
+            for r in ctx.stream_poll(16, 1000):
+                got[r.read_id] = r
+        st = ctx.stream_stats()
+    assert len(got) == min(q.nq, 6)
+    assert all(r.t_arrival_ns <= r.t_received_ns <= r.t_done_ns for r in got.values())
+    assert st["reads_decided"] == len(got) and st["batches"] >= 1
+    assert st["max_gpu_ns"] > 0 and st["max_turn_gap_ns"] > 0
