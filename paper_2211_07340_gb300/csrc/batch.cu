@@ -43,8 +43,9 @@ WsNeeds ws_needs(int precision, uint32_t nq, const LaunchCfg &lc) {
   // queries per item); the segment cap is sized for that case.
   const size_t items_min = (mode == 0 || mode == 3) ? (static_cast<size_t>(nq) + 1) / 2
                            : (mode == 1 ? (static_cast<size_t>(nq) + 3) / 4 : (3 * static_cast<size_t>(nq)) / 4);
+  // (twice that: the planner doubles the segments of the queue's tail)
   w.nseg_cap = static_cast<int>(std::min<size_t>(
-      kMaxSeg, (static_cast<size_t>(w.units_target) + items_min - 1) / std::max<size_t>(items_min, 1)));
+      kMaxSeg, 2 * ((static_cast<size_t>(w.units_target) + items_min - 1) / std::max<size_t>(items_min, 1))));
   if (w.nseg_cap < 1 || prec_span(precision)) w.nseg_cap = 1;  // start-column forms sweep unsegmented
   w.units = w.max_items * static_cast<size_t>(w.nseg_cap);
   w.qstats = 2 * static_cast<size_t>(nq);

@@ -184,6 +184,20 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
     int want = base > 0 ? (a.units_target + base - 1) / base : 1;
     if (want < 1) want = 1;
     if (want > a.nseg_cap) want = a.nseg_cap;
+    // The buckets at the end of the longest-first queue (the cheapest strips,
+    // up to a fifth of the work) get twice the segments: shorter final work
+    // units leave less of the machine idle while the last ones finish.
+    long total = 0, acc = 0;
+    for (int S = 1; S <= kMaxS; ++S) total += static_cast<long>(icount[S]) * S;
+    int tail_to = 0;  // buckets S <= tail_to form the tail
+    if (a.units_target > 1) {
+      for (int S = 1; S <= kMaxS; ++S) {
+        const long w = static_cast<long>(icount[S]) * S;
+        if ((acc + w) * 5 > total) break;
+        acc += w;
+        tail_to = S;
+      }
+    }
     int g = 0;
     for (int c = 0; c < kClasses; ++c) {
       a.ints[kIntClassFirst + c] = g;
@@ -196,7 +210,9 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         const long minlen = 4 * warmup_steps(S) > 2048 ? 4 * warmup_steps(S) : 2048;
         long lim = sweep_steps(S, a.N) / minlen;
         if (lim < 1) lim = 1;
-        nseg_of[S] = want < lim ? want : static_cast<int>(lim);
+        int ws = S <= tail_to ? 2 * want : want;
+        if (ws > a.nseg_cap) ws = a.nseg_cap;
+        nseg_of[S] = ws < lim ? ws : static_cast<int>(lim);
         gbase[S] = g;
         gcount[S] = nseg_of[S] * ((icount[S] + a.warps - 1) / a.warps);
         g += gcount[S];
