@@ -118,7 +118,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   pa.single = lc.single_kernel ? 1 : 0;
   // Auto stacking: when the batch alone fills the unit target, or when its
   // stacked items (up to four queries each) cut into reference segments
-  // (at most 64, each at least 8,192 steps: four warm-ups of a 16-row strip)
+  // (at most 64, each counted as 8,192 steps: about four warm-ups of a 16-row strip)
   // still do; small batches on short references stay unstacked for latency.
   const long seg_room = std::min<long>(kMaxSeg, ref.N / 8192);
   const bool fills = nq >= static_cast<uint32_t>(ws.units_target) ||

@@ -99,10 +99,13 @@ __host__ __device__ inline int tile_width(int S, int T) {
   return w > 0 ? w : L;
 }
 
-// Warm-up steps of a speculative segment: four strip heights of rows.
+// Steps a speculative segment runs before its own first step: three strip
+// heights, so even the strip's last row has two heights of columns behind
+// it (alignments span fewer columns than rows here; a segment whose start
+// state still differs is recomputed by the fix-up kernel).
 __host__ __device__ inline long warmup_steps(int S) {
   const int U = steps_per_chunk(S);
-  return (4L * 32 * S + U - 1) / U * U;
+  return (3L * 32 * S + U - 1) / U * U;
 }
 
 // Whole-chunk step count of one sweep of strip height S over N columns.
