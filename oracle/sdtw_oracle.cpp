@@ -29,6 +29,12 @@
 //     stands for infinity: gamma = min(CAP, delta + min3(...)).
 //   * end column: 0-based index into the concatenated reference; ties go to
 //     the smallest column.
+//   * wide accumulation (the PE of Section 4.3: 16-bit samples, 32-bit cost
+//     registers): the exact integer DP of the quantised samples, unsaturated.
+//   * start column (the paper drops backtracking): carried forward; among
+//     minimum-cost predecessors a cell keeps the up one's start, else the
+//     diagonal one's, else the left one's; a path entering row 1 at column j
+//     starts at j.
 //
 // Parity pins live in tests/ (brute-force path enumeration, exact copies,
 // closed-form special cases, bounds, algorithm equivalences).
