@@ -107,7 +107,10 @@ __global__ void ref_finish_kernel(const float *x, size_t n, const double *stats,
 __device__ __forceinline__ int sdtw_class_dev(int S) { return S >= 13 ? 0 : (S >= 9 ? 1 : (S >= 5 ? 2 : 3)); }
 
 // Bucket key of query q: its strip height S (rows per lane), plus kMaxS + 1
-// if it is stacked (16 lanes, S = ceil(M / 16)); 0 for an invalid length.
+// if it is stacked (16 lanes); 0 for an invalid length. S is the least
+// height that leaves a pad row on top of the query (S = floor(M / 32) + 1,
+// or floor(M / 16) + 1 stacked), at most kMaxS: the sweep relies on that
+// row to hold the free-start zero in strips lower than kMaxS.
 __device__ __forceinline__ int bucket_key(const uint32_t *off, uint32_t q, long N, int mode, int stack, int *status) {
   const uint32_t m = off[q + 1] - off[q];
   const long lim = N < HARU_MAX_QUERY ? N : HARU_MAX_QUERY;
@@ -115,8 +118,9 @@ __device__ __forceinline__ int bucket_key(const uint32_t *off, uint32_t q, long 
     if (status) report(status, HARU_EINVAL);
     return 0;
   }
-  if (stack && mode != 2 && m <= static_cast<uint32_t>(kStackMax)) return static_cast<int>((m + 15) / 16) + kMaxS + 1;
-  return static_cast<int>((m + 31) / 32);
+  if (stack && mode != 2 && m <= static_cast<uint32_t>(kStackMax))
+    return min(static_cast<int>(m / 16) + 1, kMaxS) + kMaxS + 1;
+  return min(static_cast<int>(m / 32) + 1, kMaxS);
 }
 
 // Items of a bucket of n queries. Mode 2 (int16 split over both pipes)

@@ -2,7 +2,8 @@
 // of Section 4.3 / Fig. 5, mapped onto warps).
 //
 // Layout of one warp's work. A query of M events is padded at the top to
-// 32 * S rows (S = ceil(M / 32)); lane l holds rows l*S .. l*S + S - 1 in
+// 32 * S rows (S = floor(M / 32) + 1, at most 16, so that a strip lower than
+// 16 rows per lane has at least one pad row); lane l holds rows l*S .. l*S + S - 1 in
 // registers. Row i processes reference column t - i at step t, so every row
 // is one processing element of the paper's PE chain and the whole strip is
 // one oblique column: the S cells of a lane in one step are independent
@@ -14,6 +15,9 @@
 // N + 32*S - 1 steps, the paper's N + M - 1 (Section 4.3) for the padded
 // height. Pad rows sit above the query and hold exactly 0, the free-start
 // boundary row, so the last query row is always lane 31's last register.
+// A pad row's minimum includes its own 0, so whatever lane 0 receives from
+// above is absorbed there, and only full-height strips (16 rows per lane,
+// no pad row) have lane 0 replace that value by the zero.
 //
 // INT16 form: two queries share a warp, one per 16-bit half (DPX
 // __viaddmax_s16x2_relu for |q - r|, __vimin3_u16x2, and __viaddmin_u16x2 on
@@ -131,6 +135,25 @@ struct RefWindow {
   }
 };
 
+// The tracked lane's last-row value of step u goes to ring[e0 + u]. Values
+// are held for four steps (two when U is not a multiple of four; U is always
+// even) and written by one vector store: e0 is a multiple of U and the ring
+// is 16-byte aligned, so every store is aligned.
+template <int U>
+struct RingStore {
+  static constexpr int W = U % 4 == 0 ? 4 : 2;
+  uint32_t v[W];
+  __device__ __forceinline__ void put(uint32_t *ring, int e0, int u, bool tracked, uint32_t x) {
+    v[u % W] = x;
+    if (u % W == W - 1 && tracked) {
+      if constexpr (W == 4)
+        *reinterpret_cast<uint4 *>(ring + e0 + u - 3) = make_uint4(v[0], v[1], v[2], v[3]);
+      else
+        *reinterpret_cast<uint2 *>(ring + e0 + u - 1) = make_uint2(v[0], v[1]);
+    }
+  }
+};
+
 template <int S>
 struct Geo {
   static constexpr int U = (S % 2 == 0) ? S : 2 * S;    // steps per unrolled chunk (register renaming period)
@@ -208,6 +231,7 @@ struct StripI16 {
                                         uint32_t nr, bool tracked, int, int) {
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
+    RingStore<U> out;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int p = (S - (u % S)) % S;
@@ -216,7 +240,12 @@ struct StripI16 {
       uint32_t gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
       uint32_t rin = __shfl_up_sync(kFull, Rr[p], 1);
       const uint32_t rv = win.get(ref, u);
-      gup = imad(gup, ng, 0u);  // a stack's first lane: the free-start row, 0
+      // A stack's first lane needs the free-start row, 0, above it. Strips
+      // of fewer than kMaxS rows per lane are planned with a pad row on top
+      // of every stack, which stays 0 whatever comes from above (its own
+      // previous value, 0, is in the minimum), so only full-height strips
+      // put the zero in.
+      if constexpr (S == kMaxS) gup = imad(gup, ng, 0u);
       rin = imad(rin, nr, rv);  // lane 0: reference sample t (other lanes read zeros)
       Rr[p] = rin;
 #pragma unroll
@@ -231,7 +260,7 @@ struct StripI16 {
         G[b][k] = v;
       }
       gprev = gup;
-      if (tracked) ring[e0 + u] = G[b][S - 1];
+      out.put(ring, e0, u, tracked, G[b][S - 1]);
     }
   }
 };
@@ -316,7 +345,7 @@ struct StripF32 {
     (void)trel;
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
-    float *fring = reinterpret_cast<float *>(ring);
+    RingStore<U> out;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int p = (S - (u % S)) % S;
@@ -325,8 +354,11 @@ struct StripF32 {
       float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
       float rin = __shfl_up_sync(kFull, Rr[p], 1);
       const float rv = ref_value(win.get(ref, u));
-      gup = ng ? gup : 0.0f;  // a stack's first lane: the free-start row, 0
-      rin = nr ? rin : rv;    // lane 0: reference sample t
+      // The free-start row above a stack's first lane: a pad row on top of
+      // the stack (weight 0, value 0) keeps it for strips of fewer than
+      // kMaxS rows per lane, as in the int16 strip.
+      if constexpr (S == kMaxS) gup = ng ? gup : 0.0f;
+      rin = nr ? rin : rv;  // lane 0: reference sample t
       Rr[p] = rin;
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
@@ -338,7 +370,7 @@ struct StripF32 {
         G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
       }
       gprev = gup;
-      if (tracked) fring[e0 + u] = G[b][S - 1];
+      out.put(ring, e0, u, tracked, __float_as_uint(G[b][S - 1]));
     }
   }
 };
@@ -957,7 +989,7 @@ constexpr int kFixWarps = 4;
 
 template <int PREC, int CLS>
 __global__ void __launch_bounds__(kFixWarps * 32) fixup_kernel(SdtwArgs A) {
-  __shared__ uint32_t rings[kFixWarps * ring_words(PREC)];
+  __shared__ __align__(16) uint32_t rings[kFixWarps * ring_words(PREC)];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int first = A.ints[kIntClassItemFirst + slot_of<CLS>()];
   const int count = A.ints[kIntClassItemCount + slot_of<CLS>()];

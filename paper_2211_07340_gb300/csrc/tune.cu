@@ -5,8 +5,9 @@
 // reference tile width, the work-unit target (how finely sweeps are cut
 // into verified reference segments; 1 = never cut) and whether one sweep
 // kernel covers every strip height or four class kernels run side by side. The
-// strip height is not a free choice here: S = ceil(M / 32) rows per lane is
-// the smallest strip that holds a query, and a taller one only adds padding.
+// strip height is not a free choice here: S = floor(M / 32) + 1 rows per
+// lane (at most 16) is the smallest strip that holds a query with a pad row
+// on top, and a taller one only adds padding.
 
 #include <cuda_runtime.h>
 
