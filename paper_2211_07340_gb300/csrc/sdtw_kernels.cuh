@@ -107,6 +107,14 @@ __device__ __forceinline__ float fmin3f(float a, float b, float c) {
   return d;
 }
 
+// x == m ? a : b as a compare and a select (never a branch).
+__device__ __forceinline__ int sel_eq(float x, float m, int a, int b) {
+  int d;
+  asm("{\n\t.reg .pred p;\n\tsetp.eq.f32 p, %1, %2;\n\tselp.b32 %0, %3, %4, p;\n\t}"
+      : "=r"(d) : "f"(x), "f"(m), "r"(a), "r"(b));
+  return d;
+}
+
 // d = a * b + c on the integer multiply-add unit (keeps lane-0 fix-ups off
 // the half-rate pipe that the DPX min/max instructions use).
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
@@ -499,14 +507,14 @@ struct StripF32Span {
       for (int k = S - 1; k >= 0; --k) {
         const float r = Rr[(p + k) % S];
         const float d = __fsub_rn(Q[k], r);
-        float m = k ? G[a][k - 1] : gup;
-        int pm = k ? P[a][k - 1] : pup;
+        const float up = k ? G[a][k - 1] : gup;
+        const int pu = k ? P[a][k - 1] : pup;
         const float dg = k ? G[b][k - 1] : gprev;
         const int pd = k ? P[b][k - 1] : pprev;
-        if (dg < m) { m = dg; pm = pd; }
-        if (G[a][k] < m) { m = G[a][k]; pm = P[a][k]; }
+        const float m = fmin3f(up, dg, G[a][k]);
+        // The start of the preferred minimum predecessor: up, else diagonal, else left.
         G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
-        P[b][k] = pm;
+        P[b][k] = sel_eq(up, m, pu, sel_eq(dg, m, pd, P[a][k]));
       }
       gprev = gup;
       pprev = pup;
