@@ -611,7 +611,7 @@ def main():
                         if msw == msw else None),
         "fp32_start_columns": ({"value": total_cells / (span_ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": span_ms,
                                 "note": "FP32 with each alignment's start column (haru_sdtw_batch_span): "
-                                        "direct launches, default launch shape, unsegmented"}
+                                        "direct launches, default launch shape"}
                                if span_ms == span_ms else None),
         "int16_over_fp32": value / value32 if value32 == value32 else None,
         "prep_ms_per_step": ms16 - sweep16,

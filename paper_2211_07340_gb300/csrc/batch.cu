@@ -46,10 +46,10 @@ WsNeeds ws_needs(int precision, uint32_t nq, const LaunchCfg &lc) {
   // (twice that: the planner doubles the segments of the queue's tail)
   w.nseg_cap = static_cast<int>(std::min<size_t>(
       kMaxSeg, 2 * ((static_cast<size_t>(w.units_target) + items_min - 1) / std::max<size_t>(items_min, 1))));
-  if (w.nseg_cap < 1 || prec_span(precision)) w.nseg_cap = 1;  // start-column forms sweep unsegmented
+  if (w.nseg_cap < 1) w.nseg_cap = 1;
   w.units = w.max_items * static_cast<size_t>(w.nseg_cap);
   w.qstats = 2 * static_cast<size_t>(nq);
-  w.states = w.nseg_cap > 1 ? w.units * 2 * kStateStride : 0;
+  w.states = w.nseg_cap > 1 ? w.units * 2 * state_words(precision) : 0;
   return w;
 }
 

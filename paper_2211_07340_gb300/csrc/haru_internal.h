@@ -59,7 +59,8 @@ struct Best {
 // codes q and their negations -q, both -4095 on pad rows; FP32: query
 // samples and row weights, 1 on real rows and 0 on pad rows).
 constexpr int kImgStride = 2 * 16 * 32;
-// A saved strip state: the last two oblique columns, [2][S][32] words.
+// A saved strip state: the last two oblique columns, [2][S][32] words (the
+// start-column forms follow them with their start columns, as many words).
 constexpr int kStateStride = 2 * 16 * 32;
 constexpr int kMaxS = 16;
 constexpr int kMaxSeg = 64;
@@ -77,6 +78,8 @@ constexpr int kPrecF32Span = 3, kPrecWideSpan = 4;
 __host__ __device__ constexpr bool prec_span(int p) { return p == kPrecF32Span || p == kPrecWideSpan; }
 // Tracking-ring words per warp: costs (and start columns, +128, for the span forms).
 __host__ __device__ constexpr int ring_words(int p) { return prec_span(p) ? 256 : 128; }
+// Words of one saved strip state: costs, and start columns for the span forms.
+__host__ __device__ constexpr int state_words(int p) { return prec_span(p) ? 2 * kStateStride : kStateStride; }
 
 // Strip-height classes, tallest first: S in 13..16, 9..12, 5..8, 1..4; kernel
 // class 4 covers 1..16 in one kernel (single queue, planned into slot 0).

@@ -561,6 +561,10 @@ struct TrackF32Span {
 constexpr int kFormF32 = 0, kFormI16 = 1, kFormExact = 2, kFormExactWide = 3;
 // and the FP32 and wide forms carrying the start column
 constexpr int kFormF32Span = 4, kFormWideSpan = 5;
+// Rows of 32 words in a saved strip state, per strip row: two oblique
+// columns of costs, and of start columns in the span forms.
+template <int FORM>
+constexpr int state_rows_per_s() { return (FORM == kFormF32Span || FORM == kFormWideSpan) ? 4 : 2; }
 
 template <int FORM, int S>
 struct FormOf;
@@ -766,8 +770,9 @@ __device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, in
   st.fresh(t_start, lane);
   uint32_t *ss = nullptr, *sf = nullptr;
   const size_t unit = static_cast<size_t>(item) * A.nseg_cap + g.seg;
-  if (g.seg > 0) ss = A.states + (unit * 2 + 0) * kStateStride;
-  if (g.seg + 1 < g.nseg) sf = A.states + (unit * 2 + 1) * kStateStride;
+  constexpr size_t kWords = state_rows_per_s<FORM>() * 16 * 32;
+  if (g.seg > 0) ss = A.states + (unit * 2 + 0) * kWords;
+  if (g.seg + 1 < g.nseg) sf = A.states + (unit * 2 + 1) * kWords;
   const bool stk = A.items[item].stacked != 0;
   const bool ok =
       run_steps<FORM, S>(st, tr, ts, ts.tile_cols, t_start, t_own, t_end, true, A.N, ss, sf, ring, lane, stk);
@@ -934,18 +939,22 @@ __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane
     st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
     const int TS = tile_width(S, A.tile_cols);
     const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u;
+    constexpr int kRows = state_rows_per_s<FORM>();
+    constexpr size_t kWords = kRows * 16 * 32;
     for (int s = 1; s < nseg; ++s) {
-      const uint32_t *exact = A.states + ((base + s - 1) * 2 + 1) * kStateStride;
-      const uint32_t *spec = A.states + ((base + s) * 2 + 0) * kStateStride;
+      // The segment is exact iff its speculative start state (costs, and
+      // start columns in the span forms) equals the previous segment's final one.
+      const uint32_t *exact = A.states + ((base + s - 1) * 2 + 1) * kWords;
+      const uint32_t *spec = A.states + ((base + s) * 2 + 0) * kWords;
       bool eq = true;
-      for (int k = 0; k < 2 * S; ++k) eq = eq && exact[k * 32 + lane] == spec[k * 32 + lane];
+      for (int k = 0; k < kRows * S; ++k) eq = eq && exact[k * 32 + lane] == spec[k * 32 + lane];
       if (!__all_sync(kFull, eq)) {
         long t_start, t_own, t_end;
         seg_bounds(S, nseg, s, A.N, &t_start, &t_own, &t_end);
         st.restore(exact, reinterpret_cast<const uint32_t *>(A.ref_img), t_own, lane, ng);
         typename FormOf<FORM, S>::Track tr;
         GlobalTiles src{reinterpret_cast<const uint32_t *>(A.ref_img), TS, t_own / TS};
-        uint32_t *sf = s + 1 < nseg ? A.states + ((base + s) * 2 + 1) * kStateStride : nullptr;
+        uint32_t *sf = s + 1 < nseg ? A.states + ((base + s) * 2 + 1) * kWords : nullptr;
         run_steps<FORM, S>(st, tr, src, TS, t_own, t_own, t_end, false, A.N, nullptr, sf, ring, lane, stk);
         tr.reduce(stk ? 16 : 32);
         if (lane == 0) {

@@ -405,6 +405,41 @@ def test_start_columns(haru, sars, stack):
             ctx.sdtw_batch_span(haru.HARU_INT16, qs.events, qs.offsets)
 
 
+def test_start_columns_across_segments(haru):
+    """Start columns stay exact when a sweep is cut into speculative reference
+    segments: the only zero-cost path of the first query enters a 10,000-column
+    plateau two columns before it and crosses it on one row, so every segment
+    boundary inside the plateau fails verification and is recomputed. The same
+    batch cut into many segments and not cut at all gives the oracle's costs,
+    end columns and start columns."""
+    N = 60000
+    ref = synth.random_signal(N, seed=44, scale=1.0, loc=0.0)
+    c, e = np.float32(0.25), np.float32(-1.5)
+    ref[20000:30000] = c
+    ref[30000] = e
+    a, b = ref[19998], ref[19999]
+    rng = np.random.default_rng(45)
+    lengths = [4, 1, 33, 250, 511] + list(rng.integers(2, 513, size=11))
+    off = offsets_of(lengths)
+    ev = synth.random_signal(int(off[-1]), seed=46, scale=1.0, loc=0.0)
+    ev[:4] = [a, b, c, e]
+    for prec, oprec in ((haru.HARU_FP32, oracle.PREC_F32), (haru.HARU_INT16_ACC32, oracle.PREC_I32)):
+        o = oracle.batch(oprec, ref, ev, off, normalize_ref=False, normalize_q=False, start=True)
+        if prec == haru.HARU_FP32:
+            assert (o.cost[0], o.col[0], o.start[0]) == (0.0, 30000, 19998)
+        for units, segmented in ((1, False), (20000, True)):
+            with haru.Context(units_target=units) as ctx:
+                ctx.ref_load(ref, normalize=False)
+                cs, js, ss = ctx.sdtw_batch_span(prec, ev, off, raw=False)
+                st = ctx.last_stats()
+            assert (st["max_segments"] > 1) == segmented
+            if segmented:
+                assert st["fixups"] > 0
+            np.testing.assert_array_equal(cs, o.cost)
+            np.testing.assert_array_equal(js, o.col)
+            np.testing.assert_array_equal(ss, o.start)
+
+
 def test_start_columns_of_planted_copies(haru):
     N = 6000
     ref = synth.random_signal(N, seed=43, scale=1.0, loc=0.0)
