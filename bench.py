@@ -72,6 +72,17 @@ def profiled_traffic(form: str):
     return float(v) if v is not None else None
 
 
+def dram_rate(traffic, cells: float, gcups: float) -> dict:
+    """DRAM bytes per second of the sweep kernel (ncu traffic per batch over the
+    batch's sweep time at the achieved rate), against the measured HBM copy peak:
+    it shows the sweep is compute bound."""
+    if traffic is None or not gcups:
+        return {"dram_gbs": None}
+    gbs = traffic / (cells / (gcups * 1e9)) / 1e9
+    hbm = peaks_file().get("hbm_gbs")
+    return {"dram_gbs": gbs, "hbm_peak_gbs": hbm, "dram_frac_of_hbm": gbs / hbm if hbm else None}
+
+
 def alu_peak_gcups(sms: int, clock_mhz: float, form: str = "int16") -> float:
     """Peak cell rate of the sweep at the given SM clock, from pipe rates.
 
@@ -592,13 +603,15 @@ def main():
                      if clocks.get("sm_mhz") else None,
                      "peak_probe": probe16, "frac_of_probe": ach16 / probe16,
                      "peak_probe_basis": "haru_probe_peak: the int16 cell-pair instructions on independent "
-                                         "chains, no shuffles/reference/tracking, same run"},
+                                         "chains, no shuffles/reference/tracking, same run",
+                     **dram_rate(profiled_traffic("int16"), cells, ach16)},
         "fp32": {"value": value32, "unit": "GCUPS", "ms_per_step": ms32, "dtype": "f32",
                  "roofline": {"bound": "alu", "kernel": "sdtw_kernel<FP32>", "achieved": ach32, "peak": peak32,
                               "unit": "GCUPS", "frac": ach32 / peak32, "traffic": profiled_traffic("fp32"),
                               "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (3 issue slots per cell: sub, "
                                             f"3-input min, fma at 4 warp-instr/clk/SM) x {max_mhz:.0f} MHz",
-                              "peak_probe": probe32, "frac_of_probe": ach32 / probe32},
+                              "peak_probe": probe32, "frac_of_probe": ach32 / probe32,
+                              **dram_rate(profiled_traffic("fp32"), cells, ach32)},
                  "clocks": clocks32},
         "int16_exact_share": ({"value": total_cells / (msdpx / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": msdpx,
                                "sweep_gcups": cells / (sweepdpx / 1e3) / 1e9,
