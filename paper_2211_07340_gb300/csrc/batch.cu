@@ -170,11 +170,14 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   // streams are given, else one after the other on s; each is persistent
   // over its own part of the group list, then verifies its segments and
   // writes its queries' results.
-  if (lc.single_kernel || precision == HARU_INT16_ACC32 || prec_span(precision)) {  // these have the single kernel only
-    int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, kClassAll, lc.tile, lc.warps);
+  // The int16 form with an exact share (planner mode 2) runs its own kernel.
+  const int kprec = precision == HARU_INT16 && plan_mode(precision, lc) == 2 ? kPrecI16Mixed : precision;
+  if (lc.single_kernel || kprec == HARU_INT16_ACC32 || kprec == kPrecI16Mixed || prec_span(kprec)) {
+    // (these have the single kernel only)
+    int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(kprec, kClassAll, lc.tile, lc.warps);
     if (per_sm < 1) per_sm = 1;
     const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
-    return launch_sdtw(precision, kClassAll, sa, grid, static_cast<int>(ws.max_items), s);
+    return launch_sdtw(kprec, kClassAll, sa, grid, static_cast<int>(ws.max_items), s);
   }
   if (fj && fj->ok() && (e = cudaEventRecord(fj->fork, s)) != cudaSuccess) return e;
   for (int c = 0; c < kClasses; ++c) {

@@ -75,6 +75,10 @@ constexpr long kRefPad = 32 * kMaxS + kMaxTile + 64;
 // HARU_INT16 and HARU_INT16_ACC32: the FP32 and wide forms that also carry
 // each alignment's start column (haru_sdtw_batch_span).
 constexpr int kPrecF32Span = 3, kPrecWideSpan = 4;
+// The int16 form with its optional exact-integer share (int16_exact_share):
+// a kernel of its own, so that the plain int16 kernel holds the int16 strip
+// alone (one kernel, every strip height).
+constexpr int kPrecI16Mixed = 5;
 __host__ __device__ constexpr bool prec_span(int p) { return p == kPrecF32Span || p == kPrecWideSpan; }
 // Tracking-ring words per warp: costs (and start columns, +128, for the span forms).
 __host__ __device__ constexpr int ring_words(int p) { return prec_span(p) ? 256 : 128; }

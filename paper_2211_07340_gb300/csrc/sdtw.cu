@@ -25,6 +25,7 @@ HARU_SDTW_DECLARE(1, 4)
 HARU_SDTW_DECLARE(2, 4)
 HARU_SDTW_DECLARE(3, 4)
 HARU_SDTW_DECLARE(4, 4)
+HARU_SDTW_DECLARE(5, 4)
 
 namespace {
 #define HARU_SDTW_BOTH(P, C)                                                               \
@@ -40,7 +41,8 @@ cudaError_t launch_p1(int cls, const SdtwArgs &a, int grid, int fix_items, cudaS
     default: HARU_SDTW_BOTH(1, 3)
   }
 }
-// The wide form and the start-column forms have the single kernel only.
+// The wide form, the start-column forms and the int16 form with an exact
+// share have the single kernel only.
 cudaError_t launch_p2(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   cudaError_t e;
   HARU_SDTW_BOTH(2, 4)
@@ -52,6 +54,10 @@ cudaError_t launch_p3(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s
 cudaError_t launch_p4(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   cudaError_t e;
   HARU_SDTW_BOTH(4, 4)
+}
+cudaError_t launch_p5(const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
+  cudaError_t e;
+  HARU_SDTW_BOTH(5, 4)
 }
 cudaError_t launch_p0(int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s) {
   cudaError_t e;
@@ -75,6 +81,7 @@ int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps) {
   if (precision == HARU_INT16_ACC32) return sdtw_occupancy_2_4(tile_cols, warps);
   if (precision == kPrecF32Span) return sdtw_occupancy_3_4(tile_cols, warps);
   if (precision == kPrecWideSpan) return sdtw_occupancy_4_4(tile_cols, warps);
+  if (precision == kPrecI16Mixed) return sdtw_occupancy_5_4(tile_cols, warps);
   if (precision == HARU_INT16) {
     switch (cls) {
       case 0: return sdtw_occupancy_1_0(tile_cols, warps);
@@ -99,6 +106,7 @@ cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int
   if (precision == HARU_INT16_ACC32) return launch_p2(a, grid, fix_items, s);
   if (precision == kPrecF32Span) return launch_p3(a, grid, fix_items, s);
   if (precision == kPrecWideSpan) return launch_p4(a, grid, fix_items, s);
+  if (precision == kPrecI16Mixed) return launch_p5(a, grid, fix_items, s);
   return precision == HARU_INT16 ? launch_p1(cls, a, grid, fix_items, s) : launch_p0(cls, a, grid, fix_items, s);
 }
 

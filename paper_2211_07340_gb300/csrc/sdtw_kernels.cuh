@@ -146,7 +146,9 @@ struct RefWindow {
 // The tracked lane's last-row value of step u goes to ring[e0 + u]. Values
 // are held for four steps (two when U is not a multiple of four; U is always
 // even) and written by one vector store: e0 is a multiple of U and the ring
-// is 16-byte aligned, so every store is aligned.
+// is 16-byte aligned, so every store is aligned. The FP32 strips use it; the
+// int16 strip stores every step, which measured faster there (the held
+// values must be moved into consecutive registers).
 template <int U>
 struct RingStore {
   static constexpr int W = U % 4 == 0 ? 4 : 2;
@@ -239,7 +241,6 @@ struct StripI16 {
                                         uint32_t nr, bool tracked, int, int) {
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
-    RingStore<U> out;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int p = (S - (u % S)) % S;
@@ -268,7 +269,7 @@ struct StripI16 {
         G[b][k] = v;
       }
       gprev = gup;
-      out.put(ring, e0, u, tracked, G[b][S - 1]);
+      if (tracked) ring[e0 + u] = G[b][S - 1];
     }
   }
 };
@@ -792,11 +793,13 @@ __device__ __forceinline__ void sweep_any(const SdtwArgs &A, TileStream &ts, con
     sweep_unit<kFormF32Span, S>(A, ts, g, item, ring, lane);
   } else if constexpr (PREC == kPrecWideSpan) {
     sweep_unit<kFormWideSpan, S>(A, ts, g, item, ring, lane);
-  } else {
+  } else if constexpr (PREC == kPrecI16Mixed) {
     if (A.items[item].kind == kItemExact)
       sweep_unit<kFormExact, S>(A, ts, g, item, ring, lane);
     else
       sweep_unit<kFormI16, S>(A, ts, g, item, ring, lane);
+  } else {
+    sweep_unit<kFormI16, S>(A, ts, g, item, ring, lane);
   }
 }
 
@@ -984,11 +987,13 @@ __device__ __forceinline__ void fixup_any(const SdtwArgs &A, int item, uint32_t 
     fixup_item<kFormF32Span, S>(A, item, ring, lane);
   } else if constexpr (PREC == kPrecWideSpan) {
     fixup_item<kFormWideSpan, S>(A, item, ring, lane);
-  } else {
+  } else if constexpr (PREC == kPrecI16Mixed) {
     if (A.items[item].kind == kItemExact)
       fixup_item<kFormExact, S>(A, item, ring, lane);
     else
       fixup_item<kFormI16, S>(A, item, ring, lane);
+  } else {
+    fixup_item<kFormI16, S>(A, item, ring, lane);
   }
 }
 
