@@ -500,7 +500,7 @@ int Server::turn_upload() {
     // the staging buffers are reused next turn: wait for this transfer
     if (e == cudaSuccess) e = cudaEventRecord(up_done_, up_stream_);
     // Poll for the transfer (a few tens of microseconds) rather than block
-    // in the driver; bounded by the context's wait limit.
+    // in the CUDA driver; bounded by the context's wait limit.
     const uint64_t ts = now_ns();
     if (e == cudaSuccess) {
       while ((e = cudaEventQuery(up_done_)) == cudaErrorNotReady) {
