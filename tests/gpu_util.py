@@ -10,7 +10,7 @@ def compare_int16(cost, col, ref_levels, events, offsets, scale_log2=6, normaliz
     prec=oracle.PREC_I32 for wide accumulation) against the oracle on queries idx."""
     prec = oracle.PREC_I16 if prec is None else prec
     q = idx if idx is not None else np.arange(offsets.shape[0] - 1)
-    sub_ev, sub_off = _subset(events, offsets, q)
+    sub_ev, sub_off = subset(events, offsets, q)
     o = oracle.batch(prec, ref_levels, sub_ev, sub_off, scale_log2=scale_log2,
                      normalize_ref=normalize_ref, normalize_q=normalize_q)
     np.testing.assert_array_equal(col[q], o.col, err_msg="integer form end column")
@@ -24,7 +24,7 @@ def compare_fp32(cost, col, ref_levels, events, offsets, normalize_ref=True, idx
     of FP64 with the FP64 end column unless the FP64 runner-up is within
     that tolerance of the best."""
     q = idx if idx is not None else np.arange(offsets.shape[0] - 1)
-    sub_ev, sub_off = _subset(events, offsets, q)
+    sub_ev, sub_off = subset(events, offsets, q)
     o32 = oracle.batch(oracle.PREC_F32, ref_levels, sub_ev, sub_off, normalize_ref=normalize_ref,
                        normalize_q=normalize_q)
     o64 = oracle.batch(oracle.PREC_F64, ref_levels, sub_ev, sub_off, normalize_ref=normalize_ref,
@@ -40,7 +40,8 @@ def compare_fp32(cost, col, ref_levels, events, offsets, normalize_ref=True, idx
     return o32, o64
 
 
-def _subset(events, offsets, q):
+def subset(events, offsets, q):
+    """Events and offsets of queries q of a CSR batch."""
     parts = [events[offsets[i]:offsets[i + 1]] for i in q]
     off = np.zeros(len(parts) + 1, dtype=np.uint32)
     off[1:] = np.cumsum([p.shape[0] for p in parts])

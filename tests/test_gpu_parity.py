@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import compare_fp32, compare_int16
+from tests.gpu_util import compare_fp32, compare_int16, subset
 
 pytestmark = pytest.mark.gpu
 
@@ -181,26 +181,45 @@ def test_device_pointers_match_host_path(haru, sars):
 
 
 def test_uneven_8192_full_size_sampled(haru, sars):
-    """The full 8,192-query uneven batch in one launch; 40 queries re-checked
-    one by one against the oracle (both forms), covering every strip height."""
+    """The full 8,192-query uneven batch in one launch, in the default launch
+    shape and in the shape the autotuner picks for it (the one the benchmark
+    times): each form gives identical results in both, and three queries of
+    every 32-event length band are re-checked one by one against the oracle
+    (int16, FP32, int16 with 32-bit accumulation, FP32 start columns)."""
     _, ref = sars
-    w = synth.workload("sars_uneven_8192")
-    qs = w.queries
-    with haru.Context() as ctx:
-        ctx.ref_load(ref)
-        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
-        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, qs.events, qs.offsets)
+    qs = synth.workload("sars_uneven_8192").queries
     lens = qs.lengths
     rng = np.random.default_rng(0)
     idx = []
-    for S in range(4, 17):
-        cand = np.nonzero((lens + 31) // 32 == S)[0]
+    for band in range(3, 16):  # every strip height, stacked (<= 256 events) and not
+        cand = np.nonzero(lens // 32 == band)[0]
         idx += list(rng.choice(cand, size=min(3, cand.shape[0]), replace=False))
-    idx = np.array(sorted(set(idx)))[:40]
+    idx = np.array(sorted(set(idx)))
+    forms = (haru.HARU_INT16, haru.HARU_FP32, haru.HARU_INT16_ACC32)
+    with haru.Context() as ctx:
+        ctx.ref_load(ref)
+        out = {p: ctx.sdtw_batch(p, qs.events, qs.offsets) for p in forms}
+        cs, js, ss = ctx.sdtw_batch_span(haru.HARU_FP32, qs.events, qs.offsets)
+        for p in forms:
+            ctx.autotune(p, qs.events, qs.offsets)
+            c, j = ctx.sdtw_batch(p, qs.events, qs.offsets)
+            np.testing.assert_array_equal(c, out[p][0], err_msg=f"precision {p}, tuned shape")
+            np.testing.assert_array_equal(j, out[p][1], err_msg=f"precision {p}, tuned shape")
+    c16, j16 = out[haru.HARU_INT16]
+    c32, j32 = out[haru.HARU_FP32]
+    cw, jw = out[haru.HARU_INT16_ACC32]
     compare_int16(c16, j16, ref, qs.events, qs.offsets, idx=idx)
     compare_fp32(c32, j32, ref, qs.events, qs.offsets, idx=idx)
+    compare_int16(cw, jw, ref, qs.events, qs.offsets, idx=idx, prec=oracle.PREC_I32)
+    # start columns: costs and end columns of the FP32 form, starts of the oracle
+    np.testing.assert_array_equal(cs, c32)
+    np.testing.assert_array_equal(js, j32)
+    sub_ev, sub_off = subset(qs.events, qs.offsets, idx)
+    o = oracle.batch(oracle.PREC_F32, ref, sub_ev, sub_off, start=True)
+    np.testing.assert_array_equal(ss[idx], o.start)
     # every query got a result
-    assert (j16 >= 0).all() and (j32 >= 0).all()
+    assert (j16 >= 0).all() and (j32 >= 0).all() and (jw >= 0).all()
+    assert ((ss >= 0) & (ss <= js)).all()
     assert np.isfinite(c32).all()
 
 
