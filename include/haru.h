@@ -304,7 +304,7 @@ int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, c
 /* Autotuner: run the batch path on this batch (layout and flags as in
  * haru_sdtw_batch; HARU_ON_DEVICE and HARU_RAW are honoured) under every
  * combination of warps per CTA {4, 8}, tile width {2048, 4096, 8192, 16384},
- * work-unit target {1 (no reference segments), auto, 2 x auto} and one or
+ * work-unit target {1 (no reference segments), auto / 2, auto, 2 x auto} and one or
  * four sweep kernels, keep the
  * fastest (minimum of two timed runs each) in the context's configuration
  * for later batches, and copy the resulting configuration to *chosen (may be

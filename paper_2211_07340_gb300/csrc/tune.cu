@@ -67,7 +67,7 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
   const int auto_units = 4 * ctx->sms * 8;
   const int warps_c[] = {4, 8};
   const int tiles_c[] = {2048, 4096, 8192, 16384};
-  const int units_c[] = {1, auto_units, 2 * auto_units};
+  const int units_c[] = {1, auto_units / 2, auto_units, 2 * auto_units};
   const int single_c[] = {0, 1};
   float best_ms = -1.0f;
   LaunchCfg best = base;
