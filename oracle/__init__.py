@@ -6,8 +6,9 @@ library never imports, links or calls it, and it shares no code with it.
 
 The arithmetic lives in sdtw_oracle.cpp (plain C++17, compiled with
 -ffp-contract=off): Eq. 1 and Algorithm 1 (full matrix), Algorithm 2 (one
-rolling cost array), the Section 4.1 reference synthesis, z-score and
-fixed-point quantiser. This module only builds that file and marshals numpy
+rolling cost array), the Section 4.3 processing-element chain (oblique
+order), the Section 4.1 reference synthesis, z-score and fixed-point
+quantiser. This module only builds that file and marshals numpy
 arrays through ctypes.
 """
 from __future__ import annotations
@@ -71,6 +72,8 @@ def _load():
         lib.oracle_sdtw_span_f32.restype = None
         lib.oracle_sdtw_span_i32.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P, P]
         lib.oracle_sdtw_span_i32.restype = None
+        lib.oracle_sdtw_wavefront_f64.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P, P]
+        lib.oracle_sdtw_wavefront_f64.restype = None
         lib.oracle_batch.restype = ctypes.c_int
         lib.oracle_cap.restype = ctypes.c_int
         lib.oracle_qmax.restype = ctypes.c_int
@@ -147,6 +150,17 @@ def sdtw_roll_f64(x, y):
     _load().oracle_sdtw_roll_f64(_p(x), x.shape[0], _p(y), y.shape[0], ctypes.byref(c), ctypes.byref(j),
                                  ctypes.byref(r))
     return c.value, j.value, r.value
+
+
+def sdtw_wavefront_f64(x, y):
+    """Eq. 1 in the processing-element chain's oblique order (Section 4.3,
+    Fig. 5): (cost, end column, steps the chain ran)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    c, j, t = ctypes.c_double(), ctypes.c_long(), ctypes.c_long()
+    _load().oracle_sdtw_wavefront_f64(_p(x), x.shape[0], _p(y), y.shape[0], ctypes.byref(c), ctypes.byref(j),
+                                      ctypes.byref(t))
+    return c.value, j.value, t.value
 
 
 def sdtw_roll_f32(x, y):

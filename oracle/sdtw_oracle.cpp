@@ -231,6 +231,51 @@ void oracle_sdtw_roll_f64(const double *x, int M, const double *y, long N, doubl
   if (runner_up) *runner_up = second;
 }
 
+// ------------------------------------- Section 4.3: the pipelined PE chain --
+// The same recurrence evaluated in the oblique order of the processing-element
+// chain (Section 4.3, Fig. 5): PE i holds query sample x_i and at step t
+// computes gamma(i, t - i), while the reference streams past one PE per step.
+// Within a step every PE updates at once from values of the two previous
+// steps: up = gamma(i-1, j) is PE i-1's value of step t-1, diagonal =
+// gamma(i-1, j-1) is PE i-1's value of step t-2, left = gamma(i, j-1) is PE
+// i's own value of step t-1. Row 0 (above PE 1) is the free-start 0 and
+// column 0 is +inf. The chain needs N + M - 1 steps for all cells; *steps
+// reports how many it ran. The last PE's values, in column order, give the
+// cost and the first column reaching it (strict <).
+void oracle_sdtw_wavefront_f64(const double *x, int M, const double *y, long N, double *cost, long *col,
+                               long *steps) {
+  const double inf = std::numeric_limits<double>::infinity();
+  // val1[i]: PE i's value after the previous step; val2[i]: the step before.
+  // Index 0 is the free-start row, always 0.
+  std::vector<double> val1((size_t)M + 1, inf), val2((size_t)M + 1, inf), next((size_t)M + 1, inf);
+  val1[0] = val2[0] = next[0] = 0.0;
+  double score = inf;
+  long pos = -1, t = 0;
+  for (; t < N + M - 1; ++t) {
+    for (int i = 1; i <= M; ++i) {
+      const long j = t - (i - 1);  // 0-based column of PE i at step t
+      if (j < 0 || j >= N) {
+        next[(size_t)i] = (j < 0) ? inf : val1[(size_t)i];  // not started: column 0's +inf; done: hold
+        continue;
+      }
+      const double up = val1[(size_t)i - 1];
+      const double diag = (j == 0) ? (i == 1 ? 0.0 : inf) : val2[(size_t)i - 1];
+      const double left = (j == 0) ? inf : val1[(size_t)i];
+      next[(size_t)i] = std::fabs(x[i - 1] - y[j]) + dmin3(up, diag, left);
+    }
+    val2.swap(val1);
+    val1.swap(next);
+    const long jl = t - (M - 1);  // the last PE's column at this step
+    if (jl >= 0 && jl < N && val1[(size_t)M] < score) {
+      score = val1[(size_t)M];
+      pos = jl;
+    }
+  }
+  *cost = score;
+  *col = pos;
+  *steps = t;
+}
+
 void oracle_sdtw_roll_f32(const float *x, int M, const float *y, long N, float *cost, long *col) {
   const float inf = std::numeric_limits<float>::infinity();
   std::vector<float> C((size_t)M + 1, inf);

@@ -187,6 +187,35 @@ def test_full_matrix_equals_rolling_array():
         assert oracle.sdtw_full_i16(xi, yi) == oracle.sdtw_roll_i16(xi, yi)
 
 
+# ------------------------------------------- the PE chain's oblique order --
+@pytest.mark.parametrize("case", list(range(60)))
+def test_wavefront_order_matches_brute_force(case):
+    """Section 4.3's processing-element chain evaluates Eq. 1 along oblique
+    columns (PE i computes column t - i at step t, all PEs at once): the same
+    cost and first end column as the enumeration of every warping path, in
+    N + M - 1 steps."""
+    x, y = list(small_cases())[case]
+    c, j = brute_force(list(x), list(y))
+    wc, wj, steps = oracle.sdtw_wavefront_f64(x, y)
+    assert (wc, wj) == (c, j)
+    assert steps == len(x) + len(y) - 1
+
+
+def test_wavefront_order_equals_rolling_array():
+    """The oblique order and Algorithm 2's column-by-column rolling array give
+    the same bits (every cell is the same |x - y| + min of the same three
+    values), on continuous values and on small integers full of ties."""
+    rng = np.random.default_rng(13)
+    for _ in range(20):
+        M, N = int(rng.integers(1, 60)), int(rng.integers(60, 300))
+        x, y = rng.normal(size=M), rng.normal(size=N)
+        wc, wj, steps = oracle.sdtw_wavefront_f64(x, y)
+        assert (wc, wj) == oracle.sdtw_roll_f64(x, y)[:2]
+        assert steps == M + N - 1
+        xi, yi = rng.integers(0, 3, M).astype(np.float64), rng.integers(0, 3, N).astype(np.float64)
+        assert oracle.sdtw_wavefront_f64(xi, yi)[:2] == oracle.sdtw_roll_f64(xi, yi)[:2]
+
+
 # ------------------------------------------------ int16 saturation identity --
 def test_int16_is_capped_exact_integer_dp():
     """Saturating at CAP in every cell equals saturating the exact integer
