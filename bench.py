@@ -503,8 +503,11 @@ def main():
     graphed = False
     msdpx = sweepdpx = nan
     msw = sweepw = nan
+    capped16 = None
     if "int16" in forms:
         ms16, sweep16, clocks, graphed = run_form(haru.HARU_INT16)
+        # queries whose int16 cost saturated at CAP (cost = integer cost / 2^6, exact)
+        capped16 = int((np.rint(cost_d.cpu().numpy().astype(np.float64) * 64) >= haru.HARU_INT16_CAP).sum())
     if "int16exact" in forms:
         msdpx, sweepdpx, _, _ = run_form(haru.HARU_INT16, exact_share=1)
     if "fp32" in forms:
@@ -627,6 +630,7 @@ def main():
                                         "direct launches, default launch shape"}
                                if span_ms == span_ms else None),
         "int16_over_fp32": value / value32 if value32 == value32 else None,
+        "int16_capped_queries": capped16,
         "prep_ms_per_step": ms16 - sweep16,
         "e2e": {"value": e2e_value, "unit": "GCUPS", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(q.events.nbytes + q.offsets.nbytes),
