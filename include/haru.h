@@ -172,8 +172,9 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
  * precision: HARU_FP32 or HARU_INT16_ACC32 (the packed int16 form has no room
  * for a start column per cell). Layout, flags, ownership and errors as in
  * haru_sdtw_batch; out_start is a host pointer, or a device pointer with
- * HARU_ON_DEVICE. About 2-3x the time of haru_sdtw_batch (more work per
- * cell), and each query sweeps the reference in one piece. */
+ * HARU_ON_DEVICE. About 2-2.5x the time of haru_sdtw_batch (more work per
+ * cell); sweeps are cut into verified reference segments as there, a segment
+ * being kept only if both its costs and its start columns match. */
 int haru_sdtw_batch_span(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
                          float *out_cost, int64_t *out_col, int64_t *out_start, uintptr_t stream, uint32_t flags);
 
