@@ -424,13 +424,15 @@ def test_start_columns(haru, sars, stack):
             ctx.sdtw_batch_span(haru.HARU_INT16, qs.events, qs.offsets)
 
 
-def test_start_columns_across_segments(haru):
+@pytest.mark.parametrize("stack", [-1, 1])
+def test_start_columns_across_segments(haru, stack):
     """Start columns stay exact when a sweep is cut into speculative reference
     segments: the only zero-cost path of the first query enters a 10,000-column
     plateau two columns before it and crosses it on one row, so every segment
     boundary inside the plateau fails verification and is recomputed. The same
-    batch cut into many segments and not cut at all gives the oracle's costs,
-    end columns and start columns."""
+    batch cut into many segments and not cut at all, with short queries stacked
+    two to a warp and not, gives the oracle's costs, end columns and start
+    columns."""
     N = 60000
     ref = synth.random_signal(N, seed=44, scale=1.0, loc=0.0)
     c, e = np.float32(0.25), np.float32(-1.5)
@@ -447,7 +449,7 @@ def test_start_columns_across_segments(haru):
         if prec == haru.HARU_FP32:
             assert (o.cost[0], o.col[0], o.start[0]) == (0.0, 30000, 19998)
         for units, segmented in ((1, False), (20000, True)):
-            with haru.Context(units_target=units) as ctx:
+            with haru.Context(units_target=units, stack_short=stack) as ctx:
                 ctx.ref_load(ref, normalize=False)
                 cs, js, ss = ctx.sdtw_batch_span(prec, ev, off, raw=False)
                 st = ctx.last_stats()
