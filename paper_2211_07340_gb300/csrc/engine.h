@@ -37,7 +37,8 @@ struct LaunchCfg {
   int ctas_per_sm = 0;
   int sms = 1;
   int units_target = 0;  // 0: 4 x sms x warps
-  int int16_mode = 1;    // int16 batches: 1 = DPX pairs only, 2 = pairs and exact-FP32 strips (1:2 warps)
+  int int16_mode = 1;    // int16 batches: 1 = DPX pairs only, 2 = pairs and exact-FP32 strips (1:2 warps,
+                         // in a sweep kernel of its own, internal precision kPrecI16Mixed)
   int single_kernel = 0; // 1: one sweep kernel for every strip height instead of four class kernels
   int stack_short = 0;   // stack short queries: 0 auto (batch >= units target), 1 always, -1 never
   unsigned long long wait_ns = 2000000000ull;
