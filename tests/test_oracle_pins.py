@@ -396,3 +396,74 @@ def test_batch_composes_the_steps():
         assert (b64.cost[q], b64.col[q]) == oracle.sdtw_roll_f64(qz.astype(np.float64), rz.astype(np.float64))[:2]
     with pytest.raises(ValueError):
         oracle.batch(oracle.PREC_F32, ref[:10], ev, off)  # M > N
+
+
+# ------------------------------------------------- FP32 rounding of Eq. 1 --
+def full_matrix_float32(x, y, acc=np.float32, cell=None):
+    """Eq. 1 as a full (M + 1) x (N + 1) matrix with every operation rounded
+    in `acc` (numpy scalar arithmetic): delta = |x_i - y_j|, then
+    delta + min(up, diagonal, left). With acc = float32 this is the FP32 form
+    written out independently of the oracle. Two plausible slips for the
+    sensitivity check: acc = float64 accumulates in double and rounds once at
+    the end; cell = float32 with acc = float64 rounds each cell once to float32
+    after forming |x - y| + min in double (no float32 rounding of delta)."""
+    M, N = len(x), len(y)
+    inf = acc(np.inf)
+    g = [[acc(0.0)] * (N + 1)] + [[inf] + [acc(0.0)] * N for _ in range(M)]
+    for i in range(1, M + 1):
+        xi = acc(x[i - 1])
+        up_row, row = g[i - 1], g[i]
+        for j in range(1, N + 1):
+            d = abs(xi - acc(y[j - 1]))
+            m = min(up_row[j], up_row[j - 1], row[j - 1])
+            row[j] = acc(d + m) if cell is None else acc(cell(d + acc(m)))
+    last = g[M][1:]
+    j = min(range(N), key=lambda k: (last[k], k))  # first column of the minimum
+    return g, np.float32(last[j]), j
+
+
+def float32_traceback_start(g, x, y, end):
+    """Start column by a traceback through the FP32 matrix from `end`: step to
+    the up neighbour if it is a minimum predecessor, else the diagonal one,
+    else the left one; the path starts where it enters row 1."""
+    i, j = len(x), end + 1
+    while i > 1:
+        up, dg, lf = g[i - 1][j], g[i - 1][j - 1], g[i][j - 1]
+        m = min(up, dg, lf)
+        if up == m:
+            i -= 1
+        elif dg == m:
+            i, j = i - 1, j - 1
+        else:
+            j -= 1
+    return j - 1
+
+
+def fp32_cases():
+    rng = np.random.default_rng(19)
+    for _ in range(40):
+        M, N = int(rng.integers(1, 41)), int(rng.integers(41, 301))
+        yield rng.normal(size=M).astype(np.float32), rng.normal(size=N).astype(np.float32)
+    # a planted copy with noise: costs small against their summands
+    y = rng.normal(size=300).astype(np.float32)
+    yield (y[100:140] + rng.normal(0.0, 0.05, 40)).astype(np.float32), y
+
+
+def test_fp32_rounding_matches_float32_restatement():
+    """The FP32 oracle (Algorithm 2 and the start-column carry) rounds every
+    cell exactly as an independent float32 full-matrix Eq. 1 does, on
+    continuous inputs where float32 and double sums differ. The same
+    restatement accumulated in double disagrees with it on these inputs, so a
+    double-accumulating oracle, or one that rounds each cell once from a
+    double |x - y| + min, would fail this pin."""
+    slips = [0, 0]
+    for x, y in fp32_cases():
+        g, c, j = full_matrix_float32(x, y)
+        oc, oj = oracle.sdtw_roll_f32(x, y)
+        assert np.float32(oc) == c and oj == j
+        st = float32_traceback_start(g, x, y, j)
+        assert oracle.sdtw_span_f32(x, y) == (float(c), j, st)
+        for k, (acc, cell) in enumerate(((np.float64, None), (np.float64, np.float32))):
+            _, cs, js = full_matrix_float32(x, y, acc=acc, cell=cell)
+            slips[k] += int(np.float32(cs) != c or js != j)
+    assert min(slips) >= 3, slips
