@@ -84,20 +84,12 @@ typedef struct {
   uint32_t serve_prefix;    /* events per decision prefix; 0 = 250 (Section 4.1) */
   int units_target;         /* work units (query x reference segment) a batch is cut into, at least;
                                0 = 4 x SMs x warps_per_cta; 1 = never split the reference */
-  int single_kernel;        /* 1 (default): one sweep kernel covers every strip height with one
-                               longest-first queue; 0: four kernels by strip height run side by side,
-                               each with registers sized for its tallest strip */
   int stack_short;          /* queries of at most 256 events stacked two to a warp strip (lanes 0-15
                                and 16-31), doubling the rows each lane sweeps: more throughput, but
                                each strip takes longer. 0 (default) = in batches of at least
                                units_target queries (or 4 x SMs x warps_per_cta when that is 0),
                                or whose stacked items cut into reference segments still make that
                                many work units (long references); 1 = always; -1 = never */
-  int int16_exact_share;    /* int16 batches: 0 (default) = every warp runs packed DPX query pairs;
-                               1 = two of every three warps compute their query exactly on the int16
-                               codes in FP32 instead (identical results: saturating every cell equals
-                               saturating the exact cost once), to load the FMA pipe as well as the
-                               half-rate min/DPX pipe. Measured slower on GB300; kept as an option. */
   int serve_spin_us;        /* serving: microseconds the worker keeps polling after its last piece of
                                work before it sleeps (a sleeping thread can be woken late on a busy
                                host); 0 = 2000, negative = never poll idle */
@@ -245,6 +237,11 @@ typedef struct {
    * switches during it (Linux; 0 elsewhere) */
   uint64_t worst_turn_complete_ns, worst_turn_upload_ns, worst_turn_launch_ns, worst_turn_wait_ns;
   uint64_t worst_turn_voluntary_switches, worst_turn_involuntary_switches;
+  /* the GPU stage split: the longest device execution of a batch (CUDA
+   * events from its first operation to its last), and the longest remainder
+   * of a read's GPU stage (queueing on the device and the worker noticing
+   * completion) */
+  uint64_t max_gpu_exec_ns, max_notice_ns;
 } haru_stream_stats;
 int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
 
@@ -281,17 +278,20 @@ int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep);
  * accept cudaMalloc's implicit synchronisation stalling its other streams.
  * It calls no cudaMalloc, cudaFree or allocating library routine. Its
  * scratch memory (planner items and groups, packed query images, status and
- * work-queue counters) is one fixed array of about 4.1 MiB compiled into
- * the library, which every GPU that loads the library holds until the
- * process exits.
+ * work-queue counters) is one fixed array of 4,409,600 bytes (4.2 MiB)
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.
  *
  * events, offsets, out_cost and out_col are DEVICE pointers owned by the
  * caller, laid out as in haru_sdtw_batch; the reference is the context's.
+ * precision: HARU_FP32 or HARU_INT16 (HARU_INT16_ACC32 returns HARU_EINVAL).
  * flags: 0 or HARU_RAW. The call is ordered on `stream` (0 = the context's)
- * and returns after the results are written.
+ * and returns after the results are written. Sweeps are never cut into
+ * reference segments and short queries are never stacked (both need more
+ * scratch); results equal haru_sdtw_batch's.
  * Limits and errors: nq <= HARU_NOALLOC_MAX_QUERIES, else HARU_EINVAL (as for
  * any other flag or bad argument); per-query rules and the other codes as
- * for haru_sdtw_batch.
+ * for haru_sdtw_batch (a CUDA error is sticky on the context).
  * The first call on a device looks up the array's device address (which may
  * load the library's GPU code); make that first call before any stream
  * capture. Every call on every context of the process shares the one array
@@ -304,10 +304,9 @@ int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, c
 
 /* Autotuner: run the batch path on this batch (layout and flags as in
  * haru_sdtw_batch; HARU_ON_DEVICE and HARU_RAW are honoured) under every
- * combination of warps per CTA {4, 8}, tile width {2048, 4096, 8192, 16384},
- * work-unit target {1 (no reference segments), auto / 2, auto, 2 x auto} and one or
- * four sweep kernels, keep the
- * fastest (minimum of two timed runs each) in the context's configuration
+ * combination of warps per CTA {4, 8}, tile width {2048, 4096, 8192, 16384}
+ * and work-unit target {1 (no reference segments), auto / 2, auto,
+ * 2 x auto}, keep the fastest (minimum of two timed runs each) in the context's configuration
  * for later batches, and copy the resulting configuration to *chosen (may be
  * NULL). The strip height is fixed by each query's length. Results of the
  * trial runs are discarded. Errors: as haru_sdtw_batch. */

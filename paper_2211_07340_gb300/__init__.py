@@ -59,9 +59,7 @@ class haru_config(ctypes.Structure):
         ("serve_max_batch", ctypes.c_uint32),
         ("serve_prefix", ctypes.c_uint32),
         ("units_target", ctypes.c_int),
-        ("single_kernel", ctypes.c_int),
         ("stack_short", ctypes.c_int),
-        ("int16_exact_share", ctypes.c_int),
         ("serve_spin_us", ctypes.c_int),
     ]
 
@@ -86,7 +84,8 @@ class haru_stream_stats(ctypes.Structure):
                                                "max_turn_gap_ns", "worst_turn_complete_ns", "worst_turn_upload_ns",
                                                "worst_turn_launch_ns", "worst_turn_wait_ns",
                                                "worst_turn_voluntary_switches",
-                                               "worst_turn_involuntary_switches")]
+                                               "worst_turn_involuntary_switches", "max_gpu_exec_ns",
+                                               "max_notice_ns")]
 
 
 _lib = None
@@ -332,8 +331,7 @@ class Context:
         check(lib().haru_autotune(self._h, int(precision), _ptr(events), _ptr(offsets), nq, flags,
                                   ctypes.byref(cfg)), "haru_autotune")
         self.config = cfg
-        return {"warps_per_cta": cfg.warps_per_cta, "tile_cols": cfg.tile_cols, "units_target": cfg.units_target,
-                "single_kernel": cfg.single_kernel}
+        return {"warps_per_cta": cfg.warps_per_cta, "tile_cols": cfg.tile_cols, "units_target": cfg.units_target}
 
     def probe_peak(self, precision: int) -> float:
         """Measured cells/s ceiling of the form's cell update (no data movement)."""

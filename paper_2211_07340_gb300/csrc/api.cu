@@ -56,8 +56,6 @@ haru::LaunchCfg haru_ctx::launch_cfg() const {
   lc.ctas_per_sm = cfg.ctas_per_sm;
   lc.sms = sms;
   lc.units_target = cfg.units_target;
-  lc.int16_mode = cfg.int16_exact_share ? 2 : 1;
-  lc.single_kernel = cfg.single_kernel ? 1 : 0;
   lc.stack_short = cfg.stack_short > 0 ? 1 : (cfg.stack_short < 0 ? -1 : 0);
   lc.wait_ns = wait_ns(cfg);
   return lc;
@@ -95,6 +93,13 @@ int ctx_reference(haru_ctx *ctx, int precision, const void **img, long *N, int *
   return HARU_OK;
 }
 
+// Record a CUDA failure of a call that does not hold the context lock (the
+// no-allocation path): the first CUDA error of a context is sticky.
+int ctx_cuda_fail(haru_ctx *ctx, cudaError_t e) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return cuda_fail(ctx, e);
+}
+
 }  // namespace haru
 
 extern "C" {
@@ -111,7 +116,6 @@ int haru_config_default(haru_config *cfg) {
   cfg->serve_budget_bytes = 64u << 20;
   cfg->serve_max_batch = 1024;
   cfg->serve_prefix = 250;
-  cfg->single_kernel = 1;
   return HARU_OK;
 }
 
@@ -153,11 +157,6 @@ int haru_create(haru_ctx **out, int device, const haru_config *cfg) {
     if (cudaMalloc(&ctx->stats, 2 * sizeof(double)) != cudaSuccess) { rc = HARU_ENOMEM; break; }
     bool ev_ok = true;
     for (auto &e : ctx->ev) ev_ok = ev_ok && cudaEventCreate(&e) == cudaSuccess;
-    ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->fj.fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int c = 0; c < haru::kClasses; ++c) {
-      ev_ok = ev_ok && cudaEventCreateWithFlags(&ctx->fj.join[c], cudaEventDisableTiming) == cudaSuccess;
-      ev_ok = ev_ok && cudaStreamCreateWithFlags(&ctx->fj.aux[c], cudaStreamNonBlocking) == cudaSuccess;
-    }
     if (!ev_ok) { rc = HARU_ECUDA; break; }
   } while (0);
   if (rc != HARU_OK) {
@@ -197,11 +196,6 @@ void haru_destroy(haru_ctx *ctx) {
   haru::ws_free(ctx->ws);
   for (auto e : ctx->ev)
     if (e) cudaEventDestroy(e);
-  if (ctx->fj.fork) cudaEventDestroy(ctx->fj.fork);
-  for (int c = 0; c < haru::kClasses; ++c) {
-    if (ctx->fj.join[c]) cudaEventDestroy(ctx->fj.join[c]);
-    if (ctx->fj.aux[c]) cudaStreamDestroy(ctx->fj.aux[c]);
-  }
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -384,7 +378,7 @@ int batch_call(haru_ctx *ctx, int precision, const float *events, const uint32_t
   HARU_CUDA(haru::ws_reserve(ctx->ws, precision, nq, lc));
   const bool prof = flags & HARU_PROFILE;
   HARU_CUDA(haru::ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, d_cost, d_col, lc, s,
-                             &ctx->fj, prof ? ctx->ev[0] : nullptr, prof ? ctx->ev[1] : nullptr, d_start));
+                             prof ? ctx->ev[0] : nullptr, prof ? ctx->ev[1] : nullptr, d_start));
   if (prof) {
     HARU_CUDA(haru::record_event(ctx->ev[2], s));
     ctx->profiled = true;

@@ -1,5 +1,5 @@
 // The batch engine: workspace sizing and the stream-ordered sequence of
-// kernels of one batch (planner, pack, class sweeps, segment fix-up).
+// kernels of one batch (planner, pack, sweep, segment fix-up).
 
 #include <cuda_runtime.h>
 
@@ -34,7 +34,7 @@ struct WsNeeds {
 
 WsNeeds ws_needs(int precision, uint32_t nq, const LaunchCfg &lc) {
   WsNeeds w;
-  const int mode = plan_mode(precision, lc);
+  const int mode = plan_mode(precision);
   w.max_items = items_bound(mode, nq);
   // Work units: enough (query x reference segment) units to keep every SM
   // busy to the end; nseg_cap bounds the segments per item for storage.
@@ -42,7 +42,7 @@ WsNeeds ws_needs(int precision, uint32_t nq, const LaunchCfg &lc) {
   // Fewest items the batch can make (stacked: four int16 or two other
   // queries per item); the segment cap is sized for that case.
   const size_t items_min = (mode == 0 || mode == 3) ? (static_cast<size_t>(nq) + 1) / 2
-                           : (mode == 1 ? (static_cast<size_t>(nq) + 3) / 4 : (3 * static_cast<size_t>(nq)) / 4);
+                                                   : (static_cast<size_t>(nq) + 3) / 4;
   // (twice that: the planner doubles the segments of the queue's tail)
   w.nseg_cap = static_cast<int>(std::min<size_t>(
       kMaxSeg, 2 * ((static_cast<size_t>(w.units_target) + items_min - 1) / std::max<size_t>(items_min, 1))));
@@ -103,8 +103,8 @@ cudaError_t ws_reserve_upto(Workspace &ws, int precision, uint32_t max_nq, const
 
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
-                       const LaunchCfg &lc, cudaStream_t s, const ForkJoin *fj, cudaEvent_t ev_prep,
-                       cudaEvent_t ev_sweep, int64_t *d_start) {
+                       const LaunchCfg &lc, cudaStream_t s, cudaEvent_t ev_prep, cudaEvent_t ev_sweep,
+                       int64_t *d_start) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(ws.ints, 0, kIntWords * sizeof(int), s)) != cudaSuccess) return e;
   if (ev_prep && (e = record_event(ev_prep, s)) != cudaSuccess) return e;
@@ -112,10 +112,9 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   pa.offsets = d_offsets;
   pa.nq = nq;
   pa.N = ref.N;
-  pa.pair = plan_mode(precision, lc);
+  pa.pair = plan_mode(precision);
   pa.warps = lc.warps;
   pa.units_target = ws.units_target;
-  pa.single = lc.single_kernel ? 1 : 0;
   // Auto stacking: when the batch alone fills the unit target, or when its
   // stacked items (up to four queries each) cut into reference segments
   // (at most 64, each counted as 8,192 steps: about four warm-ups of a 16-row strip)
@@ -166,36 +165,13 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   sa.wait_ns = lc.wait_ns;
   const size_t groups_max = ((ws.max_items + lc.warps - 1) / lc.warps + kMaxS) * static_cast<size_t>(ws.nseg_cap);
   if (ev_sweep && (e = record_event(ev_sweep, s)) != cudaSuccess) return e;
-  // The class kernels (tallest strips first) run side by side when fork/join
-  // streams are given, else one after the other on s; each is persistent
-  // over its own part of the group list, then verifies its segments and
-  // writes its queries' results.
-  // The int16 form with an exact share (planner mode 2) runs its own kernel.
-  const int kprec = precision == HARU_INT16 && plan_mode(precision, lc) == 2 ? kPrecI16Mixed : precision;
-  if (lc.single_kernel || kprec == HARU_INT16_ACC32 || kprec == kPrecI16Mixed || prec_span(kprec)) {
-    // (these have the single kernel only)
-    int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(kprec, kClassAll, lc.tile, lc.warps);
-    if (per_sm < 1) per_sm = 1;
-    const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
-    return launch_sdtw(kprec, kClassAll, sa, grid, static_cast<int>(ws.max_items), s);
-  }
-  if (fj && fj->ok() && (e = cudaEventRecord(fj->fork, s)) != cudaSuccess) return e;
-  for (int c = 0; c < kClasses; ++c) {
-    int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, c, lc.tile, lc.warps);
-    if (per_sm < 1) per_sm = 1;
-    const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
-    cudaStream_t cs = s;
-    if (fj && fj->ok()) {
-      cs = fj->aux[c];
-      if ((e = cudaStreamWaitEvent(cs, fj->fork, 0)) != cudaSuccess) return e;
-    }
-    if ((e = launch_sdtw(precision, c, sa, grid, static_cast<int>(ws.max_items), cs)) != cudaSuccess) return e;
-    if (fj && fj->ok()) {
-      if ((e = cudaEventRecord(fj->join[c], cs)) != cudaSuccess) return e;
-      if ((e = cudaStreamWaitEvent(s, fj->join[c], 0)) != cudaSuccess) return e;
-    }
-  }
-  return cudaSuccess;
+  // One persistent sweep kernel over the whole group list (tallest strips
+  // first), then the fix-up kernel, which verifies segments and writes every
+  // query's result.
+  int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, lc.tile, lc.warps);
+  if (per_sm < 1) per_sm = 1;
+  const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
+  return launch_sdtw(precision, sa, grid, static_cast<int>(ws.max_items), s);
 }
 
 }  // namespace haru

@@ -37,27 +37,22 @@ struct LaunchCfg {
   int ctas_per_sm = 0;
   int sms = 1;
   int units_target = 0;  // 0: 4 x sms x warps
-  int int16_mode = 1;    // int16 batches: 1 = DPX pairs only, 2 = pairs and exact-FP32 strips (1:2 warps,
-                         // in a sweep kernel of its own, internal precision kPrecI16Mixed)
-  int single_kernel = 0; // 1: one sweep kernel for every strip height instead of four class kernels
   int stack_short = 0;   // stack short queries: 0 auto (batch >= units target), 1 always, -1 never
   unsigned long long wait_ns = 2000000000ull;
 };
 
-// Planner mode of a batch: 0 FP32, 1 int16 pairs, 2 int16 pairs + exact
-// strips, 3 int16 inputs with wide accumulation (one exact strip per query).
-inline int plan_mode(int precision, const LaunchCfg &lc) {
+// Planner mode of a batch: 0 FP32, 1 int16 pairs, 3 int16 inputs with wide
+// accumulation (one exact strip per query).
+inline int plan_mode(int precision) {
   if (precision == HARU_INT16_ACC32 || precision == kPrecWideSpan) return 3;
-  if (precision == kPrecF32Span) return 0;
-  return precision == HARU_INT16 ? (lc.int16_mode == 1 ? 1 : 2) : 0;
+  return precision == HARU_INT16 ? 1 : 0;
 }
 
 // Most items a batch of nq queries can make in `mode` (per-bucket rounding
 // included: each strip height has a plain and a stacked bucket).
 inline size_t items_bound(int mode, size_t nq) {
   if (mode == 0 || mode == 3) return nq + kMaxS;
-  if (mode == 1) return (nq + 1) / 2 + 2 * kMaxS;
-  return (3 * nq + 3) / 4 + 2 * kMaxS;
+  return (nq + 1) / 2 + 2 * kMaxS;
 }
 
 // The reference as the kernels read it.
@@ -95,22 +90,14 @@ cudaError_t ws_reserve(Workspace &ws, int precision, uint32_t nq, const LaunchCf
 cudaError_t ws_reserve_upto(Workspace &ws, int precision, uint32_t max_nq, const LaunchCfg &lc);
 void ws_free(Workspace &ws);
 
-// Streams/events to run the class kernels side by side (optional).
-struct ForkJoin {
-  cudaStream_t aux[kClasses] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fork = nullptr;
-  cudaEvent_t join[kClasses] = {nullptr, nullptr, nullptr, nullptr};
-  bool ok() const { return fork != nullptr; }
-};
-
 // Enqueue the whole batch path on stream s: zero the counters, plan, pack
-// (z-score and quantise when raw), sweep each strip-height class, verify
-// segments and write (cost, column) per query. ev_prep/ev_sweep (optional)
-// are recorded after the counters are zeroed and after packing.
+// (z-score and quantise when raw), sweep, verify segments and write (cost,
+// column) per query. ev_prep/ev_sweep (optional) are recorded after the
+// counters are zeroed and after packing.
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
-                       const LaunchCfg &lc, cudaStream_t s, const ForkJoin *fj, cudaEvent_t ev_prep,
-                       cudaEvent_t ev_sweep, int64_t *d_start = nullptr);
+                       const LaunchCfg &lc, cudaStream_t s, cudaEvent_t ev_prep, cudaEvent_t ev_sweep,
+                       int64_t *d_start = nullptr);
 
 // Record `e` on `s`; inside a stream capture, as an external event node so
 // its time can be read after every replay.
@@ -149,7 +136,6 @@ struct haru_ctx {
   int64_t *d_col = nullptr;
   int64_t *d_start = nullptr;
   size_t cap_q = 0;
-  haru::ForkJoin fj;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // HARU_PROFILE
   bool profiled = false;
 

@@ -11,9 +11,9 @@
 namespace haru {
 
 // One warp's work: a query (FP32), a pair of queries packed into the two
-// 16-bit halves of every register (INT16 pair), or one query of an int16
-// batch computed exactly on integer codes in FP32 (INT16 exact). qb < 0 when
-// a pair is short. Its steps are cut into nseg segments (work units).
+// 16-bit halves of every register (INT16 pair), or one query whose int16
+// codes are computed exactly in FP32 (wide accumulation). qb < 0 when a pair
+// is short. Its steps are cut into nseg segments (work units).
 constexpr int kItemF32 = 0, kItemPair = 1, kItemExact = 2;
 // A stacked item holds two strips one above the other in the warp's PE
 // chain: lanes 0..15 sweep qa (and qb, INT16), lanes 16..31 sweep qc (and
@@ -30,8 +30,8 @@ struct Item {
   int stacked;  // 1: two stacks of 16 lanes
 };
 
-// Queries of at most this many events are stacked two to a warp strip
-// (planner modes 0 and 1) in batches large enough to fill the machine:
+// Queries of at most this many events are stacked two to a warp strip in
+// batches large enough to fill the machine:
 // stacking doubles the rows per lane, which raises throughput but also the
 // time one strip takes, so small (latency-bound) batches stay unstacked.
 constexpr int kStackMax = 16 * 16;
@@ -75,25 +75,17 @@ constexpr long kRefPad = 32 * kMaxS + kMaxTile + 64;
 // HARU_INT16 and HARU_INT16_ACC32: the FP32 and wide forms that also carry
 // each alignment's start column (haru_sdtw_batch_span).
 constexpr int kPrecF32Span = 3, kPrecWideSpan = 4;
-// The int16 form with its optional exact-integer share (int16_exact_share):
-// a kernel of its own, so that the plain int16 kernel holds the int16 strip
-// alone (one kernel, every strip height).
-constexpr int kPrecI16Mixed = 5;
 __host__ __device__ constexpr bool prec_span(int p) { return p == kPrecF32Span || p == kPrecWideSpan; }
 // Tracking-ring words per warp: costs (and start columns, +128, for the span forms).
 __host__ __device__ constexpr int ring_words(int p) { return prec_span(p) ? 256 : 128; }
 // Words of one saved strip state: costs, and start columns for the span forms.
 __host__ __device__ constexpr int state_words(int p) { return prec_span(p) ? 2 * kStateStride : kStateStride; }
 
-// Strip-height classes, tallest first: S in 13..16, 9..12, 5..8, 1..4; kernel
-// class 4 covers 1..16 in one kernel (single queue, planned into slot 0).
-constexpr int kClasses = 4;
-constexpr int kClassAll = 4;
-
-// Layout of the small integer block every batch uses (status and counters).
-constexpr int kIntStatus = 0, kIntGroups = 1, kIntItems = 2, kIntFixups = 3, kIntQueues = 4, kIntClassFirst = 8,
-              kIntClassCount = 12, kIntClassItemFirst = 16, kIntClassItemCount = 20, kIntMaxSeg = 24,
-              kIntWords = 25;
+// Layout of the small integer block every batch uses: the status word, the
+// planner's group and item counts, the fix-up count, the sweep kernel's work
+// queue counter and the most segments any item was cut into.
+constexpr int kIntStatus = 0, kIntGroups = 1, kIntItems = 2, kIntFixups = 3, kIntQueue = 4, kIntMaxSeg = 5,
+              kIntWords = 6;
 
 __host__ __device__ inline int steps_per_chunk(int S) { return (S % 2 == 0) ? S : 2 * S; }
 
@@ -157,12 +149,11 @@ struct PlanArgs {
   const uint32_t *offsets;  // nq + 1
   uint32_t nq;
   long N;
-  int pair;                 // 0: FP32 singles; 1: INT16 pairs; 2: INT16 pairs and exact-FP32 singles (1:2 warps);
-                            // 3: exact-integer singles, unsaturated (HARU_INT16_ACC32)
+  int pair;                 // 0: FP32 singles; 1: INT16 pairs; 3: exact-integer singles, unsaturated
+                            // (HARU_INT16_ACC32)
   int warps;                // items per group
   int units_target;         // wanted work units (item x segment) in the batch
-  int single;               // 1: every strip height in slot 0 (one kernel, one queue)
-  int stack;                // 1: stack queries of <= kStackMax events two to a strip (modes 0, 1)
+  int stack;                // 1: stack queries of <= kStackMax events two to a strip
   int nseg_cap;             // most segments per item (state storage is sized for it)
   Item *items;
   Group *groups;
@@ -188,9 +179,9 @@ cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s);
 // Mean and population sigma (FP64, sequential order) of each query of 1..512 events.
 cudaError_t launch_qstats(const float *events, const uint32_t *offsets, uint32_t nq, double *qstats, int *status,
                           cudaStream_t s);
-cudaError_t launch_sdtw(int precision, int cls, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s);
+cudaError_t launch_sdtw(int precision, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s);
 size_t sdtw_smem_bytes(int precision, int tile_cols, int warps);
-int sdtw_max_ctas_per_sm(int precision, int cls, int tile_cols, int warps);
+int sdtw_max_ctas_per_sm(int precision, int tile_cols, int warps);
 
 // Reference preparation.
 cudaError_t launch_ref_levels(const uint8_t *bases, size_t n, const float *model, int k, float *out,

@@ -36,6 +36,8 @@ constexpr size_t kNaBestsOff = kNaGroupsOff + ((kNaItems * sizeof(Group) + 255) 
 constexpr size_t kNaImgOff = kNaBestsOff + ((2 * kNaItems * sizeof(Best) + 255) / 256) * 256;
 constexpr size_t kNaStatsOff = kNaImgOff + ((kNaItems * kImgStride * sizeof(uint32_t) + 255) / 256) * 256;
 constexpr size_t kNaBytes = kNaStatsOff + 2 * HARU_NOALLOC_MAX_QUERIES * sizeof(double);
+// The size include/haru.h states for this array.
+static_assert(kNaBytes == 4409600, "the documented scratch size (4,409,600 bytes) is out of date");
 
 static __device__ __align__(256) unsigned char scratch[kNaBytes];
 
@@ -45,23 +47,26 @@ void *g_ptr[kMaxDevices] = {nullptr};
 
 // Device address of `scratch` on `device` (current). Looked up once per
 // device; the first lookup may load the module.
-int scratch_on(int device, unsigned char **out) {
-  if (device < 0 || device >= kMaxDevices) return HARU_EINVAL;
+cudaError_t scratch_on(int device, unsigned char **out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_ptr[device]) {
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, scratch) != cudaSuccess || !p) return HARU_ECUDA;
+    const cudaError_t e = cudaGetSymbolAddress(&p, scratch);
+    if (e != cudaSuccess) return e;
+    if (!p) return cudaErrorInvalidSymbol;
     g_ptr[device] = p;
   }
   *out = static_cast<unsigned char *>(g_ptr[device]);
-  return HARU_OK;
+  return cudaSuccess;
 }
 
 }  // namespace
 
-// Reference access for the no-allocation path (defined in api.cu).
+// Reference access and sticky CUDA errors for the no-allocation path (defined in api.cu).
 int ctx_reference(haru_ctx *ctx, int precision, const void **img, long *N, int *scale_log2, int *device,
                   cudaStream_t *stream, int *warps, int *tile, unsigned long long *wait, int *per_sm, int *sms);
+int ctx_cuda_fail(haru_ctx *ctx, cudaError_t e);
 
 }  // namespace haru
 
@@ -82,10 +87,11 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   cudaStream_t own = nullptr;
   int rc = ctx_reference(ctx, precision, &img, &N, &scale, &device, &own, &warps, &tile, &wait, &per_sm, &sms);
   if (rc != HARU_OK) return rc;
-  if (cudaSetDevice(device) != cudaSuccess) return HARU_ECUDA;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e);
   unsigned char *base = nullptr;
-  rc = scratch_on(device, &base);
-  if (rc != HARU_OK) return rc;
+  e = scratch_on(device, &base);
+  if (e != cudaSuccess) return ctx_cuda_fail(ctx, e);
   cudaStream_t s = stream ? reinterpret_cast<cudaStream_t>(stream) : own;
   int *status = reinterpret_cast<int *>(base);
   Item *items = reinterpret_cast<Item *>(base + kNaItemsOff);
@@ -97,7 +103,7 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
 
   // The array keeps the previous call's contents: the status word and the
   // counters must start at zero; items, groups and images are rewritten.
-  if (cudaMemsetAsync(status, 0, kIntWords * sizeof(int), s) != cudaSuccess) return HARU_ECUDA;
+  if ((e = cudaMemsetAsync(status, 0, kIntWords * sizeof(int), s)) != cudaSuccess) return ctx_cuda_fail(ctx, e);
   PlanArgs pa;
   pa.offsets = offsets;
   pa.nq = nq;
@@ -105,15 +111,15 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   pa.pair = precision == HARU_INT16;
   pa.warps = warps;
   pa.units_target = 1;
-  pa.single = 0;
   pa.stack = 0;  // at most HARU_NOALLOC_MAX_QUERIES queries: latency over throughput
   pa.nseg_cap = 1;
   pa.items = items;
   pa.groups = groups;
   pa.ints = status;
-  if (launch_plan(pa, s) != cudaSuccess) return HARU_ECUDA;
-  if ((flags & HARU_RAW) && launch_qstats(events, offsets, nq, qstats, status + kIntStatus, s) != cudaSuccess)
-    return HARU_ECUDA;
+  if ((e = launch_plan(pa, s)) != cudaSuccess) return ctx_cuda_fail(ctx, e);
+  if ((flags & HARU_RAW) &&
+      (e = launch_qstats(events, offsets, nq, qstats, status + kIntStatus, s)) != cudaSuccess)
+    return ctx_cuda_fail(ctx, e);
   PackArgs ka;
   ka.events = events;
   ka.offsets = offsets;
@@ -125,7 +131,7 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   ka.pair = pa.pair;
   ka.scale_log2 = scale;
   ka.status = status + kIntStatus;
-  if (launch_pack(ka, static_cast<uint32_t>(max_items), s) != cudaSuccess) return HARU_ECUDA;
+  if ((e = launch_pack(ka, static_cast<uint32_t>(max_items), s)) != cudaSuccess) return ctx_cuda_fail(ctx, e);
   SdtwArgs sa;
   sa.ref_img = img;
   sa.N = N;
@@ -144,15 +150,14 @@ extern "C" int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float
   sa.warps = warps;
   sa.wait_ns = wait;
   const size_t groups_max = (max_items + warps - 1) / warps + kMaxS;
-  for (int c = 0; c < kClasses; ++c) {
-    int cps = per_sm > 0 ? per_sm : sdtw_max_ctas_per_sm(precision, c, tile, warps);
-    size_t grid = static_cast<size_t>(sms) * (cps > 0 ? cps : 1);
-    if (grid > groups_max) grid = groups_max;
-    if (launch_sdtw(precision, c, sa, static_cast<int>(grid), static_cast<int>(max_items), s) != cudaSuccess)
-      return HARU_ECUDA;
-  }
+  const int cps = per_sm > 0 ? per_sm : sdtw_max_ctas_per_sm(precision, tile, warps);
+  size_t grid = static_cast<size_t>(sms) * (cps > 0 ? cps : 1);
+  if (grid > groups_max) grid = groups_max;
+  if ((e = launch_sdtw(precision, sa, static_cast<int>(grid), static_cast<int>(max_items), s)) != cudaSuccess)
+    return ctx_cuda_fail(ctx, e);
   int st = 0;
-  if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HARU_ECUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return HARU_ECUDA;
+  if ((e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return ctx_cuda_fail(ctx, e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return ctx_cuda_fail(ctx, e);
   return st;
 }

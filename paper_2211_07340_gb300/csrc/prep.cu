@@ -104,8 +104,6 @@ __global__ void ref_finish_kernel(const float *x, size_t n, const double *stats,
 }
 
 // --------------------------------------------------------------- planner --
-__device__ __forceinline__ int sdtw_class_dev(int S) { return S >= 13 ? 0 : (S >= 9 ? 1 : (S >= 5 ? 2 : 3)); }
-
 // Bucket key of query q: its strip height S (rows per lane), plus kMaxS + 1
 // if it is stacked (16 lanes); 0 for an invalid length. S is the least
 // height that leaves a pad row on top of the query (S = floor(M / 32) + 1,
@@ -118,24 +116,17 @@ __device__ __forceinline__ int bucket_key(const uint32_t *off, uint32_t q, long 
     if (status) report(status, HARU_EINVAL);
     return 0;
   }
-  if (stack && mode != 2 && m <= static_cast<uint32_t>(kStackMax))
+  if (stack && m <= static_cast<uint32_t>(kStackMax))
     return min(static_cast<int>(m / 16) + 1, kMaxS) + kMaxS + 1;
   return min(static_cast<int>(m / 32) + 1, kMaxS);
 }
 
-// Items of a bucket of n queries. Mode 2 (int16 split over both pipes)
-// repeats the pattern [pair, exact, exact] over runs of four queries, so a
-// group's warps mix the DPX pairs and the exact-FP32 singles 1:2.
-// Modes 0 (FP32) and 3 (int16 inputs, wide accumulation) make one item per
-// query (two per stacked item); modes 1 and 2 pair int16 queries.
+// Items of a bucket of n queries. Modes 0 (FP32) and 3 (int16 inputs, wide
+// accumulation) make one item per query (two per stacked item); mode 1
+// pairs int16 queries (four per stacked item).
 __device__ __forceinline__ bool singles(int mode) { return mode == 0 || mode == 3; }
 __device__ __forceinline__ int stacked_items(int mode, int n) { return singles(mode) ? (n + 1) / 2 : (n + 3) / 4; }
-__device__ __forceinline__ int bucket_items(int mode, int n) {
-  if (singles(mode)) return n;
-  if (mode == 1) return (n + 1) / 2;
-  const int r = n % 4;
-  return 3 * (n / 4) + (r == 0 ? 0 : (r == 3 ? 2 : 1));
-}
+__device__ __forceinline__ int bucket_items(int mode, int n) { return singles(mode) ? n : (n + 1) / 2; }
 
 // One CTA of 1024 threads. Buckets queries by strip height S (descending,
 // the longest-processing-time-first order of the work queue), keeps the
@@ -202,28 +193,19 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         tail_to = S;
       }
     }
+    // Groups, tallest strips first: one longest-first queue for the sweep kernel.
     int g = 0;
-    for (int c = 0; c < kClasses; ++c) {
-      a.ints[kIntClassFirst + c] = g;
-      a.ints[kIntQueues + c] = 0;
-      int ifirst = -1, icnt = 0;
-      for (int S = kMaxS; S >= 1; --S) {
-        if ((a.single ? 0 : sdtw_class_dev(S)) != c) continue;
-        if (icount[S] > 0 && ifirst < 0) ifirst = ibase[S];
-        icnt += icount[S];
-        const long minlen = 4 * warmup_steps(S) > 2048 ? 4 * warmup_steps(S) : 2048;
-        long lim = sweep_steps(S, a.N) / minlen;
-        if (lim < 1) lim = 1;
-        int ws = S <= tail_to ? 2 * want : want;
-        if (ws > a.nseg_cap) ws = a.nseg_cap;
-        nseg_of[S] = ws < lim ? ws : static_cast<int>(lim);
-        gbase[S] = g;
-        gcount[S] = nseg_of[S] * ((icount[S] + a.warps - 1) / a.warps);
-        g += gcount[S];
-      }
-      a.ints[kIntClassCount + c] = g - a.ints[kIntClassFirst + c];
-      a.ints[kIntClassItemFirst + c] = ifirst < 0 ? 0 : ifirst;
-      a.ints[kIntClassItemCount + c] = icnt;
+    a.ints[kIntQueue] = 0;
+    for (int S = kMaxS; S >= 1; --S) {
+      const long minlen = 4 * warmup_steps(S) > 2048 ? 4 * warmup_steps(S) : 2048;
+      long lim = sweep_steps(S, a.N) / minlen;
+      if (lim < 1) lim = 1;
+      int ws = S <= tail_to ? 2 * want : want;
+      if (ws > a.nseg_cap) ws = a.nseg_cap;
+      nseg_of[S] = ws < lim ? ws : static_cast<int>(lim);
+      gbase[S] = g;
+      gcount[S] = nseg_of[S] * ((icount[S] + a.warps - 1) / a.warps);
+      g += gcount[S];
     }
     a.ints[kIntGroups] = g;
     int most = 0;
@@ -279,15 +261,6 @@ __global__ void __launch_bounds__(1024) plan_kernel(PlanArgs a) {
         Item *it = &a.items[ibase[b] + pos / 2];
         if (pos % 2 == 0) { it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b]; }
         else it->qb = static_cast<int>(q);
-      } else if (a.pair == 2) {
-        const int w = pos % 4;
-        Item *it = &a.items[ibase[b] + 3 * (pos / 4) + (w < 2 ? 0 : w - 1)];
-        if (w == 1) {
-          it->qb = static_cast<int>(q);
-        } else {
-          it->qa = static_cast<int>(q); it->S = b; it->nseg = nseg_of[b];
-          it->kind = w == 0 ? kItemPair : kItemExact;
-        }
       } else {
         Item it;
         it.qa = static_cast<int>(q); it.qb = -1; it.S = b; it.nseg = nseg_of[b];

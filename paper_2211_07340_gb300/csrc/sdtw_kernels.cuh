@@ -384,17 +384,12 @@ struct StripF32 {
   }
 };
 
-// CAPPED: last-row costs are compared as min(CAP, cost), the saturation of
-// the int16 form, so an exact-integer strip reports what a saturating one
-// would (saturating every cell equals saturating the exact result once).
-template <bool CAPPED>
 struct TrackF32 {
   float best;
   long col;
   __device__ TrackF32() : best(__builtin_huge_valf()), col(-1) {}
   __device__ __forceinline__ void add(const uint32_t *rg, int j, long c) {
-    float f = __uint_as_float(rg[j]);
-    if constexpr (CAPPED) f = fminf(f, static_cast<float>(kCap));
+    const float f = __uint_as_float(rg[j]);
     if (f < best) { best = f; col = c; }
   }
   __device__ __forceinline__ void reduce(int width) {  // over aligned groups of `width` lanes
@@ -553,13 +548,11 @@ struct TrackF32Span {
   }
 };
 
-// Arithmetic forms of a strip: FP32 queries, int16 pairs (DPX), int16
-// codes computed exactly in FP32 and saturated like the int16 form (an int16
-// batch may run both side by side, to use the half-rate DPX/min pipe and the
-// full-rate FMA pipe at once), and int16 codes computed exactly without
-// saturation: wide accumulation (every cost of a query of <= 512 events is
-// an integer below 512 * 4094 < 2^24, so FP32 holds it exactly).
-constexpr int kFormF32 = 0, kFormI16 = 1, kFormExact = 2, kFormExactWide = 3;
+// Arithmetic forms of a strip: FP32 queries, int16 pairs (DPX), and int16
+// codes computed exactly without saturation: wide accumulation (every cost
+// of a query of <= 512 events is an integer below 512 * 4094 < 2^24, so FP32
+// holds it exactly).
+constexpr int kFormF32 = 0, kFormI16 = 1, kFormExactWide = 3;
 // and the FP32 and wide forms carrying the start column
 constexpr int kFormF32Span = 4, kFormWideSpan = 5;
 // Rows of 32 words in a saved strip state, per strip row: two oblique
@@ -578,19 +571,13 @@ struct FormOf<kFormI16, S> {
 template <int S>
 struct FormOf<kFormF32, S> {
   using Strip = StripF32<S, false>;
-  using Track = TrackF32<false>;
-  static constexpr bool kMasked = false;
-};
-template <int S>
-struct FormOf<kFormExact, S> {
-  using Strip = StripF32<S, true>;
-  using Track = TrackF32<true>;
+  using Track = TrackF32;
   static constexpr bool kMasked = false;
 };
 template <int S>
 struct FormOf<kFormExactWide, S> {
   using Strip = StripF32<S, true>;
-  using Track = TrackF32<false>;
+  using Track = TrackF32;
   static constexpr bool kMasked = false;
 };
 template <int S>
@@ -793,44 +780,28 @@ __device__ __forceinline__ void sweep_any(const SdtwArgs &A, TileStream &ts, con
     sweep_unit<kFormF32Span, S>(A, ts, g, item, ring, lane);
   } else if constexpr (PREC == kPrecWideSpan) {
     sweep_unit<kFormWideSpan, S>(A, ts, g, item, ring, lane);
-  } else if constexpr (PREC == kPrecI16Mixed) {
-    if (A.items[item].kind == kItemExact)
-      sweep_unit<kFormExact, S>(A, ts, g, item, ring, lane);
-    else
-      sweep_unit<kFormI16, S>(A, ts, g, item, ring, lane);
   } else {
     sweep_unit<kFormI16, S>(A, ts, g, item, ring, lane);
   }
 }
 
-// Strip heights of one kernel class: registers are allocated for the
-// tallest strip a kernel can meet, so short strips get their own kernels.
-template <int CLS>
-struct Cls;
-template <> struct Cls<0> { static constexpr int lo = 13, hi = 16; };
-template <> struct Cls<1> { static constexpr int lo = 9, hi = 12; };
-template <> struct Cls<2> { static constexpr int lo = 5, hi = 8; };
-template <> struct Cls<3> { static constexpr int lo = 1, hi = 4; };
-// One kernel for every strip height (a single longest-first queue), planned into slot 0.
-template <> struct Cls<4> { static constexpr int lo = 1, hi = 16; };
-template <int CLS> constexpr int slot_of() { return CLS == 4 ? 0 : CLS; }
-
-template <int PREC, int CLS, int S = Cls<CLS>::lo>
+// One kernel covers every strip height S = 1..16 (registers are allocated
+// for the tallest), fed by one longest-first queue of groups.
+template <int PREC, int S = 1>
 __device__ __forceinline__ void dispatch_sweep(int s, const SdtwArgs &A, TileStream &ts, const Group &g, int item,
                                                uint32_t *ring, int lane) {
-  if constexpr (S <= Cls<CLS>::hi) {
+  if constexpr (S <= kMaxS) {
     if (s == S)
       sweep_any<PREC, S>(A, ts, g, item, ring, lane);
     else
-      dispatch_sweep<PREC, CLS, S + 1>(s, A, ts, g, item, ring, lane);
+      dispatch_sweep<PREC, S + 1>(s, A, ts, g, item, ring, lane);
   }
 }
 
-// Two CTAs (16 warps) per SM for strips up to 12 rows per lane; kernels that
-// run strips of 13..16 rows need more registers than that allows without
-// spilling (a 168-register cap, for 12 warps per SM, measured ~20% slower).
-template <int PREC, int CLS>
-__global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kernel(SdtwArgs A) {
+// One 8-warp CTA per SM: a strip of 16 rows per lane needs ~190 registers (a
+// 168-register cap, for 12 warps per SM, measured ~20% slower).
+template <int PREC>
+__global__ void __launch_bounds__(256, 1) sdtw_kernel(SdtwArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared *sh = reinterpret_cast<Shared *>(smem);
   // layout: Shared (128 B) | per-warp tracking rings | zero words | two tile slots
@@ -850,15 +821,14 @@ __global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kern
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int first = A.ints[kIntClassFirst + slot_of<CLS>()];
-  const int count = A.ints[kIntClassCount + slot_of<CLS>()];
-  int *queue = A.ints + kIntQueues + slot_of<CLS>();
+  const int count = A.ints[kIntGroups];
+  int *queue = A.ints + kIntQueue;
   for (;;) {
     if (threadIdx.x == 0) sh->group = atomicAdd(queue, 1);
     __syncthreads();
     const int gi = sh->group;
     if (gi >= count || sh->abort) break;
-    const Group grp = A.groups[first + gi];
+    const Group grp = A.groups[gi];
     const int S = grp.S;
     const int TS = tile_width(S, A.tile_cols);
     long t_start, t_own, t_end;
@@ -879,7 +849,7 @@ __global__ void __launch_bounds__(256, (CLS == 0 || CLS == 4) ? 1 : 2) sdtw_kern
       if (ts.K > 1) ts.issue(1);
     }
     __syncthreads();
-    if (warp < grp.count) dispatch_sweep<PREC, CLS>(S, A, ts, grp, grp.first + warp, rings + warp * kRing, lane);
+    if (warp < grp.count) dispatch_sweep<PREC>(S, A, ts, grp, grp.first + warp, rings + warp * kRing, lane);
     __syncthreads();
     if (threadIdx.x == 0) sh->tile_base += ts.K;
   }
@@ -919,7 +889,7 @@ __device__ __forceinline__ void write_out(const SdtwArgs &A, const Best &b, int 
       A.out_cost[qb] = static_cast<float>(b.ib) * A.inv_scale;
       A.out_col[qb] = b.cb;
     }
-  } else if (FORM == kFormExact || FORM == kFormExactWide || FORM == kFormWideSpan) {
+  } else if (FORM == kFormExactWide || FORM == kFormWideSpan) {
     A.out_cost[qa] = b.f * A.inv_scale;
     A.out_col[qa] = b.ca;
   } else {
@@ -987,61 +957,54 @@ __device__ __forceinline__ void fixup_any(const SdtwArgs &A, int item, uint32_t 
     fixup_item<kFormF32Span, S>(A, item, ring, lane);
   } else if constexpr (PREC == kPrecWideSpan) {
     fixup_item<kFormWideSpan, S>(A, item, ring, lane);
-  } else if constexpr (PREC == kPrecI16Mixed) {
-    if (A.items[item].kind == kItemExact)
-      fixup_item<kFormExact, S>(A, item, ring, lane);
-    else
-      fixup_item<kFormI16, S>(A, item, ring, lane);
   } else {
     fixup_item<kFormI16, S>(A, item, ring, lane);
   }
 }
 
-template <int PREC, int CLS, int S = Cls<CLS>::lo>
+template <int PREC, int S = 1>
 __device__ __forceinline__ void dispatch_fixup(int s, const SdtwArgs &A, int item, uint32_t *ring, int lane) {
-  if constexpr (S <= Cls<CLS>::hi) {
+  if constexpr (S <= kMaxS) {
     if (s == S)
       fixup_any<PREC, S>(A, item, ring, lane);
     else
-      dispatch_fixup<PREC, CLS, S + 1>(s, A, item, ring, lane);
+      dispatch_fixup<PREC, S + 1>(s, A, item, ring, lane);
   }
 }
 
 constexpr int kFixWarps = 4;
 
-template <int PREC, int CLS>
+template <int PREC>
 __global__ void __launch_bounds__(kFixWarps * 32) fixup_kernel(SdtwArgs A) {
   __shared__ __align__(16) uint32_t rings[kFixWarps * ring_words(PREC)];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int first = A.ints[kIntClassItemFirst + slot_of<CLS>()];
-  const int count = A.ints[kIntClassItemCount + slot_of<CLS>()];
-  const int i = blockIdx.x * kFixWarps + warp;
-  if (i >= count) return;
-  const int item = first + i;
-  dispatch_fixup<PREC, CLS>(A.items[item].S, A, item, rings + warp * ring_words(PREC), lane);
+  const int count = A.ints[kIntItems];
+  const int item = blockIdx.x * kFixWarps + warp;
+  if (item >= count) return;
+  dispatch_fixup<PREC>(A.items[item].S, A, item, rings + warp * ring_words(PREC), lane);
 }
 
-template <int PREC, int CLS>
-cudaError_t launch_sweep_cls(const SdtwArgs &a, int grid, cudaStream_t s) {
+template <int PREC>
+cudaError_t launch_sweep_prec(const SdtwArgs &a, int grid, cudaStream_t s) {
   const size_t sm = sdtw_smem_bytes(PREC, a.tile_cols, a.warps);
-  cudaError_t e = cudaFuncSetAttribute(sdtw_kernel<PREC, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(sdtw_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm));
   if (e != cudaSuccess) return e;
-  sdtw_kernel<PREC, CLS><<<grid, a.warps * 32, sm, s>>>(a);
+  sdtw_kernel<PREC><<<grid, a.warps * 32, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int PREC, int CLS>
-cudaError_t launch_fixup_cls(const SdtwArgs &a, int fix_items, cudaStream_t s) {
+template <int PREC>
+cudaError_t launch_fixup_prec(const SdtwArgs &a, int fix_items, cudaStream_t s) {
   if (fix_items <= 0) return cudaSuccess;
-  fixup_kernel<PREC, CLS><<<(fix_items + kFixWarps - 1) / kFixWarps, kFixWarps * 32, 0, s>>>(a);
+  fixup_kernel<PREC><<<(fix_items + kFixWarps - 1) / kFixWarps, kFixWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int PREC, int CLS>
-int occupancy_cls(int tile_cols, int warps) {
+template <int PREC>
+int occupancy_prec(int tile_cols, int warps) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sdtw_kernel<PREC, CLS>, warps * 32,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sdtw_kernel<PREC>, warps * 32,
                                                 sdtw_smem_bytes(PREC, tile_cols, warps));
   return n;
 }
@@ -1050,18 +1013,19 @@ int occupancy_cls(int tile_cols, int warps) {
 }  // namespace haru
 
 // Define the entry points of the sweep kernel (launch, occupancy) or of the
-// segment fix-up kernel for precision P (0 FP32, 1 INT16) and strip-height
-// class C; one per translation unit, so the kernels compile in parallel.
-#define HARU_SDTW_SWEEP_INSTANCE(P, C)                                                         \
+// segment fix-up kernel for kernel precision P (0 FP32, 1 INT16, 2 int16
+// inputs with wide accumulation, 3 FP32 with start columns, 4 wide with start
+// columns); one per translation unit, so the kernels compile in parallel.
+#define HARU_SDTW_SWEEP_INSTANCE(P)                                                            \
   namespace haru {                                                                             \
-  cudaError_t sdtw_sweep_##P##_##C(const SdtwArgs &a, int grid, cudaStream_t s) {             \
-    return launch_sweep_cls<P, C>(a, grid, s);                                                 \
+  cudaError_t sdtw_sweep_##P(const SdtwArgs &a, int grid, cudaStream_t s) {                   \
+    return launch_sweep_prec<P>(a, grid, s);                                                   \
   }                                                                                            \
-  int sdtw_occupancy_##P##_##C(int tile_cols, int warps) { return occupancy_cls<P, C>(tile_cols, warps); } \
+  int sdtw_occupancy_##P(int tile_cols, int warps) { return occupancy_prec<P>(tile_cols, warps); } \
   }
-#define HARU_SDTW_FIXUP_INSTANCE(P, C)                                                         \
+#define HARU_SDTW_FIXUP_INSTANCE(P)                                                            \
   namespace haru {                                                                             \
-  cudaError_t sdtw_fixup_##P##_##C(const SdtwArgs &a, int fix_items, cudaStream_t s) {        \
-    return launch_fixup_cls<P, C>(a, fix_items, s);                                            \
+  cudaError_t sdtw_fixup_##P(const SdtwArgs &a, int fix_items, cudaStream_t s) {              \
+    return launch_fixup_prec<P>(a, fix_items, s);                                              \
   }                                                                                            \
   }

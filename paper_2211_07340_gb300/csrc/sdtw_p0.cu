@@ -1,0 +1,4 @@
+// FP32: the sweep kernel, every strip height (1..16).
+#include "sdtw_kernels.cuh"
+
+HARU_SDTW_SWEEP_INSTANCE(0)

@@ -114,6 +114,7 @@ class Server {
   struct BatchCtx {
     Workspace ws;
     cudaStream_t stream = nullptr;
+    cudaEvent_t start = nullptr;  // device time of the batch: start -> done
     cudaEvent_t done = nullptr;
     float *d_events = nullptr;
     uint32_t *d_off = nullptr;
@@ -193,6 +194,9 @@ class Server {
   // per-stage latency diagnosis (worker thread writes, stats() reads)
   std::atomic<uint64_t> max_stage_[3] = {{0}, {0}, {0}}, slow_stage_[3] = {{0}, {0}, {0}};
   std::atomic<uint64_t> max_sync_{0}, max_gap_{0};
+  // device execution of the slowest batch, and the longest host-side share of
+  // a batch's GPU stage (launch -> completion seen, minus device execution)
+  std::atomic<uint64_t> max_exec_{0}, max_notice_{0};
   uint64_t spin_ns_ = 0;  // keep polling this long after the last piece of work
   std::atomic<uint64_t> worst_[6] = {{0}, {0}, {0}, {0}, {0}, {0}};  // parts of the slowest turn
   void note_stage(int k, uint64_t dt) {
@@ -231,7 +235,8 @@ int Server::start() {
   for (auto &b : batches_) {
     if (e != cudaSuccess) break;
     e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&b.start);
+    if (e == cudaSuccess) e = cudaEventCreate(&b.done);
     if (e == cudaSuccess) e = cudaMalloc(&b.d_events, static_cast<size_t>(max_batch_) * slot_len_ * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&b.d_off, (max_batch_ + 1) * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&b.d_slot, max_batch_ * sizeof(uint32_t));
@@ -277,6 +282,7 @@ void Server::stop() {
     void *h[] = {b.h_off, b.h_slot, b.h_cost, b.h_col, b.h_status};
     for (void *p : h)
       if (p) cudaFreeHost(p);
+    if (b.start) cudaEventDestroy(b.start);
     if (b.done) cudaEventDestroy(b.done);
     if (b.stream) cudaStreamDestroy(b.stream);
   }
@@ -434,6 +440,8 @@ void Server::stats(haru_stream_stats *out) {
   out->slow_gpu = slow_stage_[2];
   out->max_upload_sync_ns = max_sync_;
   out->max_turn_gap_ns = max_gap_;
+  out->max_gpu_exec_ns = max_exec_;
+  out->max_notice_ns = max_notice_;
   out->worst_turn_complete_ns = worst_[0];
   out->worst_turn_upload_ns = worst_[1];
   out->worst_turn_launch_ns = worst_[2];
@@ -549,6 +557,7 @@ int Server::turn_launch() {
     }
     cudaStream_t s = b.stream;
     cudaError_t e = cudaStreamWaitEvent(s, up_done_, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(b.start, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.d_off, b.h_off, (n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.d_slot, b.h_slot, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
@@ -583,6 +592,10 @@ int Server::turn_complete() {
     if (q == cudaErrorNotReady) continue;
     if (q != cudaSuccess) return HARU_ECUDA;
     const uint64_t t = now_ns();
+    float exec_ms = 0.0f;
+    if (cudaEventElapsedTime(&exec_ms, b.start, b.done) != cudaSuccess) return HARU_ECUDA;
+    const uint64_t exec_ns = static_cast<uint64_t>(static_cast<double>(exec_ms) * 1e6);
+    if (exec_ns > max_exec_) max_exec_ = exec_ns;
     const int st = *b.h_status;
     const float s = static_cast<float>(1 << ref_.scale_log2);
     const float thr = precision_ == HARU_INT16 ? std::floor(threshold_ * s) / s : threshold_;
@@ -607,6 +620,9 @@ int Server::turn_complete() {
         note_stage(0, r.t_queued - r.t_received);
         note_stage(1, r.t_launched - r.t_queued);
         note_stage(2, t - r.t_launched);
+        const uint64_t stage = t - r.t_launched;
+        const uint64_t host_share = stage > exec_ns ? stage - exec_ns : 0;
+        if (host_share > max_notice_) max_notice_ = host_share;
         free_slots_.push_back(r.slot);
         reads_.erase(it);
       }

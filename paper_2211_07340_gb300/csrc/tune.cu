@@ -2,10 +2,9 @@
 // launch shapes and keeps the fastest in the context's configuration.
 //
 // Tuned: warps per CTA (queries or pairs sharing one reference tile stream),
-// reference tile width, the work-unit target (how finely sweeps are cut
-// into verified reference segments; 1 = never cut) and whether one sweep
-// kernel covers every strip height or four class kernels run side by side. The
-// strip height is not a free choice here: S = floor(M / 32) + 1 rows per
+// reference tile width and the work-unit target (how finely sweeps are cut
+// into verified reference segments; 1 = never cut). The strip height is not
+// a free choice here: S = floor(M / 32) + 1 rows per
 // lane (at most 16) is the smallest strip that holds a query with a pad row
 // on top, and a taller one only adds padding.
 
@@ -68,12 +67,9 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
   const int warps_c[] = {4, 8};
   const int tiles_c[] = {2048, 4096, 8192, 16384};
   const int units_c[] = {1, auto_units / 2, auto_units, 2 * auto_units};
-  const int single_c[] = {0, 1};
   float best_ms = -1.0f;
   LaunchCfg best = base;
-  for (int one : single_c)
   for (int w : warps_c)
-    if (one || precision != HARU_INT16_ACC32)  // the wide form has the single kernel only
     for (int t : tiles_c)
       for (int u : units_c) {
         if (e != cudaSuccess) break;
@@ -81,13 +77,12 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
         lc.warps = w;
         lc.tile = t;
         lc.units_target = u;
-        lc.single_kernel = one;
         e = ws_reserve(ctx->ws, precision, nq, lc);
         float ms_min = -1.0f;
         for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
           e = cudaEventRecord(e0, s);
           if (e == cudaSuccess)
-            e = ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, t_cost, t_col, lc, s, &ctx->fj,
+            e = ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, t_cost, t_col, lc, s,
                            nullptr, nullptr);
           if (e == cudaSuccess) e = cudaEventRecord(e1, s);
           if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -116,7 +111,6 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
   ctx->cfg.warps_per_cta = best.warps;
   ctx->cfg.tile_cols = best.tile;
   ctx->cfg.units_target = best.units_target;
-  ctx->cfg.single_kernel = best.single_kernel;
   if (chosen) *chosen = ctx->cfg;
   return HARU_OK;
 }
