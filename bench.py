@@ -153,10 +153,32 @@ class ClockSampler:
                 "below_1000_mhz": sum(1 for x in sm if x < 1000.0)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(ref, queries, target_s: float = 12.0, prec=None):
     """The oracle (as it stands) on the host cores over a bounded sample."""
     import oracle
     prec = oracle.PREC_I16 if prec is None else prec
+    form = {oracle.PREC_I16: "int16", oracle.PREC_F64: "fp64", oracle.PREC_F32: "fp32",
+            oracle.PREC_I32: "int16_acc32"}[prec]
     threads = os.cpu_count() or 1
     N = ref.shape[0]
     probe = queries.subset(np.arange(min(queries.nq, max(threads, 16))))
@@ -173,8 +195,21 @@ def cpu_baseline(ref, queries, target_s: float = 12.0, prec=None):
     dt = time.perf_counter() - t
     cells = float(sample.lengths.sum()) * N
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": threads, "kind": "oracle",
-            "sample": f"first {n} of {queries.nq} queries ({cells / 1e9:.1f} G cells), int16 form, "
+            "sample": f"first {n} of {queries.nq} queries ({cells / 1e9:.1f} G cells), {form} form, "
                       f"{dt:.1f} s"}
+
+
+def cpu_baselines(ref, queries, target_s: float = 8.0):
+    """The oracle's int16 form (the headline's) and its FP64 form, each on a
+    bounded sample of the workload; value/sample are the int16 form's."""
+    import oracle
+    i16 = cpu_baseline(ref, queries, target_s, oracle.PREC_I16)
+    f64 = cpu_baseline(ref, queries, target_s, oracle.PREC_F64)
+    out = dict(i16)
+    out["cpu_model"] = cpu_model()
+    out["forms"] = {"int16": {k: i16[k] for k in ("value", "unit", "sample")},
+                    "fp64": {k: f64[k] for k in ("value", "unit", "sample")}}
+    return out
 
 
 def ref_sweep(haru, args, dev):
@@ -247,10 +282,11 @@ def pick_threshold(costs, on_target):
     return float(0.5 * (c[k - 1] + c[k]))
 
 
-def run_serving(haru, args, local, w, threshold):
+def run_serving(haru, args, local, w, threshold, channels):
     """Serve a simulated flow cell in real time; latency from the delivery of
     the chunk that completes a read's 250-event prefix to its decision."""
-    chunks, q = synth.flowcell_schedule(args.serve_channels, args.serve_seconds, seed=105)
+    span = args.serve_warm + args.serve_seconds
+    chunks, q = synth.flowcell_schedule(channels, span, seed=105)
     ctx = haru.Context(local, serve_precision=haru.HARU_INT16, threshold=threshold)
     ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
     results = []
@@ -288,8 +324,7 @@ def run_serving(haru, args, local, w, threshold):
     dec = {r.read_id: r.decision for r in results}
     acc = float(np.mean([dec.get(i, 0) == int(q.on_target[i]) for i in range(q.nq)])) if q.nq else None
     N = 2 * (synth.SARS_COV_2_BASES - 5)
-    span = args.serve_seconds
-    return {"channels": args.serve_channels, "seconds": span, "warmup_s": args.serve_warm, "reads": q.nq,
+    return {"channels": channels, "seconds": args.serve_seconds, "warmup_s": args.serve_warm, "reads": q.nq,
             "decided": len(results), "precision": "int16", "threshold_z": threshold,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
@@ -303,7 +338,8 @@ def run_serving(haru, args, local, w, threshold):
             "accept_eject_accuracy_vs_truth": acc, "batches": st["batches"], "max_batch": st["max_batch"],
             "max_concurrent_batches": st["max_concurrent"], "late_chunks": late, "clocks": clk.summary(),
             "stages": {"max_upload_ms": st["max_upload_ns"] / 1e6, "max_queue_ms": st["max_queue_ns"] / 1e6,
-                       "max_gpu_ms": st["max_gpu_ns"] / 1e6, "over_10ms_upload": st["slow_upload"],
+                       "max_gpu_ms": st["max_gpu_ns"] / 1e6, "max_gpu_exec_ms": st["max_gpu_exec_ns"] / 1e6,
+                       "max_notice_ms": st["max_notice_ns"] / 1e6, "over_10ms_upload": st["slow_upload"],
                        "over_10ms_queue": st["slow_queue"], "over_10ms_gpu": st["slow_gpu"],
                        "max_upload_sync_ms": st["max_upload_sync_ns"] / 1e6,
                        "max_worker_turn_gap_ms": st["max_turn_gap_ns"] / 1e6,
@@ -367,17 +403,18 @@ def main():
     ap.add_argument("--nq", type=int, default=0, help="first nq queries only (profiling runs)")
     ap.add_argument("--units", type=int, default=0, help="work units target (0 = library default)")
     ap.add_argument("--fixed-len", type=int, default=0, help="profiling: every query this many events")
-    ap.add_argument("--single", type=int, default=-1, help="1: one sweep kernel, 0: four class kernels "
-                    "(-1 = library default; the autotuner may change it)")
     ap.add_argument("--forms", default="int16,fp32,acc32,span",
-                    help="forms to time: int16, int16exact (exact-share option), fp32, acc32 (int16 inputs, "
-                         "32-bit accumulation), span (FP32 with alignment start columns)")
+                    help="forms to time: int16, fp32, acc32 (int16 inputs, 32-bit accumulation), span (FP32 with "
+                         "alignment start columns)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the library defaults)")
     ap.add_argument("--workload", default=WORKLOAD, help="sars_uneven_8192 (default) or long_512x250")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="simulated flow-cell run (0 = skip)")
-    ap.add_argument("--serve-warm", type=float, default=2.0, help="seconds of serving excluded from latency stats")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="measured seconds of the simulated flow-cell run, after the warm-up (0 = skip)")
+    ap.add_argument("--serve-warm", type=float, default=5.0, help="seconds of serving before the measured span")
     ap.add_argument("--serve-channels", type=int, default=512)
+    ap.add_argument("--stress-channels", type=int, default=4096,
+                    help="second serving run at this many channels, same length (0 = skip)")
     ap.add_argument("--ref-sweep", action="store_true",
                     help="reference-length sweep (59,796 / 257,820 / 9,999,990 columns) instead of the benchmark")
     ap.add_argument("--sweep-reps", type=int, default=10)
@@ -417,8 +454,6 @@ def main():
         cfg.warps_per_cta = args.warps
     if args.units:
         cfg.units_target = args.units
-    if args.single >= 0:
-        cfg.single_kernel = args.single
     ctx = haru.Context(local, config=cfg)
     ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
     N = ctx.ref_length
@@ -432,18 +467,16 @@ def main():
     launches = []  # own kernels per timed step of each form
 
     def kernels_per_step():
-        # planner, query statistics (raw events), pack, then a sweep and a
-        # segment fix-up kernel per strip-height class
-        return 3 + 2 * (1 if ctx.configure().single_kernel else 4)
+        # planner, query statistics (raw events), pack, the sweep and the
+        # segment fix-up kernel
+        return 5
 
     tuned = {}
 
-    def run_form(prec, exact_share=0):
+    def run_form(prec):
         sh = stream.cuda_stream
-        ctx.configure(int16_exact_share=exact_share)
         if not args.no_tune:
-            key = ("int16_exact_share" if exact_share else
-                   {haru.HARU_INT16: "int16", haru.HARU_FP32: "fp32", haru.HARU_INT16_ACC32: "int16_acc32"}[prec])
+            key = {haru.HARU_INT16: "int16", haru.HARU_FP32: "fp32", haru.HARU_INT16_ACC32: "int16_acc32"}[prec]
             tuned[key] = ctx.autotune(prec, ev_d, off_d, raw=True, on_device=True)
         with torch.cuda.stream(stream):
             for _ in range(2):  # allocate the context workspace outside capture
@@ -501,15 +534,12 @@ def main():
     ms16 = sweep16 = ms32 = sweep32 = nan
     clocks = clocks32 = {}
     graphed = False
-    msdpx = sweepdpx = nan
     msw = sweepw = nan
     capped16 = None
     if "int16" in forms:
         ms16, sweep16, clocks, graphed = run_form(haru.HARU_INT16)
         # queries whose int16 cost saturated at CAP (cost = integer cost / 2^6, exact)
         capped16 = int((np.rint(cost_d.cpu().numpy().astype(np.float64) * 64) >= haru.HARU_INT16_CAP).sum())
-    if "int16exact" in forms:
-        msdpx, sweepdpx, _, _ = run_form(haru.HARU_INT16, exact_share=1)
     if "fp32" in forms:
         ms32, sweep32, clocks32, _ = run_form(haru.HARU_FP32)
     if "acc32" in forms:
@@ -537,7 +567,6 @@ def main():
             raise haru.HaruError(ctx.last_status(), "span batch")
         span_ms = float(np.mean(times))
         launches.append(5 * len(times))  # plan, statistics, pack, sweep, fix-up
-    ctx.configure(int16_exact_share=0)
     if "int16" in tuned:
         ctx.configure(**tuned["int16"])
 
@@ -607,6 +636,7 @@ def main():
                      "peak_probe": probe16, "frac_of_probe": ach16 / probe16,
                      "peak_probe_basis": "haru_probe_peak: the int16 cell-pair instructions on independent "
                                          "chains, no shuffles/reference/tracking, same run",
+                     "probe_ratio_int16_over_fp32": probe16 / probe32,
                      **dram_rate(profiled_traffic("int16"), cells, ach16)},
         "fp32": {"value": value32, "unit": "GCUPS", "ms_per_step": ms32, "dtype": "f32",
                  "roofline": {"bound": "alu", "kernel": "sdtw_kernel<FP32>", "achieved": ach32, "peak": peak32,
@@ -616,10 +646,6 @@ def main():
                               "peak_probe": probe32, "frac_of_probe": ach32 / probe32,
                               **dram_rate(profiled_traffic("fp32"), cells, ach32)},
                  "clocks": clocks32},
-        "int16_exact_share": ({"value": total_cells / (msdpx / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": msdpx,
-                               "sweep_gcups": cells / (sweepdpx / 1e3) / 1e9,
-                               "note": "int16 with two thirds of the warps on exact-integer FP32 strips"}
-                              if msdpx == msdpx else None),
         "int16_acc32": ({"value": total_cells / (msw / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": msw,
                          "sweep_gcups": cells / (sweepw / 1e3) / 1e9,
                          "note": "int16 inputs with 32-bit accumulation (Section 4.3's PE): exact integer costs, "
@@ -642,11 +668,13 @@ def main():
         held = synth.workload("sars_heldout_1024", seed=103)
         hc, _ = ctx.sdtw_batch(haru.HARU_FP32, held.queries.events, held.queries.offsets)
         thr = pick_threshold(hc.astype(np.float64), held.queries.on_target)
-        result["serving"] = run_serving(haru, args, local, w, thr)
+        result["serving"] = run_serving(haru, args, local, w, thr, args.serve_channels)
+        if args.stress_channels > 0:
+            result["serving_stress"] = run_serving(haru, args, local, w, thr, args.stress_channels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         ref_levels = oracle.ref_levels(w.genome, w.model, w.k)
-        result["cpu_baseline"] = cpu_baseline(ref_levels, q)
+        result["cpu_baseline"] = cpu_baselines(ref_levels, q)
     if rank == 0:
         print(json.dumps(result))
     ctx.close()

@@ -1,0 +1,240 @@
+"""Full-size parity: every query of every benchmark-shaped workload against
+the oracle, in the launch shapes the benchmark times.
+
+sars_uneven_8192 (8,192 queries, M ~ U[100, 500]): int16, FP32, int16 inputs
+with 32-bit accumulation and FP32 with start columns, in the default launch
+shape and in the shape the autotuner picks (the benchmark's).
+sars_4096x250 + sars_heldout_1024 (the precision study): int16 at scale 2^6
+and the wide form at 2^5 and 2^6 bit-exact, FP32 bitwise and within 1e-5 of
+FP64, and the accept/eject agreement report.
+long_512x250 (9,999,990 columns, cut into verified segments) and
+rfc1_512x250 (257,820 columns): int16 and FP32.
+
+int16 and the wide form: bit-exact cost and end column. FP32: bitwise equal
+to the FP32 oracle, within 1e-5 relative of FP64, FP64's end column wherever
+its runner-up is more than 1e-5 away. No sampling: each test checks all of
+its queries. The oracle runs multi-threaded on the host cores; results are
+cached per (workload, form, scale) for the session.
+"""
+import functools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import compare_fp32, compare_int16
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def haru():
+    import paper_2211_07340_gb300 as h
+    h.build_library()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return h
+
+
+@functools.lru_cache(maxsize=None)
+def work(name):
+    w = synth.workload(name)
+    return w, oracle.ref_levels(w.genome, w.model, w.k)
+
+
+def run_device(h, ctx, prec, q, span=False):
+    """The benchmark's call: device pointers, raw events z-scored on the device."""
+    dev = torch.device("cuda:0")
+    ev = torch.from_numpy(q.events).to(dev)
+    off = torch.from_numpy(q.offsets.astype(np.int32)).to(dev)
+    cost = torch.full((q.nq,), -1.0, dtype=torch.float32, device=dev)
+    col = torch.full((q.nq,), -9, dtype=torch.int64, device=dev)
+    s = torch.cuda.current_stream().cuda_stream
+    if span:
+        start = torch.full((q.nq,), -9, dtype=torch.int64, device=dev)
+        ctx.sdtw_batch_span_device(prec, ev, off, cost, col, start, stream=s)
+        return cost.cpu().numpy(), col.cpu().numpy(), start.cpu().numpy()
+    ctx.sdtw_batch_device(prec, ev, off, cost, col, stream=s)
+    return cost.cpu().numpy(), col.cpu().numpy()
+
+
+# ------------------------------------------------------ sars_uneven_8192 --
+@pytest.fixture(scope="module")
+def uneven(haru):
+    """The benchmark batch in the default launch shape and, per form, in the
+    autotuned shape; each form's results must be identical in both."""
+    w, ref = work("sars_uneven_8192")
+    q = w.queries
+    forms = (haru.HARU_INT16, haru.HARU_FP32, haru.HARU_INT16_ACC32)
+    out = {}
+    with haru.Context() as ctx:
+        ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
+        for p in forms:
+            out[p] = run_device(haru, ctx, p, q)
+        out["span"] = run_device(haru, ctx, haru.HARU_FP32, q, span=True)
+        tuned = {}
+        for p in forms:
+            tuned[p] = ctx.autotune(p, q.events, q.offsets)
+            c, j = run_device(haru, ctx, p, q)
+            np.testing.assert_array_equal(c, out[p][0], err_msg=f"precision {p}, tuned shape {tuned[p]}")
+            np.testing.assert_array_equal(j, out[p][1], err_msg=f"precision {p}, tuned shape {tuned[p]}")
+    print(json.dumps({"autotuned_sars_uneven_8192": {str(k): v for k, v in tuned.items()}}))
+    return q, ref, out
+
+
+def test_uneven_8192_int16_every_query(haru, uneven):
+    q, ref, out = uneven
+    c, j = out[haru.HARU_INT16]
+    compare_int16(c, j, ref, q.events, q.offsets)
+
+
+def test_uneven_8192_fp32_every_query(haru, uneven):
+    q, ref, out = uneven
+    c, j = out[haru.HARU_FP32]
+    compare_fp32(c, j, ref, q.events, q.offsets)
+
+
+def test_uneven_8192_wide_accumulation_every_query(haru, uneven):
+    q, ref, out = uneven
+    c, j = out[haru.HARU_INT16_ACC32]
+    compare_int16(c, j, ref, q.events, q.offsets, prec=oracle.PREC_I32)
+
+
+def test_uneven_8192_start_columns_every_query(haru, uneven):
+    q, ref, out = uneven
+    cs, js, ss = out["span"]
+    np.testing.assert_array_equal(cs, out[haru.HARU_FP32][0])
+    np.testing.assert_array_equal(js, out[haru.HARU_FP32][1])
+    o = oracle.batch(oracle.PREC_F32, ref, q.events, q.offsets, start=True)
+    np.testing.assert_array_equal(js, o.col)
+    np.testing.assert_array_equal(ss, o.start)
+    assert ((ss >= 0) & (ss <= js)).all()
+
+
+# -------------------------------------------------- the precision study --
+def decisions(cost, thr):
+    return cost <= thr
+
+
+def test_precision_study_4096x250_and_heldout(haru):
+    """Config 2 in full: the 4,096 queries and the 1,024 held-out ones, int16
+    at 2^6 and the wide form (the paper's PE) at 2^5 and 2^6 bit-exact, FP32
+    bitwise; then cost error against FP64, end-column agreement and
+    accept/eject agreement at a threshold fixed on the held-out set (FP64
+    costs; fewest misclassified, midpoint of the gap), and the scale sweep
+    2..128."""
+    import bench
+    w, ref = work("sars_4096x250")
+    held = synth.workload("sars_heldout_1024")
+    q, hq = w.queries, held.queries
+    with haru.Context() as ctx:
+        res = {}
+        for k in range(1, 8):
+            ctx.ref_load(ref, scale_log2=k)
+            for name, qq in (("test", q), ("held", hq)):
+                res[(name, "i16", k)] = ctx.sdtw_batch(haru.HARU_INT16, qq.events, qq.offsets)
+                res[(name, "i32", k)] = ctx.sdtw_batch(haru.HARU_INT16_ACC32, qq.events, qq.offsets)
+        for name, qq in (("test", q), ("held", hq)):
+            res[(name, "f32")] = ctx.sdtw_batch(haru.HARU_FP32, qq.events, qq.offsets)
+    for name, qq in (("test", q), ("held", hq)):
+        compare_int16(*res[(name, "i16", 6)], ref, qq.events, qq.offsets, scale_log2=6)
+        for k in (5, 6):
+            compare_int16(*res[(name, "i32", k)], ref, qq.events, qq.offsets, scale_log2=k, prec=oracle.PREC_I32)
+    _, o64 = compare_fp32(*res[("test", "f32")], ref, q.events, q.offsets)
+    _, h64 = compare_fp32(*res[("held", "f32")], ref, hq.events, hq.offsets)
+    thr = bench.pick_threshold(h64.cost, hq.on_target)
+    c16, j16 = res[("test", "i16", 6)]
+    c32, j32 = res[("test", "f32")]
+    d64 = decisions(o64.cost, thr)
+    agree = {}
+    for key, (c, _) in (("fp32", res[("test", "f32")]), ("int16_scale64", res[("test", "i16", 6)]),
+                        ("int16_acc32_scale32", res[("test", "i32", 5)]),
+                        ("int16_acc32_scale64", res[("test", "i32", 6)])):
+        s_ = {"fp32": None, "int16_scale64": 64, "int16_acc32_scale32": 32, "int16_acc32_scale64": 64}[key]
+        t = thr if s_ is None else np.floor(thr * s_) / s_
+        agree[key] = float(np.mean(decisions(c.astype(np.float64), t) == d64))
+    assert min(agree.values()) >= 0.999, agree
+    sweep = {}
+    for k in range(1, 8):
+        ck, jk = res[("test", "i16", k)]
+        cw, jw = res[("test", "i32", k)]
+        s_ = 2 ** k
+        sweep[s_] = {"position_agreement_vs_fp32": float(np.mean(jk == j32)),
+                     "position_within_5_vs_fp32": float(np.mean(np.abs(jk - j32) <= 5)),
+                     "capped": int(np.sum(ck * s_ >= haru.HARU_INT16_CAP)),
+                     "acc32_position_agreement_vs_fp32": float(np.mean(jw == j32)),
+                     "acc32_decision_agreement_vs_fp64":
+                         float(np.mean(decisions(cw.astype(np.float64), np.floor(thr * s_) / s_) == d64))}
+    # wide accumulation never saturates: equal to int16 below CAP, larger above
+    cw64 = res[("test", "i32", 6)][0]
+    below = c16 * 64 < haru.HARU_INT16_CAP
+    np.testing.assert_array_equal(cw64[below], c16[below])
+    assert (cw64[~below] * 64 >= haru.HARU_INT16_CAP).all()
+
+    def err(c, j):
+        r = np.abs(c.astype(np.float64) - o64.cost) / o64.cost
+        return {"max_rel_err": float(r.max()), "p99_rel_err": float(np.percentile(r, 99)),
+                "col_agreement": float(np.mean(j == o64.col)),
+                "col_within_5": float(np.mean(np.abs(j - o64.col) <= 5))}
+    report = {"threshold_z": thr, "decision_agreement_vs_fp64": agree,
+              "fp32": err(c32, j32), "int16_scale64": err(c16, j16),
+              "int16_acc32_scale32": err(*res[("test", "i32", 5)]),
+              "int16_acc32_scale64": err(*res[("test", "i32", 6)]),
+              "truth_accuracy_fp64": float(np.mean(d64 == q.on_target)),
+              "scale_sweep_vs_fp32": sweep,
+              "bit_exact": "int16 2^6 and wide 2^5, 2^6 on all 4,096 + 1,024 queries"}
+    out = os.environ.get("HARU_PRECISION_REPORT")
+    if out:
+        with open(out, "w") as f:
+            json.dump(report, f, indent=1)
+    print(json.dumps(report))
+
+
+# ------------------------------------------- long and RFC1-sized references --
+@pytest.fixture(scope="module")
+def long_ref(haru):
+    w, ref = work("long_512x250")
+    assert ref.shape[0] == 9_999_990
+    q = w.queries
+    with haru.Context() as ctx:
+        ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
+        assert ctx.ref_length == ref.shape[0]
+        r16 = run_device(haru, ctx, haru.HARU_INT16, q)
+        st16 = ctx.last_stats()
+        r32 = run_device(haru, ctx, haru.HARU_FP32, q)
+        st32 = ctx.last_stats()
+    # the sweeps were cut into many verified reference segments
+    assert st16["max_segments"] > 4 and st32["max_segments"] > 4
+    print(json.dumps({"long_reference": {"int16": st16, "fp32": st32}}))
+    return q, ref, r16, r32
+
+
+def test_long_reference_int16_every_query(long_ref):
+    q, ref, (c, j), _ = long_ref
+    compare_int16(c, j, ref, q.events, q.offsets)
+
+
+def test_long_reference_fp32_every_query(long_ref):
+    q, ref, _, (c, j) = long_ref
+    compare_fp32(c, j, ref, q.events, q.offsets)
+    on = q.on_target
+    assert (np.abs(j[on] - q.truth_end[on]) <= 8).mean() >= 0.9
+
+
+def test_rfc1_reference_every_query(haru):
+    """The RFC1-sized reference (128,915 bases, 257,820 columns on both
+    strands), 512 x 250 queries: int16 and FP32 against the oracle."""
+    w, ref = work("rfc1_512x250")
+    assert ref.shape[0] == 257_820
+    q = w.queries
+    with haru.Context() as ctx:
+        ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
+        c16, j16 = run_device(haru, ctx, haru.HARU_INT16, q)
+        c32, j32 = run_device(haru, ctx, haru.HARU_FP32, q)
+    compare_int16(c16, j16, ref, q.events, q.offsets)
+    compare_fp32(c32, j32, ref, q.events, q.offsets)

@@ -3,8 +3,8 @@
 int16: bit-exact cost and end column. FP32: bitwise equal to the FP32
 oracle (sub, abs, add and min round identically), within 1e-5 relative of
 FP64, same column as FP64 unless the FP64 runner-up ties within 1e-5.
-Sizes span several reference tiles and ragged tails; the full-size batch is
-checked on a sample of queries the oracle recomputes one by one.
+Sizes span several reference tiles and ragged tails; the benchmark-sized
+workloads are checked in full in test_gpu_full_size.py.
 """
 import numpy as np
 import pytest
@@ -180,49 +180,6 @@ def test_device_pointers_match_host_path(haru, sars):
             np.testing.assert_array_equal(dj.cpu().numpy(), hj)
 
 
-def test_uneven_8192_full_size_sampled(haru, sars):
-    """The full 8,192-query uneven batch in one launch, in the default launch
-    shape and in the shape the autotuner picks for it (the one the benchmark
-    times): each form gives identical results in both, and three queries of
-    every 32-event length band are re-checked one by one against the oracle
-    (int16, FP32, int16 with 32-bit accumulation, FP32 start columns)."""
-    _, ref = sars
-    qs = synth.workload("sars_uneven_8192").queries
-    lens = qs.lengths
-    rng = np.random.default_rng(0)
-    idx = []
-    for band in range(3, 16):  # every strip height, stacked (<= 256 events) and not
-        cand = np.nonzero(lens // 32 == band)[0]
-        idx += list(rng.choice(cand, size=min(3, cand.shape[0]), replace=False))
-    idx = np.array(sorted(set(idx)))
-    forms = (haru.HARU_INT16, haru.HARU_FP32, haru.HARU_INT16_ACC32)
-    with haru.Context() as ctx:
-        ctx.ref_load(ref)
-        out = {p: ctx.sdtw_batch(p, qs.events, qs.offsets) for p in forms}
-        cs, js, ss = ctx.sdtw_batch_span(haru.HARU_FP32, qs.events, qs.offsets)
-        for p in forms:
-            ctx.autotune(p, qs.events, qs.offsets)
-            c, j = ctx.sdtw_batch(p, qs.events, qs.offsets)
-            np.testing.assert_array_equal(c, out[p][0], err_msg=f"precision {p}, tuned shape")
-            np.testing.assert_array_equal(j, out[p][1], err_msg=f"precision {p}, tuned shape")
-    c16, j16 = out[haru.HARU_INT16]
-    c32, j32 = out[haru.HARU_FP32]
-    cw, jw = out[haru.HARU_INT16_ACC32]
-    compare_int16(c16, j16, ref, qs.events, qs.offsets, idx=idx)
-    compare_fp32(c32, j32, ref, qs.events, qs.offsets, idx=idx)
-    compare_int16(cw, jw, ref, qs.events, qs.offsets, idx=idx, prec=oracle.PREC_I32)
-    # start columns: costs and end columns of the FP32 form, starts of the oracle
-    np.testing.assert_array_equal(cs, c32)
-    np.testing.assert_array_equal(js, j32)
-    sub_ev, sub_off = subset(qs.events, qs.offsets, idx)
-    o = oracle.batch(oracle.PREC_F32, ref, sub_ev, sub_off, start=True)
-    np.testing.assert_array_equal(ss[idx], o.start)
-    # every query got a result
-    assert (j16 >= 0).all() and (j32 >= 0).all() and (jw >= 0).all()
-    assert ((ss >= 0) & (ss <= js)).all()
-    assert np.isfinite(c32).all()
-
-
 @pytest.mark.parametrize("units", [1, 4096, 100_000])
 def test_reference_segments_are_exact(haru, sars, units):
     """Splitting every sweep into speculative reference segments (verified
@@ -265,44 +222,6 @@ def test_autotuner_keeps_results(haru, sars):
             c, j = ctx.sdtw_batch(p, qs.events, qs.offsets)
             np.testing.assert_array_equal(c, before[i][0])
             np.testing.assert_array_equal(j, before[i][1])
-
-
-def test_int16_split_over_both_pipes_is_identical(haru, sars):
-    """int16 batches can run two thirds of their warps as exact-integer FP32
-    strips or (default) all as packed DPX pairs; results are bit-identical,
-    with and without reference segments, and equal the int16 oracle."""
-    _, ref = sars
-    qs = synth.workload("sars_uneven_8192", nq=523).queries
-    out = {}
-    for share in (0, 1):
-        for units in (1, 0):
-            with haru.Context(int16_exact_share=share, units_target=units) as ctx:
-                ctx.ref_load(ref)
-                out[(share, units)] = ctx.sdtw_batch(haru.HARU_INT16, qs.events, qs.offsets)
-    base = out[(0, 1)]
-    for k, (c, j) in out.items():
-        np.testing.assert_array_equal(c, base[0], err_msg=str(k))
-        np.testing.assert_array_equal(j, base[1], err_msg=str(k))
-    compare_int16(base[0], base[1], ref, qs.events, qs.offsets, idx=np.arange(0, 523, 29))
-
-
-@pytest.mark.parametrize("units", [1, 0])
-def test_single_sweep_kernel_is_identical(haru, sars, units):
-    """One sweep kernel over every strip height (one longest-first queue)
-    gives the four class kernels' results bit for bit, for both forms."""
-    _, ref = sars
-    qs = synth.workload("sars_uneven_8192", nq=611).queries
-    out = {}
-    for one in (0, 1):
-        with haru.Context(single_kernel=one, units_target=units) as ctx:
-            ctx.ref_load(ref)
-            out[one] = [ctx.sdtw_batch(p, qs.events, qs.offsets) for p in (haru.HARU_INT16, haru.HARU_FP32)]
-    for p in range(2):
-        np.testing.assert_array_equal(out[1][p][0], out[0][p][0])
-        np.testing.assert_array_equal(out[1][p][1], out[0][p][1])
-    idx = np.arange(0, 611, 47)
-    compare_int16(out[1][0][0], out[1][0][1], ref, qs.events, qs.offsets, idx=idx)
-    compare_fp32(out[1][1][0], out[1][1][1], ref, qs.events, qs.offsets, idx=idx)
 
 
 @pytest.mark.parametrize("units", [1, 4096])
