@@ -8,8 +8,9 @@ The arithmetic lives in sdtw_oracle.cpp (plain C++17, compiled with
 -ffp-contract=off): Eq. 1 and Algorithm 1 (full matrix), Algorithm 2 (one
 rolling cost array), the Section 4.3 processing-element chain (oblique
 order), the Section 4.1 reference synthesis, z-score and fixed-point
-quantiser. This module only builds that file and marshals numpy
-arrays through ctypes.
+quantiser; and in event_oracle.cpp: the event detection and adaptor trimming
+of the Section 4.1 pre-processing (two-window t-test). This module only
+builds those files and marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
 
@@ -22,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sdtw_oracle.cpp")
+_SRC_EVENTS = os.path.join(_HERE, "event_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -32,10 +34,11 @@ PREC_F32, PREC_I16, PREC_F64, PREC_I32 = 0, 1, 2, 3  # PREC_I32: int16 inputs, 3
 def build(force: bool = False) -> str:
     """Compile the oracle with the host C++ compiler (no CUDA involved)."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC),
+                                                                              os.path.getmtime(_SRC_EVENTS)):
             tmp = _LIB + f".{os.getpid()}.tmp"
             subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
-                                   "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp])
+                                   "-fPIC", "-shared", "-pthread", _SRC, _SRC_EVENTS, "-o", tmp])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -75,6 +78,16 @@ def _load():
         lib.oracle_sdtw_wavefront_f64.argtypes = [P, ctypes.c_int, P, ctypes.c_long, P, P, P]
         lib.oracle_sdtw_wavefront_f64.restype = None
         lib.oracle_batch.restype = ctypes.c_int
+        L = ctypes.c_long
+        lib.oracle_event_tstat.argtypes = [P, L, ctypes.c_int, P, P]
+        lib.oracle_event_tstat.restype = None
+        lib.oracle_event_boundaries.argtypes = [P, L, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, L]
+        lib.oracle_event_boundaries.restype = L
+        lib.oracle_read_events.argtypes = [P, L, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, L, L, P]
+        lib.oracle_read_events.restype = L
+        lib.oracle_signal_batch.argtypes = [P, P, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, L, L, ctypes.c_int, P, P]
+        lib.oracle_signal_batch.restype = None
         lib.oracle_cap.restype = ctypes.c_int
         lib.oracle_qmax.restype = ctypes.c_int
         _lib = lib
@@ -236,3 +249,60 @@ def batch(prec: int, ref, events, offsets, scale_log2: int = 6, normalize_ref: b
         raise ValueError(f"invalid input (query {bad.value})")
     return BatchResult(cost, col, ru if prec == PREC_F64 else None, ic if prec in (PREC_I16, PREC_I32) else None,
                        st)
+
+
+# --------------------------------------------------- event detection --
+# Defaults read for R9.4 (see event_oracle.cpp): windows of 3 and 6 samples,
+# t thresholds 1.40 and 9.00 (in hundredths), 50 adaptor events trimmed,
+# 250 query events.
+EVENT_DEFAULTS = {"w1": 3, "w2": 6, "tau1_centi": 140, "tau2_centi": 900, "trim": 50, "max_events": 250}
+
+
+def event_tstat(x, w: int):
+    """Two-window t statistic of every position 0..n as (num, den): t^2 =
+    num / den; den = 0 where it is undefined (positions < w or > n - w)."""
+    x = np.ascontiguousarray(x, dtype=np.int16)
+    n = x.shape[0]
+    num = np.empty(n + 1, dtype=np.int64)
+    den = np.empty(n + 1, dtype=np.int64)
+    _load().oracle_event_tstat(_p(x), n, int(w), _p(num), _p(den))
+    return num, den
+
+
+def event_boundaries(x, w1=3, w2=6, tau1_centi=140, tau2_centi=900) -> np.ndarray:
+    """Sample positions where a new event starts (0 excluded), ascending."""
+    x = np.ascontiguousarray(x, dtype=np.int16)
+    n = x.shape[0]
+    out = np.empty(n + 1, dtype=np.int64)
+    nb = _load().oracle_event_boundaries(_p(x), n, int(w1), int(w2), int(tau1_centi), int(tau2_centi), _p(out),
+                                         n + 1)
+    return out[:nb].copy()
+
+
+def read_events(x, w1=3, w2=6, tau1_centi=140, tau2_centi=900, trim=50, max_events=250) -> np.ndarray:
+    """The query of one read: means of events [trim, trim + max_events) (float32)."""
+    x = np.ascontiguousarray(x, dtype=np.int16)
+    out = np.empty(max(1, int(max_events)), dtype=np.float32)
+    k = _load().oracle_read_events(_p(x), x.shape[0], int(w1), int(w2), int(tau1_centi), int(tau2_centi),
+                                   int(trim), int(max_events), _p(out))
+    return out[:k].copy()
+
+
+def signal_events(samples, offsets, threads: int = 0, **params):
+    """Every read of a raw-signal batch to its query events: (events float32
+    CSR, offsets uint32[nreads + 1])."""
+    p = dict(EVENT_DEFAULTS, **params)
+    samples = np.ascontiguousarray(samples, dtype=np.int16)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+    nr = offsets.shape[0] - 1
+    cap = int(p["max_events"])
+    out = np.empty(max(1, nr * cap), dtype=np.float32)
+    counts = np.zeros(max(1, nr), dtype=np.uint32)
+    smp = samples if samples.shape[0] else np.zeros(1, np.int16)
+    _load().oracle_signal_batch(_p(smp), _p(offsets), nr, int(p["w1"]), int(p["w2"]), int(p["tau1_centi"]),
+                                int(p["tau2_centi"]), int(p["trim"]), cap, int(threads), _p(out), _p(counts))
+    counts = counts[:nr]
+    off = np.zeros(nr + 1, dtype=np.uint32)
+    off[1:] = np.cumsum(counts)
+    ev = np.concatenate([out[r * cap:r * cap + int(counts[r])] for r in range(nr)]) if nr else np.zeros(0)
+    return ev.astype(np.float32), off

@@ -159,6 +159,133 @@ def make_queries(lengths, on_fraction: float, seed: int, genome_on: np.ndarray,
     return Queries(ev.astype(np.float32), off, on, truth)
 
 
+# --------------------------------------------------------- raw signal --
+# The sequencer's raw output: integer ADC samples at 4 kHz. A level of the
+# pore model holds for a dwell of several samples, each sample is the level
+# plus Gaussian noise, and the current is digitised as
+# adc = round(pA * ADC_DIGITISATION / ADC_RANGE_PA) - ADC_OFFSET (the R9.4
+# MinION's digitisation and range; the offset is arbitrary). Before the
+# genome, a read passes the sequencing adaptor: ADAPTOR_LEVELS levels drawn
+# from their own distribution.
+SAMPLE_RATE_HZ = 4000
+ADC_DIGITISATION = 8192
+ADC_RANGE_PA = 1402.1
+ADC_OFFSET = 10
+ADAPTOR_LEVELS = 50
+
+
+@dataclasses.dataclass
+class SignalReads:
+    """A batch of raw-signal reads in CSR form.
+
+    samples[offsets[r]:offsets[r+1]] are read r's int16 ADC samples.
+    level_pos[i] is, for sample i, the index (in the forward-then-reverse
+    strand concatenation of the read's source genome) of the pore-model level
+    it was drawn from; -1 for adaptor samples and for off-target reads.
+    """
+
+    samples: np.ndarray  # int16 [sum n]
+    offsets: np.ndarray  # uint32 [nreads + 1]
+    on_target: np.ndarray  # bool [nreads]
+    level_pos: np.ndarray  # int64 [sum n]
+
+    @property
+    def nreads(self) -> int:
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def lengths(self) -> np.ndarray:
+        return np.diff(self.offsets.astype(np.int64))
+
+    def read(self, r: int) -> np.ndarray:
+        return self.samples[self.offsets[r]:self.offsets[r + 1]]
+
+    def subset(self, idx) -> "SignalReads":
+        idx = np.asarray(idx, dtype=np.int64)
+        parts = [self.read(int(r)) for r in idx]
+        pos = [self.level_pos[self.offsets[r]:self.offsets[r + 1]] for r in idx]
+        off = np.zeros(len(parts) + 1, dtype=np.uint32)
+        off[1:] = np.cumsum([p.shape[0] for p in parts])
+        cat = (lambda xs, dt: np.concatenate(xs).astype(dt) if xs else np.zeros(0, dt))
+        return SignalReads(cat(parts, np.int16), off, self.on_target[idx].copy(), cat(pos, np.int64))
+
+
+def to_adc(pa: np.ndarray) -> np.ndarray:
+    return (np.rint(pa * (ADC_DIGITISATION / ADC_RANGE_PA)) - ADC_OFFSET).astype(np.int16)
+
+
+def _signal(rng: np.random.Generator, levels: np.ndarray, pos: np.ndarray, dwell_min: int, dwell_mean: float,
+            noise_sd: float):
+    """Samples of a run of levels: each level held for dwell_min + Geometric
+    samples (mean dwell_mean), each sample the level plus N(0, noise_sd) pA."""
+    p = 1.0 / max(1.0, dwell_mean - dwell_min + 1.0)
+    dwell = dwell_min - 1 + rng.geometric(p, size=levels.shape[0])
+    pa = np.repeat(levels.astype(np.float64), dwell) + rng.normal(0.0, noise_sd, size=int(dwell.sum()))
+    return to_adc(pa), np.repeat(pos, dwell)
+
+
+def make_signal_reads(n_levels, on_fraction: float, seed: int, genome_on: np.ndarray, genome_off: np.ndarray,
+                      model: np.ndarray, k: int = 6, adaptor_levels: int = ADAPTOR_LEVELS, p_skip: float = 0.1,
+                      dwell_min: int = 4, dwell_mean: float = 10.0, noise_sd: float = 2.5,
+                      shuffle: bool = True) -> SignalReads:
+    """Raw-signal reads: read r passes the adaptor (adaptor_levels levels
+    ~ N(75, 8) pA), then follows a random strand and start of genome_on (the
+    first round(on_fraction * n) reads, order shuffled) or genome_off through
+    the pore model for n_levels[r] levels, each skipped with probability
+    p_skip."""
+    n_levels = np.asarray(n_levels, dtype=np.int64)
+    nr = n_levels.shape[0]
+    rng = np.random.default_rng(seed)
+    on = np.zeros(nr, dtype=bool)
+    on[: int(round(on_fraction * nr))] = True
+    if shuffle:
+        on = on[rng.permutation(nr)]
+    s_on = _Strands(genome_on, model, k)
+    s_off = _Strands(genome_off, model, k) if (~on).any() else None
+    parts, poss = [], []
+    for r in range(nr):
+        src = s_on if on[r] else s_off
+        m = int(n_levels[r])
+        strand = int(rng.integers(0, 2))
+        levels = src.fwd if strand == 0 else src.rev
+        start = int(rng.integers(0, max(1, levels.shape[0] - m)))
+        idx = np.arange(start, min(levels.shape[0], start + m))
+        idx = idx[rng.random(idx.shape[0]) >= p_skip]
+        ad = rng.normal(75.0, 8.0, size=adaptor_levels)
+        a_smp, a_pos = _signal(rng, ad, np.full(adaptor_levels, -1, np.int64), dwell_min, dwell_mean, noise_sd)
+        gpos = (strand * src.fwd.shape[0] + idx) if on[r] else np.full(idx.shape[0], -1, np.int64)
+        g_smp, g_pos = _signal(rng, levels[idx], gpos.astype(np.int64), dwell_min, dwell_mean, noise_sd)
+        parts.append(np.concatenate([a_smp, g_smp]))
+        poss.append(np.concatenate([a_pos, g_pos]))
+    off = np.zeros(nr + 1, dtype=np.uint32)
+    off[1:] = np.cumsum([p.shape[0] for p in parts])
+    smp = np.concatenate(parts).astype(np.int16) if parts else np.zeros(0, np.int16)
+    pos = np.concatenate(poss).astype(np.int64) if poss else np.zeros(0, np.int64)
+    return SignalReads(smp, off, on, pos)
+
+
+def signal_workload(name: str, nreads: int | None = None, seed: int | None = None):
+    """Raw-signal forms of the paper-shaped workloads: (genome, model, k, SignalReads).
+
+    sars_signal_32x250      32 reads whose trimmed prefixes hold ~250 events
+    sars_signal_uneven_8192 8,192 reads, genome levels uniform in [100, 500]
+                            plus a margin, half on-target
+    """
+    model = pore_model(6)
+    g_on = genome(SARS_COV_2_BASES, SEED_GENOME_ON)
+    g_off = genome(SARS_COV_2_BASES, SEED_GENOME_OFF)
+    table = {"sars_signal_32x250": (32, 110, None), "sars_signal_uneven_8192": (8192, 111, (100, 500))}
+    n_default, s_default, span = table[name]
+    n = n_default if nreads is None else nreads
+    s = s_default if seed is None else seed
+    if span is None:
+        lv = np.full(n, 250, dtype=np.int64)
+    else:
+        lv = np.random.default_rng(s + 1000).integers(span[0], span[1] + 1, size=n)
+    lv = lv + lv // 4 + 16  # levels beyond the prefix, so that skips and merges leave enough events
+    return g_on, model, 6, make_signal_reads(lv, 0.5, s, g_on, g_off, model, 6)
+
+
 def random_signal(n: int, seed: int, scale: float = 12.0, loc: float = 90.0) -> np.ndarray:
     """Generic Gaussian signal (pA) for small parity cases."""
     return np.random.default_rng(seed).normal(loc, scale, size=n).astype(np.float32)
