@@ -170,6 +170,66 @@ int haru_sdtw_batch(haru_ctx *ctx, int precision, const float *events, const uin
 int haru_sdtw_batch_span(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets, uint32_t nq,
                          float *out_cost, int64_t *out_col, int64_t *out_start, uintptr_t stream, uint32_t flags);
 
+/* ---- Raw signal: event detection on the device ---------------------------
+ * Section 4.1's pre-processing (Section 5.1: event detection, prefix
+ * trimming, normalisation) on the GPU: raw ADC samples in, events out, and
+ * the sDTW path run on them. The detector is the two-window t-test of the
+ * R9.4 tool chain Section 5.2 names (its parameters are not printed in the
+ * paper; the defaults below are this library's reading of them). At sample
+ * position i, the w samples before i and the w samples from i on give
+ *   t^2 = w (B - A)^2 / max(1, w (QA + QB) - A^2 - B^2)
+ * for their sums A, B and sums of squares QA, QB: the squared difference of
+ * the window means over (v1 + v2) / w with population variances; defined for
+ * w <= i <= n - w. Statistics are compared exactly (as rationals). A peak of
+ * a window is a position whose t exceeds the window's threshold, is strictly
+ * greater than the defined t of the w positions before it and at least that
+ * of the w positions after it. Events start at the long window's peaks and at
+ * the short window's peaks that have no long-window peak within window_short
+ * positions; event e spans samples [b_e, b_{e+1}) (b_0 = 0, the last b = n)
+ * and its value is its mean, (float)((double) sum / length). A read's query is
+ * events [trim_events, trim_events + max_events): the adaptor's events are
+ * dropped and the decision prefix kept. The event values are in ADC units;
+ * the sDTW path z-scores each query (HARU_RAW behaviour). */
+#define HARU_MAX_READ_SAMPLES 16384 /* samples of one read's signal, at most */
+
+typedef struct {
+  int window_short;          /* samples per window of the short t-test, 2..16 (default 3) */
+  int window_long;           /* of the long t-test, window_short..16 (default 6) */
+  int threshold_short_centi; /* t threshold of the short window in hundredths, 1..10000 (default 140) */
+  int threshold_long_centi;  /* of the long window (default 900) */
+  uint32_t trim_events;      /* leading events dropped: the read adaptor (default 50, Section 4.1) */
+  uint32_t max_events;       /* events kept after the trim: the query prefix, 1..HARU_MAX_QUERY (default 250) */
+} haru_event_params;
+
+/* Fill *p with the defaults. Returns HARU_OK, or HARU_EINVAL if p is NULL. */
+int haru_event_params_default(haru_event_params *p);
+
+/* Detect the events of nreads reads. samples[sample_offsets[r] ..
+ * sample_offsets[r+1]) are read r's int16 ADC samples (at most
+ * HARU_MAX_READ_SAMPLES each); sample_offsets has nreads + 1 entries,
+ * non-decreasing from 0. params may be NULL (defaults). Output: read r's
+ * query events in events[event_offsets[r] .. event_offsets[r+1]) (float, ADC
+ * units); event_offsets has nreads + 1 entries; events must hold nreads *
+ * max_events floats. A read with fewer than trim_events + 1 events gets an
+ * empty query. flags: HARU_ON_DEVICE (all four arrays are device pointers,
+ * ordered on `stream`), HARU_ASYNC (with HARU_ON_DEVICE). Errors: HARU_EINVAL
+ * (bad parameters, offsets or read length), HARU_ENOMEM, HARU_ECUDA. */
+int haru_detect_events(haru_ctx *ctx, const int16_t *samples, const uint32_t *sample_offsets, uint32_t nreads,
+                       const haru_event_params *params, float *events, uint32_t *event_offsets, uintptr_t stream,
+                       uint32_t flags);
+
+/* The whole path from raw signal to alignment: haru_detect_events, then
+ * haru_sdtw_batch on each read's query (z-scored on the device), in one
+ * stream-ordered sequence. Layout of samples/sample_offsets and params as in
+ * haru_detect_events; precision, out_cost, out_col, stream and flags
+ * (HARU_ON_DEVICE, HARU_ASYNC, HARU_PROFILE) as in haru_sdtw_batch.
+ * out_events (may be NULL): the query length used per read (uint32, nreads).
+ * Every read must give a query of 2 or more events with a nonzero spread,
+ * else the batch returns HARU_EINVAL. Errors: as haru_sdtw_batch. */
+int haru_sdtw_batch_signal(haru_ctx *ctx, int precision, const int16_t *samples, const uint32_t *sample_offsets,
+                           uint32_t nreads, const haru_event_params *params, float *out_cost, int64_t *out_col,
+                           uint32_t *out_events, uintptr_t stream, uint32_t flags);
+
 /* ---- Serving: continuous batching of Read Until decisions -----------------
  * A persistent request loop inside the context (a worker thread) takes the
  * event chunks of reads as a flow cell delivers them, keeps each admitted

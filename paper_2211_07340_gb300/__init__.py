@@ -38,6 +38,7 @@ HARU_INT16_QMAX = 2047
 HARU_INT16_CAP = 28673
 HARU_MAX_QUERY = 512
 HARU_NOALLOC_MAX_QUERIES = 1024
+HARU_MAX_READ_SAMPLES = 16384
 
 
 class HaruError(RuntimeError):
@@ -62,6 +63,12 @@ class haru_config(ctypes.Structure):
         ("stack_short", ctypes.c_int),
         ("serve_spin_us", ctypes.c_int),
     ]
+
+
+class haru_event_params(ctypes.Structure):
+    _fields_ = [("window_short", ctypes.c_int), ("window_long", ctypes.c_int),
+                ("threshold_short_centi", ctypes.c_int), ("threshold_long_centi", ctypes.c_int),
+                ("trim_events", ctypes.c_uint32), ("max_events", ctypes.c_uint32)]
 
 
 class haru_batch_stats(ctypes.Structure):
@@ -108,6 +115,13 @@ _SIGS = {
                                             ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_size_t, ctypes.c_uint32]),
     "haru_last_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "haru_event_params_default": (ctypes.c_int, [ctypes.POINTER(haru_event_params)]),
+    "haru_detect_events": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                          ctypes.POINTER(haru_event_params), ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_size_t, ctypes.c_uint32]),
+    "haru_sdtw_batch_signal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_uint32, ctypes.POINTER(haru_event_params), ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32]),
     "haru_last_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_batch_stats)]),
     "haru_stream_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int]),
@@ -291,6 +305,68 @@ class Context:
                  | (HARU_PROFILE if profile else 0))
         return check(self.sdtw_batch_raw(precision, events, offsets, nq, out_cost, out_col, stream, flags),
                      "haru_sdtw_batch")
+
+    # raw signal ------------------------------------------------------------
+    @staticmethod
+    def event_params(**kw) -> haru_event_params:
+        p = haru_event_params()
+        check(lib().haru_event_params_default(ctypes.byref(p)))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    def detect_events(self, samples, offsets, params: haru_event_params | None = None):
+        """Host int16 samples (CSR) in: (events float32 CSR, event offsets uint32)."""
+        p = params if params is not None else self.event_params()
+        samples = np.ascontiguousarray(samples, dtype=np.int16)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+        nr = offsets.shape[0] - 1
+        ev = np.empty(max(1, nr * p.max_events), dtype=np.float32)
+        eoff = np.zeros(nr + 1, dtype=np.uint32)
+        smp = samples if samples.shape[0] else np.zeros(1, np.int16)
+        check(int(lib().haru_detect_events(self._h, _ptr(smp), _ptr(offsets), nr, ctypes.byref(p), _ptr(ev),
+                                           _ptr(eoff), 0, 0)), "haru_detect_events")
+        return ev[:int(eoff[-1])].copy(), eoff
+
+    def detect_events_device(self, samples, offsets, events, event_offsets, params=None, stream: int = 0,
+                             asynchronous: bool = False):
+        """haru_detect_events on device tensors (torch), ordered on `stream`."""
+        p = params if params is not None else self.event_params()
+        nr = int(offsets.shape[0]) - 1
+        flags = HARU_ON_DEVICE | (HARU_ASYNC if asynchronous else 0)
+        return check(int(lib().haru_detect_events(self._h, _ptr(samples), _ptr(offsets), nr, ctypes.byref(p),
+                                                  _ptr(events), _ptr(event_offsets), int(stream), flags)),
+                     "haru_detect_events")
+
+    def sdtw_batch_signal(self, precision: int, samples, offsets, params: haru_event_params | None = None):
+        """Raw int16 samples (host CSR) to (cost float32[nr], col int64[nr], query events uint32[nr])."""
+        p = params if params is not None else self.event_params()
+        samples = np.ascontiguousarray(samples, dtype=np.int16)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint32)
+        nr = offsets.shape[0] - 1
+        cost = np.empty(max(nr, 1), dtype=np.float32)
+        col = np.empty(max(nr, 1), dtype=np.int64)
+        nev = np.zeros(max(nr, 1), dtype=np.uint32)
+        smp = samples if samples.shape[0] else np.zeros(1, np.int16)
+        check(self.sdtw_batch_signal_raw(precision, smp, offsets, nr, p, cost, col, nev, 0, 0),
+              "haru_sdtw_batch_signal")
+        return cost[:nr], col[:nr], nev[:nr]
+
+    def sdtw_batch_signal_raw(self, precision: int, samples, offsets, nreads: int, params, out_cost, out_col,
+                              out_events, stream: int = 0, flags: int = 0) -> int:
+        """Direct call of haru_sdtw_batch_signal; returns the status code."""
+        p = params if params is not None else self.event_params()
+        return int(lib().haru_sdtw_batch_signal(self._h, int(precision), _ptr(samples), _ptr(offsets), int(nreads),
+                                                ctypes.byref(p), _ptr(out_cost), _ptr(out_col), _ptr(out_events),
+                                                int(stream), int(flags)))
+
+    def sdtw_batch_signal_device(self, precision: int, samples, offsets, out_cost, out_col, out_events=None,
+                                 params=None, stream: int = 0, asynchronous: bool = False, profile: bool = False):
+        """haru_sdtw_batch_signal on device tensors (torch), ordered on `stream`."""
+        nr = int(offsets.shape[0]) - 1
+        flags = HARU_ON_DEVICE | (HARU_ASYNC if asynchronous else 0) | (HARU_PROFILE if profile else 0)
+        return check(self.sdtw_batch_signal_raw(precision, samples, offsets, nr, params, out_cost, out_col,
+                                                out_events, stream, flags), "haru_sdtw_batch_signal")
 
     def last_status(self) -> int:
         return int(lib().haru_last_status(self._h))

@@ -189,8 +189,10 @@ void haru_destroy(haru_ctx *ctx) {
     ctx->server = nullptr;
   }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void *ptrs[] = {ctx->ref_z,    ctx->img16,     ctx->img32,  ctx->stats, ctx->partials,
-                  ctx->d_events, ctx->d_offsets, ctx->d_cost, ctx->d_col, ctx->d_start};
+  void *ptrs[] = {ctx->ref_z,     ctx->img16,       ctx->img32,       ctx->stats,      ctx->partials,
+                  ctx->d_events,  ctx->d_offsets,   ctx->d_cost,      ctx->d_col,      ctx->d_start,
+                  ctx->d_samples, ctx->d_soff,      ctx->sig_strided, ctx->sig_events, ctx->sig_counts,
+                  ctx->sig_off};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   haru::ws_free(ctx->ws);

@@ -104,9 +104,10 @@ cudaError_t ws_reserve_upto(Workspace &ws, int precision, uint32_t max_nq, const
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
                        const LaunchCfg &lc, cudaStream_t s, cudaEvent_t ev_prep, cudaEvent_t ev_sweep,
-                       int64_t *d_start) {
+                       int64_t *d_start, bool zero_counters) {
   cudaError_t e;
-  if ((e = cudaMemsetAsync(ws.ints, 0, kIntWords * sizeof(int), s)) != cudaSuccess) return e;
+  // (a caller that ran kernels reporting into the status word first has zeroed the counters itself)
+  if (zero_counters && (e = cudaMemsetAsync(ws.ints, 0, kIntWords * sizeof(int), s)) != cudaSuccess) return e;
   if (ev_prep && (e = record_event(ev_prep, s)) != cudaSuccess) return e;
   PlanArgs pa;
   pa.offsets = d_offsets;

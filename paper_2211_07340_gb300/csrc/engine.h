@@ -97,7 +97,16 @@ void ws_free(Workspace &ws);
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
                        const LaunchCfg &lc, cudaStream_t s, cudaEvent_t ev_prep, cudaEvent_t ev_sweep,
-                       int64_t *d_start = nullptr);
+                       int64_t *d_start = nullptr, bool zero_counters = true);
+
+// Event detection (events.cu): parameter defaults and checks, and the
+// stream-ordered detection of nreads raw-signal reads: strided events and
+// per-read counts, then CSR offsets (nreads + 1) and CSR events.
+void event_params_default(haru_event_params *p);
+bool event_params_valid(const haru_event_params &p);
+cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uint32_t nreads,
+                           const haru_event_params &p, float *strided, uint32_t *counts, uint32_t *ev_off,
+                           float *ev_csr, int *status, cudaStream_t s);
 
 // Record `e` on `s`; inside a stream capture, as an external event node so
 // its time can be read after every replay.
@@ -136,6 +145,20 @@ struct haru_ctx {
   int64_t *d_col = nullptr;
   int64_t *d_start = nullptr;
   size_t cap_q = 0;
+
+  // raw-signal path (signal.cu): staged samples and offsets, detected events
+  int16_t *d_samples = nullptr;
+  size_t cap_samples = 0;
+  uint32_t *d_soff = nullptr;
+  size_t cap_soff = 0;
+  float *sig_strided = nullptr;
+  size_t cap_strided = 0;
+  float *sig_events = nullptr;
+  size_t cap_sig_events = 0;
+  uint32_t *sig_counts = nullptr;
+  size_t cap_sig_counts = 0;
+  uint32_t *sig_off = nullptr;
+  size_t cap_sig_off = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // HARU_PROFILE
   bool profiled = false;
 

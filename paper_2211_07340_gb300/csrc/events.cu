@@ -1,0 +1,314 @@
+// Event detection on the device: the pre-processing of HARU's software layer
+// (Section 4.1; Section 5.1 lists event detection, prefix trimming and
+// normalisation) turned into kernels, so that raw samples go in and the
+// existing z-score / quantise / sDTW path runs on their events.
+//
+// The detector is the two-window t-test of the Nanopolish/f5c tool chain
+// that Section 5.2 names (R9.4 defaults: windows 3 and 6 samples,
+// thresholds 1.40 and 9.00). At sample position i the w samples before i and
+// the w samples from i on give
+//   t^2 = w (B - A)^2 / max(1, w (QA + QB) - A^2 - B^2)
+// for their sums A, B and sums of squares QA, QB (the squared difference of
+// the window means over (v1 + v2) / w with population variances), defined
+// for w <= i <= n - w. Statistics are compared as exact rationals (128-bit
+// cross products), never rounded: a peak of a window is a position above the
+// window's threshold, strictly above the w statistics before it and at least
+// the w after it; boundaries are the long window's peaks and the short
+// window's peaks with no long-window peak within w_short. Event e spans
+// [b_e, b_{e+1}) (b_0 = 0, last b = n) and its value is the mean
+// (float)((double) sum / length). A read's query is events
+// [trim, trim + max_events).
+//
+// Kernels: detect_kernel (one CTA per read: the read's samples in shared
+// memory, statistics over tiles of kEvTile positions with halos, peaks, an
+// ordered block-wide compaction of boundaries that stops once the query's
+// boundaries are known, then the event means), scan_kernel (CSR offsets of
+// the per-read event counts) and compact_kernel (strided -> CSR).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "engine.h"
+
+namespace haru {
+namespace {
+
+constexpr int kEvThreads = 256;
+constexpr int kEvTile = 1024;                      // boundary positions per tile
+constexpr int kEvPer = kEvTile / kEvThreads;       // consecutive positions per thread
+constexpr int kEvMaxW = 16;                        // longest window
+constexpr int kEvTpos = kEvTile + 4 * kEvMaxW;     // statistics per tile (halo w1 + w2 on each side)
+constexpr int kEvLp = kEvTile + 2 * kEvMaxW;       // long-peak flags per tile (halo w1 on each side)
+static_assert(kEvTile % kEvThreads == 0 && kEvPer <= 32, "tile split");
+
+// Shared-memory layout of detect_kernel (bytes).
+constexpr size_t kSmX = 0;                                            // int16 samples
+constexpr size_t kSmStats = kSmX + HARU_MAX_READ_SAMPLES * sizeof(int16_t);  // 4 x kEvTpos uint64
+constexpr size_t kSmLp = kSmStats + 4 * kEvTpos * sizeof(unsigned long long);
+constexpr size_t kSmBounds = kSmLp + (kEvLp + 15) / 16 * 16;          // int bounds
+// boundaries are at least w_short + 1 >= 3 samples apart: at most n / 3 + 1
+constexpr size_t kSmBytes = kSmBounds + (HARU_MAX_READ_SAMPLES / 3 + 2) * sizeof(int);
+
+struct EvArgs {
+  const int16_t *samples;
+  const uint32_t *offsets;  // nreads + 1
+  uint32_t nreads;
+  int w1, w2;
+  unsigned long long tau1sq, tau2sq;  // (100 tau)^2
+  int trim, maxev;
+  float *out;        // [nreads][maxev]
+  uint32_t *counts;  // nreads
+  int *status;
+};
+
+// a * b as 128 bits (hi, lo): every product of a statistic's numerator
+// (< 2^45) or denominator (< 2^40) with another, or with a squared threshold.
+__device__ __forceinline__ bool mul_gt(unsigned long long a, unsigned long long b, unsigned long long c,
+                                       unsigned long long d) {  // a * b > c * d
+  const unsigned long long h1 = __umul64hi(a, b), h2 = __umul64hi(c, d);
+  return h1 > h2 || (h1 == h2 && a * b > c * d);
+}
+
+// Statistic of window w at position i (num, den; 0, 0 where undefined).
+__device__ __forceinline__ void tstat(const int16_t *x, int n, int w, int i, unsigned long long *num,
+                                      unsigned long long *den) {
+  if (i < w || i > n - w) {
+    *num = 0;
+    *den = 0;
+    return;
+  }
+  long long A = 0, B = 0, QA = 0, QB = 0;
+  for (int k = i - w; k < i; ++k) {
+    const long long v = x[k];
+    A += v;
+    QA += v * v;
+  }
+  for (int k = i; k < i + w; ++k) {
+    const long long v = x[k];
+    B += v;
+    QB += v * v;
+  }
+  const long long d = B - A;
+  long long D = static_cast<long long>(w) * (QA + QB) - A * A - B * B;
+  if (D < 1) D = 1;
+  *num = static_cast<unsigned long long>(static_cast<long long>(w) * d * d);
+  *den = static_cast<unsigned long long>(D);
+}
+
+// Peak test of statistic index j (num/den arrays of the tile): above the
+// threshold, strictly above the w defined statistics before it, at least the
+// w after it. The caller keeps j - w >= 0 and j + w < kEvTpos.
+__device__ __forceinline__ bool peak(const unsigned long long *num, const unsigned long long *den, int j, int w,
+                                     unsigned long long tausq) {
+  const unsigned long long nj = num[j], dj = den[j];
+  if (dj == 0 || !mul_gt(nj, 10000ull, dj, tausq)) return false;
+  for (int k = 1; k <= w; ++k) {
+    const unsigned long long dl = den[j - k];
+    if (dl != 0 && !mul_gt(nj, dl, num[j - k], dj)) return false;  // need t_j > t_{j-k}
+    const unsigned long long dr = den[j + k];
+    if (dr != 0 && mul_gt(num[j + k], dj, nj, dr)) return false;   // need t_{j+k} <= t_j
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kEvThreads) detect_kernel(EvArgs a) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  int16_t *x = reinterpret_cast<int16_t *>(sm + kSmX);
+  unsigned long long *n1 = reinterpret_cast<unsigned long long *>(sm + kSmStats);
+  unsigned long long *d1 = n1 + kEvTpos, *n2 = d1 + kEvTpos, *d2 = n2 + kEvTpos;
+  unsigned char *lp = sm + kSmLp;
+  int *bounds = reinterpret_cast<int *>(sm + kSmBounds);
+  __shared__ int warp_tot[kEvThreads / 32];
+  __shared__ int s_nb;
+  const uint32_t r = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t base = a.offsets[r];
+  const long len = static_cast<long>(a.offsets[r + 1]) - static_cast<long>(base);
+  if (len < 0 || len > HARU_MAX_READ_SAMPLES) {
+    if (tid == 0) {
+      report(a.status, HARU_EINVAL);
+      a.counts[r] = 0;
+    }
+    return;
+  }
+  const int n = static_cast<int>(len);
+  for (int i = tid; i < n; i += kEvThreads) x[i] = a.samples[base + i];
+  if (tid == 0) s_nb = 0;
+  __syncthreads();
+  const int w1 = a.w1, w2 = a.w2, H = w1 + w2;
+  const int need = a.trim + a.maxev;  // boundaries b_1 .. b_need close the query's last event
+  for (int p0 = 0; p0 < n; p0 += kEvTile) {
+    // statistics at positions q = p0 - H + j, j in [0, kEvTile + 2H)
+    for (int j = tid; j < kEvTile + 2 * H; j += kEvThreads) {
+      const int q = p0 - H + j;
+      if (q < 0 || q > n) {
+        n1[j] = d1[j] = n2[j] = d2[j] = 0;
+      } else {
+        tstat(x, n, w1, q, &n1[j], &d1[j]);
+        tstat(x, n, w2, q, &n2[j], &d2[j]);
+      }
+    }
+    __syncthreads();
+    // long-window peaks at q = p0 - w1 + j, j in [0, kEvTile + 2 w1)
+    for (int j = tid; j < kEvTile + 2 * w1; j += kEvThreads) lp[j] = peak(n2, d2, j + w2, w2, a.tau2sq) ? 1 : 0;
+    __syncthreads();
+    // boundaries among this thread's positions p0 + tid * kEvPer + u
+    unsigned flags = 0;
+    int cnt = 0;
+#pragma unroll
+    for (int u = 0; u < kEvPer; ++u) {
+      const int p = p0 + tid * kEvPer + u;
+      if (p < 1 || p > n - 1) continue;
+      const int jl = p - p0 + w1;  // its long-peak flag
+      bool b = lp[jl] != 0;
+      if (!b && peak(n1, d1, p - p0 + H, w1, a.tau1sq)) {
+        bool near = false;
+        for (int k = -w1; k <= w1; ++k) near = near || lp[jl + k] != 0;
+        b = !near;
+      }
+      if (b) {
+        flags |= 1u << u;
+        ++cnt;
+      }
+    }
+    // ordered compaction: exclusive prefix of cnt over the block
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kEvThreads / 32; ++w) {
+      const int t = warp_tot[w];
+      before += w < warp ? t : 0;
+      total += t;
+    }
+    int pos = s_nb + before + incl - cnt;
+#pragma unroll
+    for (int u = 0; u < kEvPer; ++u)
+      if (flags & (1u << u)) bounds[pos++] = p0 + tid * kEvPer + u;
+    __syncthreads();
+    if (tid == 0) s_nb += total;
+    __syncthreads();
+    if (s_nb >= need) break;  // uniform: every thread reads the same s_nb
+  }
+  const int nb = s_nb;
+  int K = n > 0 ? nb + 1 - a.trim : 0;  // events after the trim (an empty read has none)
+  K = K < 0 ? 0 : (K > a.maxev ? a.maxev : K);
+  for (int k = tid; k < K; k += kEvThreads) {
+    const int e = a.trim + k;
+    const int lo = e == 0 ? 0 : bounds[e - 1];
+    const int hi = e + 1 <= nb ? bounds[e] : n;
+    long long s = 0;
+    for (int i = lo; i < hi; ++i) s += x[i];
+    a.out[static_cast<size_t>(r) * a.maxev + k] =
+        __double2float_rn(__ddiv_rn(static_cast<double>(s), static_cast<double>(hi - lo)));
+  }
+  if (tid == 0) a.counts[r] = static_cast<uint32_t>(K);
+}
+
+// CSR offsets of the per-read event counts (one CTA).
+__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t *counts, uint32_t nreads, uint32_t *offsets) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    carry = 0;
+    offsets[0] = 0;
+  }
+  __syncthreads();
+  for (uint32_t b = 0; b < nreads; b += 1024) {
+    const uint32_t r = b + tid;
+    const uint32_t c = r < nreads ? counts[r] : 0u;
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < 32; ++w) {
+      before += w < warp ? warp_tot[w] : 0u;
+      total += warp_tot[w];
+    }
+    if (r < nreads) offsets[r + 1] = carry + before + incl;
+    __syncthreads();
+    if (tid == 0) carry += total;
+    __syncthreads();
+  }
+}
+
+// Strided per-read events -> CSR (one warp per read).
+__global__ void compact_kernel(const float *strided, int maxev, const uint32_t *counts, const uint32_t *offsets,
+                               uint32_t nreads, float *csr) {
+  const uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= nreads) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = counts[r], o = offsets[r];
+  for (uint32_t i = lane; i < c; i += 32) csr[o + i] = strided[static_cast<size_t>(r) * maxev + i];
+}
+
+}  // namespace
+
+// Fill defaults (R9.4 readings).
+void event_params_default(haru_event_params *p) {
+  std::memset(p, 0, sizeof(*p));
+  p->window_short = 3;
+  p->window_long = 6;
+  p->threshold_short_centi = 140;
+  p->threshold_long_centi = 900;
+  p->trim_events = 50;
+  p->max_events = 250;
+}
+
+bool event_params_valid(const haru_event_params &p) {
+  return p.window_short >= 2 && p.window_long >= p.window_short && p.window_long <= kEvMaxW &&
+         p.threshold_short_centi >= 1 && p.threshold_short_centi <= 10000 && p.threshold_long_centi >= 1 &&
+         p.threshold_long_centi <= 10000 && p.trim_events <= HARU_MAX_READ_SAMPLES && p.max_events >= 1 &&
+         p.max_events <= HARU_MAX_QUERY;
+}
+
+// Enqueue detection of nreads reads on s: strided events and counts, then
+// CSR offsets and events (ev_csr holds up to nreads * max_events floats).
+cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uint32_t nreads,
+                           const haru_event_params &p, float *strided, uint32_t *counts, uint32_t *ev_off,
+                           float *ev_csr, int *status, cudaStream_t s) {
+  if (nreads == 0) return cudaSuccess;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmBytes));
+  });
+  if (attr != cudaSuccess) return attr;
+  EvArgs a;
+  a.samples = d_samples;
+  a.offsets = d_soff;
+  a.nreads = nreads;
+  a.w1 = p.window_short;
+  a.w2 = p.window_long;
+  a.tau1sq = static_cast<unsigned long long>(p.threshold_short_centi) * p.threshold_short_centi;
+  a.tau2sq = static_cast<unsigned long long>(p.threshold_long_centi) * p.threshold_long_centi;
+  a.trim = static_cast<int>(p.trim_events);
+  a.maxev = static_cast<int>(p.max_events);
+  a.out = strided;
+  a.counts = counts;
+  a.status = status;
+  detect_kernel<<<nreads, kEvThreads, kSmBytes, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  scan_kernel<<<1, 1024, 0, s>>>(counts, nreads, ev_off);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  compact_kernel<<<(nreads + 7) / 8, 256, 0, s>>>(strided, a.maxev, counts, ev_off, nreads, ev_csr);
+  return cudaGetLastError();
+}
+
+}  // namespace haru
