@@ -339,7 +339,8 @@ def run_serving(haru, args, local, w, threshold, channels):
             "max_concurrent_batches": st["max_concurrent"], "late_chunks": late, "clocks": clk.summary(),
             "stages": {"max_upload_ms": st["max_upload_ns"] / 1e6, "max_queue_ms": st["max_queue_ns"] / 1e6,
                        "max_gpu_ms": st["max_gpu_ns"] / 1e6, "max_gpu_exec_ms": st["max_gpu_exec_ns"] / 1e6,
-                       "max_notice_ms": st["max_notice_ns"] / 1e6, "over_10ms_upload": st["slow_upload"],
+                       "max_notice_ms": st["max_notice_ns"] / 1e6, "max_drain_ms": st["max_drain_ns"] / 1e6,
+                       "over_10ms_upload": st["slow_upload"],
                        "over_10ms_queue": st["slow_queue"], "over_10ms_gpu": st["slow_gpu"],
                        "max_upload_sync_ms": st["max_upload_sync_ns"] / 1e6,
                        "max_worker_turn_gap_ms": st["max_turn_gap_ns"] / 1e6,

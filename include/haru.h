@@ -302,6 +302,9 @@ typedef struct {
    * of a read's GPU stage (queueing on the device and the worker noticing
    * completion) */
   uint64_t max_gpu_exec_ns, max_notice_ns;
+  /* the longest time the worker spent taking submitted chunks into its reads
+   * (part of the upload stage) */
+  uint64_t max_drain_ns;
 } haru_stream_stats;
 int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
 

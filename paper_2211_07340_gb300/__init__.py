@@ -92,7 +92,7 @@ class haru_stream_stats(ctypes.Structure):
                                                "worst_turn_launch_ns", "worst_turn_wait_ns",
                                                "worst_turn_voluntary_switches",
                                                "worst_turn_involuntary_switches", "max_gpu_exec_ns",
-                                               "max_notice_ns")]
+                                               "max_notice_ns", "max_drain_ns")]
 
 
 _lib = None

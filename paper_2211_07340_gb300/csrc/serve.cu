@@ -158,6 +158,18 @@ class Server {
   // submit pushes chunks here without a lock (newest first); the worker
   // takes the whole list each turn, so neither side ever waits for the other
   std::atomic<Chunk *> intake_{nullptr};
+  // chunks the worker has consumed, handed back to the submitting side to be
+  // freed there: the worker never frees memory the submitter allocated (a
+  // free into another thread's malloc arena takes that arena's lock, and a
+  // submitter descheduled inside malloc then stalls the worker)
+  std::atomic<Chunk *> garbage_{nullptr};
+  static void free_list(Chunk *c) {
+    while (c) {
+      Chunk *nx = c->next;
+      std::free(c);
+      c = nx;
+    }
+  }
   std::atomic<size_t> intake_events_{0};
   std::unordered_map<uint64_t, Read> reads_;
   std::deque<uint64_t> admit_q_;        // reads waiting for a slot
@@ -197,6 +209,7 @@ class Server {
   // device execution of the slowest batch, and the longest host-side share of
   // a batch's GPU stage (launch -> completion seen, minus device execution)
   std::atomic<uint64_t> max_exec_{0}, max_notice_{0};
+  std::atomic<uint64_t> max_drain_{0};  // longest intake drain (part of the upload stage)
   uint64_t spin_ns_ = 0;  // keep polling this long after the last piece of work
   std::atomic<uint64_t> worst_[6] = {{0}, {0}, {0}, {0}, {0}, {0}};  // parts of the slowest turn
   void note_stage(int k, uint64_t dt) {
@@ -267,11 +280,8 @@ void Server::stop() {
     cv_work_.notify_all();
     if (thread_.joinable()) thread_.join();
   }
-  for (Chunk *c = intake_.exchange(nullptr); c;) {  // chunks never taken
-    Chunk *nx = c->next;
-    std::free(c);
-    c = nx;
-  }
+  free_list(intake_.exchange(nullptr));  // chunks never taken
+  free_list(garbage_.exchange(nullptr));
   cudaSetDevice(ctx_->device);
   for (auto &b : batches_) {
     if (b.stream) cudaStreamSynchronize(b.stream);
@@ -313,6 +323,7 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
     if (error_ != HARU_OK) return error_;
   }
   if (n > 0 && !ev) return HARU_EINVAL;
+  free_list(garbage_.exchange(nullptr, std::memory_order_acquire));
   if (intake_events_.load() + host_events_.load() + n > stage_cap_ * 4) return HARU_EBUSY;
   Chunk *c = static_cast<Chunk *>(std::malloc(offsetof(Chunk, ev) + sizeof(float) * std::max<uint32_t>(n, 1)));
   if (!c) return HARU_ENOMEM;
@@ -332,25 +343,33 @@ int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t
   return HARU_OK;
 }
 
-// Worker: take every chunk submitted so far, in submission order.
+// Worker: take every chunk submitted so far, in submission order, then hand
+// the chunks back to the submitting side for freeing.
 void Server::drain_intake() {
+  const uint64_t t0 = now_ns();
   Chunk *list = intake_.exchange(nullptr, std::memory_order_acquire);
   if (!list) return;
-  Chunk *ord = nullptr;
+  Chunk *ord = nullptr, *last = list;
   while (list) {
     Chunk *nx = list->next;
     list->next = ord;
     ord = list;
     list = nx;
   }
-  std::lock_guard<std::mutex> lk(mu_);
-  while (ord) {
-    Chunk *nx = ord->next;
-    take_chunk(ord);
-    intake_events_ -= ord->n;
-    std::free(ord);
-    ord = nx;
+  {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (Chunk *c = ord; c; c = c->next) {
+      take_chunk(c);
+      intake_events_ -= c->n;
+    }
   }
+  // ord .. last is one list: push it onto the garbage list as a whole
+  Chunk *head = garbage_.load(std::memory_order_relaxed);
+  do {
+    last->next = head;
+  } while (!garbage_.compare_exchange_weak(head, ord, std::memory_order_release, std::memory_order_relaxed));
+  const uint64_t dt = now_ns() - t0;
+  if (dt > max_drain_) max_drain_ = dt;
 }
 
 // Worker, under mu_: append a chunk's events to its read (up to the prefix).
@@ -442,6 +461,7 @@ void Server::stats(haru_stream_stats *out) {
   out->max_turn_gap_ns = max_gap_;
   out->max_gpu_exec_ns = max_exec_;
   out->max_notice_ns = max_notice_;
+  out->max_drain_ns = max_drain_;
   out->worst_turn_complete_ns = worst_[0];
   out->worst_turn_upload_ns = worst_[1];
   out->worst_turn_launch_ns = worst_[2];
