@@ -106,18 +106,21 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_ms: int = 100):
         self.index = index
+        self.period_ms = period_ms  # 0: no sampling
         self.proc = None
         self.path = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
+        if self.period_ms <= 0:
+            return self
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -134,7 +137,10 @@ class ClockSampler:
 
     def summary(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            if os.path.exists(self.path):
+                os.unlink(self.path)
+            return {"sm_mhz": None, "sm_max_mhz": None,
+                    "reasons": ["not sampled" if self.period_ms <= 0 else "nvidia-smi unavailable"]}
         rows = []
         with open(self.path) as f:
             for line in f:
@@ -305,7 +311,7 @@ def run_serving(haru, args, local, w, threshold, channels):
     gc.collect()
     gc.disable()
     try:
-        with ClockSampler(local) as clk:
+        with ClockSampler(local, args.serve_clock_ms) as clk:
             late = synth.replay(chunks, lambda c, t: ctx.stream_submit(c.read_id, c.channel, c.events, t, c.last))
     finally:
         gc.enable()
@@ -340,6 +346,8 @@ def run_serving(haru, args, local, w, threshold, channels):
             "stages": {"max_upload_ms": st["max_upload_ns"] / 1e6, "max_queue_ms": st["max_queue_ns"] / 1e6,
                        "max_gpu_ms": st["max_gpu_ns"] / 1e6, "max_gpu_exec_ms": st["max_gpu_exec_ns"] / 1e6,
                        "max_notice_ms": st["max_notice_ns"] / 1e6, "max_drain_ms": st["max_drain_ns"] / 1e6,
+                       "max_cuda_calls_ms": {k: st["max_" + k + "_ns"] / 1e6 for k in
+                                             ("upload_calls", "launch_inputs", "launch_path", "launch_results")},
                        "over_10ms_upload": st["slow_upload"],
                        "over_10ms_queue": st["slow_queue"], "over_10ms_gpu": st["slow_gpu"],
                        "max_upload_sync_ms": st["max_upload_sync_ns"] / 1e6,
@@ -414,6 +422,8 @@ def main():
                     help="measured seconds of the simulated flow-cell run, after the warm-up (0 = skip)")
     ap.add_argument("--serve-warm", type=float, default=5.0, help="seconds of serving before the measured span")
     ap.add_argument("--serve-channels", type=int, default=512)
+    ap.add_argument("--serve-clock-ms", type=int, default=100,
+                    help="nvidia-smi sampling period during the serving runs (0 = none)")
     ap.add_argument("--stress-channels", type=int, default=4096,
                     help="second serving run at this many channels, same length (0 = skip)")
     ap.add_argument("--ref-sweep", action="store_true",

@@ -72,7 +72,8 @@ extern "C" {
 typedef struct haru_ctx haru_ctx;
 
 typedef struct {
-  int warps_per_cta;        /* warps (queries or query pairs) sharing one reference tile stream; 0 = auto */
+  int warps_per_cta;        /* warps (queries or query pairs) sharing one reference tile stream: 2, 4, 8
+                               or 12 (start-column batches run at most 8); other values = 8 */
   int tile_cols;            /* reference columns per shared-memory tile, 2048..16384; 0 = auto */
   int ctas_per_sm;          /* persistent CTAs per SM; 0 = as many as fit */
   uint32_t wait_limit;      /* longest single device wait, microseconds, before HARU_ETIMEDOUT; 0 = 2 s */
@@ -305,6 +306,11 @@ typedef struct {
   /* the longest time the worker spent taking submitted chunks into its reads
    * (part of the upload stage) */
   uint64_t max_drain_ns;
+  /* the longest time spent inside one group of CUDA calls of the worker: the
+   * upload (staged copy, scatter launch, event), and a batch launch's input
+   * copies and gather, its device path (planner to fix-up) and its result
+   * copies and completion event */
+  uint64_t max_upload_calls_ns, max_launch_inputs_ns, max_launch_path_ns, max_launch_results_ns;
 } haru_stream_stats;
 int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
 
@@ -367,7 +373,7 @@ int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, c
 
 /* Autotuner: run the batch path on this batch (layout and flags as in
  * haru_sdtw_batch; HARU_ON_DEVICE and HARU_RAW are honoured) under every
- * combination of warps per CTA {4, 8}, tile width {2048, 4096, 8192, 16384}
+ * combination of warps per CTA {4, 8, 12}, tile width {2048, 4096, 8192, 16384}
  * and work-unit target {1 (no reference segments), auto / 2, auto,
  * 2 x auto}, keep the fastest (minimum of two timed runs each) in the context's configuration
  * for later batches, and copy the resulting configuration to *chosen (may be

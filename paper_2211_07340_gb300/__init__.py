@@ -92,7 +92,9 @@ class haru_stream_stats(ctypes.Structure):
                                                "worst_turn_launch_ns", "worst_turn_wait_ns",
                                                "worst_turn_voluntary_switches",
                                                "worst_turn_involuntary_switches", "max_gpu_exec_ns",
-                                               "max_notice_ns", "max_drain_ns")]
+                                               "max_notice_ns", "max_drain_ns", "max_upload_calls_ns",
+                                               "max_launch_inputs_ns", "max_launch_path_ns",
+                                               "max_launch_results_ns")]
 
 
 _lib = None

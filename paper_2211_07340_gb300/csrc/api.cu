@@ -33,7 +33,7 @@ int cuda_fail(haru_ctx *c, cudaError_t e) {
 
 int pick_warps(const haru_config &cfg) {
   int w = cfg.warps_per_cta;
-  if (w != 2 && w != 4 && w != 8) w = 8;
+  if (w != 2 && w != 4 && w != 8 && w != 12) w = 8;
   return w;
 }
 

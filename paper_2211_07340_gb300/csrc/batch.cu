@@ -38,7 +38,7 @@ WsNeeds ws_needs(int precision, uint32_t nq, const LaunchCfg &lc) {
   w.max_items = items_bound(mode, nq);
   // Work units: enough (query x reference segment) units to keep every SM
   // busy to the end; nseg_cap bounds the segments per item for storage.
-  w.units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * lc.warps;
+  w.units_target = lc.units_target > 0 ? lc.units_target : 4 * lc.sms * kernel_warps(precision, lc);
   // Fewest items the batch can make (stacked: four int16 or two other
   // queries per item); the segment cap is sized for that case.
   const size_t items_min = (mode == 0 || mode == 3) ? (static_cast<size_t>(nq) + 1) / 2
@@ -114,7 +114,8 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   pa.nq = nq;
   pa.N = ref.N;
   pa.pair = plan_mode(precision);
-  pa.warps = lc.warps;
+  const int warps = kernel_warps(precision, lc);
+  pa.warps = warps;
   pa.units_target = ws.units_target;
   // Auto stacking: when the batch alone fills the unit target, or when its
   // stacked items (up to four queries each) cut into reference segments
@@ -162,14 +163,14 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   sa.out_col = d_col;
   sa.inv_scale = 1.0f / static_cast<float>(1 << ref.scale_log2);
   sa.tile_cols = lc.tile;
-  sa.warps = lc.warps;
+  sa.warps = warps;
   sa.wait_ns = lc.wait_ns;
-  const size_t groups_max = ((ws.max_items + lc.warps - 1) / lc.warps + kMaxS) * static_cast<size_t>(ws.nseg_cap);
+  const size_t groups_max = ((ws.max_items + warps - 1) / warps + kMaxS) * static_cast<size_t>(ws.nseg_cap);
   if (ev_sweep && (e = record_event(ev_sweep, s)) != cudaSuccess) return e;
   // One persistent sweep kernel over the whole group list (tallest strips
   // first), then the fix-up kernel, which verifies segments and writes every
   // query's result.
-  int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, lc.tile, lc.warps);
+  int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, lc.tile, warps);
   if (per_sm < 1) per_sm = 1;
   const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
   return launch_sdtw(precision, sa, grid, static_cast<int>(ws.max_items), s);

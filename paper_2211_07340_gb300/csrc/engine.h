@@ -41,6 +41,13 @@ struct LaunchCfg {
   unsigned long long wait_ns = 2000000000ull;
 };
 
+// Warps per CTA that the kernels of `precision` run: the start-column forms
+// hold ~240 registers a thread and launch at most 8 warps; the others fit
+// 12 warps (3 per scheduler) in an SM's register file.
+inline int kernel_warps(int precision, const LaunchCfg &lc) {
+  return prec_span(precision) && lc.warps > 8 ? 8 : lc.warps;
+}
+
 // Planner mode of a batch: 0 FP32, 1 int16 pairs, 3 int16 inputs with wide
 // accumulation (one exact strip per query).
 inline int plan_mode(int precision) {

@@ -180,8 +180,9 @@ constexpr uint32_t kCap2 = (static_cast<uint32_t>(kCap) << 16) | static_cast<uin
 
 // Sparse saturation. Costs are held as unsigned 16-bit halves and only rows
 // k = S-1, S-1-kCapRun, ... of each lane take min(CAP, .); the rows between
-// add without a cap (__vadd2 on the full-rate pipe instead of a DPX
-// instruction on the half-rate one). Every cell lies between min(CAP, exact)
+// add without a cap: a plain 32-bit add of the two packed words, which is the
+// per-half add exactly because no half's sum reaches 2^16 (see below), and
+// keeps those rows off the DPX min/max pipe. Every cell lies between min(CAP, exact)
 // and the exact cost, and a min3 is at most its `up` input, so the j-th
 // uncapped row after a capped one holds at most CAP + j * 4094. Runs are at
 // most kCapRun - 1 = 8 rows (also across lanes: row S-1 is capped), so every
@@ -202,19 +203,22 @@ struct StripI16 {
       NQ[k] = img[(S + k) * 32 + lane];
     }
   }
-  // Initial value of row k of this lane: CAP (infinity) for a real row, 0 for a pad row.
-  __device__ __forceinline__ uint32_t init(int k) const { return ~__vcmpeq2(Q[k], kPadQ2) & kCap2; }
-  // As if the reference began at the current step: every row at its initial
-  // value; the masked chunks hold rows that have not reached their first
-  // column at that value.
-  __device__ __forceinline__ void fresh(long, int) {
+  // As if the reference began at the current step: every row, pad rows
+  // included, holds CAP (infinity), and the row above a stack's top row held
+  // the free-start 0 one step back (gprev). The top row then turns 0 at
+  // step 0 (min(up, 0, CAP) + 0; a pad row's distance is 0), each pad row
+  // below turns 0 exactly at its own first column, and a real row stays at
+  // or above CAP until its first column: infinity under min(CAP, .). No
+  // cell is masked; every value is the plain DP's modulo min(CAP, .), which
+  // is all the tracked (capped) last row and the segment check look at.
+  __device__ __forceinline__ void fresh(long, int, uint32_t ng) {
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-      G[0][k] = init(k);
-      G[1][k] = G[0][k];
+      G[0][k] = kCap2;
+      G[1][k] = kCap2;
       Rr[k] = 0u;
     }
-    gprev = 0u;
+    gprev = ng ? kCap2 : 0u;
   }
   // Exact state before step t: G[1] = step t-1, G[0] = step t-2, and the
   // reference samples the cells used at step t-1 (from the global image).
@@ -236,8 +240,7 @@ struct StripI16 {
     }
   }
 
-  template <bool MASK>
-  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int lane, uint32_t *ring, int e0, uint32_t ng,
                                         uint32_t nr, bool tracked, int, int) {
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
@@ -264,12 +267,14 @@ struct StripI16 {
         const uint32_t up = k ? G[a][k - 1] : gup;
         const uint32_t dg = k ? G[b][k - 1] : gprev;
         const uint32_t m = __vimin3_u16x2(up, dg, G[a][k]);
-        uint32_t v = (S - 1 - k) % kCapRun == 0 ? __viaddmin_u16x2(d, m, kCap2) : __vadd2(m, d);
-        if (MASK) v = (trel + u - lane * S >= k) ? v : init(k);
-        G[b][k] = v;
+        // rows between caps: one 32-bit add, exact per half (no carry leaves a half: every sum is below 2^16)
+        G[b][k] = (S - 1 - k) % kCapRun == 0 ? __viaddmin_u16x2(d, m, kCap2) : m + d;
       }
       gprev = gup;
-      if (tracked) ring[e0 + u] = G[b][S - 1];
+      // The last row's values of steps u - 1 and u sit in G[0] and G[1]: one
+      // 8-byte store every two steps (U is even, the ring 16-byte aligned).
+      if ((u & 1) && tracked)
+        *reinterpret_cast<uint2 *>(ring + e0 + u - 1) = make_uint2(G[0][S - 1], G[1][S - 1]);
     }
   }
 };
@@ -320,7 +325,7 @@ struct StripF32 {
       W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
     }
   }
-  __device__ __forceinline__ void fresh(long, int) {
+  __device__ __forceinline__ void fresh(long, int, uint32_t) {
     const float kBig = 1.0e30f;  // stands for +inf; sums of these stay finite
 #pragma unroll
     for (int k = 0; k < S; ++k) {
@@ -348,10 +353,8 @@ struct StripF32 {
     }
   }
 
-  template <bool MASK>
-  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int lane, uint32_t *ring, int e0, uint32_t ng,
                                         uint32_t nr, bool tracked, int, int) {
-    (void)trel;
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
     RingStore<U> out;
@@ -438,7 +441,7 @@ struct StripF32Span {
   }
   // Before step t_start: row i = lane * S + k held its column t_start - 1 - i
   // (and t_start - 2 - i one step earlier) as the start of a pad row's path.
-  __device__ __forceinline__ void fresh(long t_start, int lane) {
+  __device__ __forceinline__ void fresh(long t_start, int lane, uint32_t) {
     const float kBig = 1.0e30f;
 #pragma unroll
     for (int k = 0; k < S; ++k) {
@@ -480,10 +483,8 @@ struct StripF32Span {
   // t0: the absolute step of the chunk's first step; top: the first row of
   // this lane's stack (0, or 16 * S in the lower stack). The ring's start
   // columns sit 128 words after the costs.
-  template <bool MASK>
-  __device__ __forceinline__ void chunk(const uint32_t *ref, int trel, int lane, uint32_t *ring, int e0, uint32_t ng,
+  __device__ __forceinline__ void chunk(const uint32_t *ref, int lane, uint32_t *ring, int e0, uint32_t ng,
                                         uint32_t nr, bool tracked, int t0, int top) {
-    (void)trel;
     constexpr int U = Geo<S>::U;
     RefWindow<U> win;
 #pragma unroll
@@ -566,31 +567,26 @@ template <int S>
 struct FormOf<kFormI16, S> {
   using Strip = StripI16<S>;
   using Track = TrackI16;
-  static constexpr bool kMasked = true;
 };
 template <int S>
 struct FormOf<kFormF32, S> {
   using Strip = StripF32<S, false>;
   using Track = TrackF32;
-  static constexpr bool kMasked = false;
 };
 template <int S>
 struct FormOf<kFormExactWide, S> {
   using Strip = StripF32<S, true>;
   using Track = TrackF32;
-  static constexpr bool kMasked = false;
 };
 template <int S>
 struct FormOf<kFormF32Span, S> {
   using Strip = StripF32Span<S, false>;
   using Track = TrackF32Span;
-  static constexpr bool kMasked = false;
 };
 template <int S>
 struct FormOf<kFormWideSpan, S> {
   using Strip = StripF32Span<S, true>;
   using Track = TrackF32Span;
-  static constexpr bool kMasked = false;
 };
 
 // ----------------------------------------------------------- tile sources --
@@ -673,7 +669,7 @@ struct GlobalTiles {
 // ------------------------------------------------------------ one unit --
 // Runs steps [t_start, t_end) of one strip (a query or a pair) and tracks
 // the last row over own steps [t_own, t_end). fresh: the strip starts from
-// the fresh state at t_start (masked prologue for the int16 form).
+// the fresh state at t_start.
 // save_start / save_final: where to store the state before step t_own and
 // before step t_end (nullptr: not stored). stk: a stacked item (lanes 0..15
 // and 16..31 are two strips; each lane tracks its own stack's last row).
@@ -686,7 +682,6 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
                           int TS, long t_start, long t_own, long t_end, bool fresh, long N, uint32_t *save_start,
                           uint32_t *save_final, uint32_t *ring, int lane, bool stk) {
   constexpr int U = Geo<S>::U, F = Geo<S>::F;
-  constexpr bool kMasked = FormOf<FORM, S>::kMasked;
   // ng: 0 on a lane that starts a stack from the free-start row; nr: 0 on
   // lane 0, which injects the reference (it flows on through every lane)
   const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u, nr = lane != 0 ? 1u : 0u;
@@ -695,7 +690,6 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
   const int top = stk && lane >= 16 ? 16 * S : 0;  // first row of this lane's stack
   const long last_row = (stk && lane < 16 ? 16L : 32L) * S - 1;
   const int nscan = stk ? 2 : 1;
-  const long mask_end = fresh ? t_start + 32L * S : t_start;
   const long k_first = t_start / TS;
   const int K = static_cast<int>((t_end + TS - 1) / TS - k_first);
   int fl = 0, buf = 0;
@@ -710,20 +704,14 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
     const long hi = tk0 + TS < t_end ? tk0 + TS : t_end;
     const int n = static_cast<int>(hi - lo);
     const int own_at = (save_start && t_own >= lo && t_own < hi) ? static_cast<int>(t_own - lo) : -1;
-    const long mrem = mask_end - lo;
-    const int mask_n = !kMasked || mrem <= 0 ? 0 : (mrem >= n ? n : static_cast<int>(mrem));
     const bool last_tile = t_end <= tk0 + TS;
-    const int trel0 = static_cast<int>(lo - t_start);
     const uint32_t *tref = tile + (lo - tk0);
     for (int o = 0; o < n; o += U) {
       if (o == own_at) st.save(save_start, lane);
       uint32_t *rg = ring + buf * 64 + soff;
       const uint32_t *ref = nr ? zw : tref + o;
       const int tabs = static_cast<int>(lo) + o;
-      if (kMasked && o < mask_n)
-        st.template chunk<true>(ref, trel0 + o, lane, rg, fl * U, ng, nr, tracked, tabs, top);
-      else
-        st.template chunk<false>(ref, 0, lane, rg, fl * U, ng, nr, tracked, tabs, top);
+      st.chunk(ref, lane, rg, fl * U, ng, nr, tracked, tabs, top);
       if (++fl == F || (last_tile && o + U >= n)) {
         __syncwarp();
         for (int r = 0; r < nscan; ++r) {  // entry j = step tflush + j of this lane's stack
@@ -755,7 +743,8 @@ __device__ void sweep_unit(const SdtwArgs &A, TileStream &ts, const Group &g, in
   st.load(A.img + static_cast<size_t>(item) * kImgStride, lane);
   long t_start, t_own, t_end;
   seg_bounds(S, g.nseg, g.seg, A.N, &t_start, &t_own, &t_end);
-  st.fresh(t_start, lane);
+  const bool stk0 = A.items[item].stacked != 0;
+  st.fresh(t_start, lane, (stk0 ? (lane & 15) : lane) != 0 ? 1u : 0u);
   uint32_t *ss = nullptr, *sf = nullptr;
   const size_t unit = static_cast<size_t>(item) * A.nseg_cap + g.seg;
   constexpr size_t kWords = state_rows_per_s<FORM>() * 16 * 32;
@@ -798,10 +787,10 @@ __device__ __forceinline__ void dispatch_sweep(int s, const SdtwArgs &A, TileStr
   }
 }
 
-// One 8-warp CTA per SM: a strip of 16 rows per lane needs ~190 registers (a
-// 168-register cap, for 12 warps per SM, measured ~20% slower).
+// Up to 12 warps per CTA (3 per scheduler): the int16, FP32 and wide strips
+// fit in 168 registers a thread; the start-column strips (~240) up to 8.
 template <int PREC>
-__global__ void __launch_bounds__(256, 1) sdtw_kernel(SdtwArgs A) {
+__global__ void __launch_bounds__(prec_span(PREC) ? 256 : 384, 1) sdtw_kernel(SdtwArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared *sh = reinterpret_cast<Shared *>(smem);
   // layout: Shared (128 B) | per-warp tracking rings | zero words | two tile slots
@@ -919,8 +908,12 @@ __device__ void fixup_item(const SdtwArgs &A, int item, uint32_t *ring, int lane
       // start columns in the span forms) equals the previous segment's final one.
       const uint32_t *exact = A.states + ((base + s - 1) * 2 + 1) * kWords;
       const uint32_t *spec = A.states + ((base + s) * 2 + 0) * kWords;
+      // (int16: equal modulo min(CAP, .), which fixes every later capped value)
       bool eq = true;
-      for (int k = 0; k < kRows * S; ++k) eq = eq && exact[k * 32 + lane] == spec[k * 32 + lane];
+      for (int k = 0; k < kRows * S; ++k) {
+        const uint32_t x = exact[k * 32 + lane], y = spec[k * 32 + lane];
+        eq = eq && (FORM == kFormI16 ? __vminu2(x, kCap2) == __vminu2(y, kCap2) : x == y);
+      }
       if (!__all_sync(kFull, eq)) {
         long t_start, t_own, t_end;
         seg_bounds(S, nseg, s, A.N, &t_start, &t_own, &t_end);

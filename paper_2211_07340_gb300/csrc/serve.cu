@@ -210,6 +210,14 @@ class Server {
   // a batch's GPU stage (launch -> completion seen, minus device execution)
   std::atomic<uint64_t> max_exec_{0}, max_notice_{0};
   std::atomic<uint64_t> max_drain_{0};  // longest intake drain (part of the upload stage)
+  // longest time in each group of CUDA calls of a turn: upload = the staged
+  // copy, the scatter launch and the event record; launch = the batch's input
+  // copies and gather, the device path's launches, the result copies and
+  // the completion event
+  std::atomic<uint64_t> max_part_[4] = {{0}, {0}, {0}, {0}};
+  void note_part(int k, uint64_t dt) {
+    if (dt > max_part_[k]) max_part_[k] = dt;
+  }
   uint64_t spin_ns_ = 0;  // keep polling this long after the last piece of work
   std::atomic<uint64_t> worst_[6] = {{0}, {0}, {0}, {0}, {0}, {0}};  // parts of the slowest turn
   void note_stage(int k, uint64_t dt) {
@@ -462,6 +470,10 @@ void Server::stats(haru_stream_stats *out) {
   out->max_gpu_exec_ns = max_exec_;
   out->max_notice_ns = max_notice_;
   out->max_drain_ns = max_drain_;
+  out->max_upload_calls_ns = max_part_[0];
+  out->max_launch_inputs_ns = max_part_[1];
+  out->max_launch_path_ns = max_part_[2];
+  out->max_launch_results_ns = max_part_[3];
   out->worst_turn_complete_ns = worst_[0];
   out->worst_turn_upload_ns = worst_[1];
   out->worst_turn_launch_ns = worst_[2];
@@ -516,6 +528,7 @@ int Server::turn_upload() {
   }
   if (!ops.empty()) {
     std::memcpy(h_ops_, ops.data(), ops.size() * sizeof(CopyOp));
+    const uint64_t tc = now_ns();
     cudaError_t e = cudaMemcpyAsync(d_stage_, h_stage_, staged * sizeof(float), cudaMemcpyHostToDevice, up_stream_);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_ops_, h_ops_, ops.size() * sizeof(CopyOp), cudaMemcpyHostToDevice, up_stream_);
@@ -527,6 +540,7 @@ int Server::turn_upload() {
     }
     // the staging buffers are reused next turn: wait for this transfer
     if (e == cudaSuccess) e = cudaEventRecord(up_done_, up_stream_);
+    note_part(0, now_ns() - tc);
     // Poll for the transfer (a few tens of microseconds) rather than block
     // in the CUDA driver; bounded by the context's wait limit.
     const uint64_t ts = now_ns();
@@ -576,6 +590,7 @@ int Server::turn_launch() {
       }
     }
     cudaStream_t s = b.stream;
+    const uint64_t t0 = now_ns();
     cudaError_t e = cudaStreamWaitEvent(s, up_done_, 0);
     if (e == cudaSuccess) e = cudaEventRecord(b.start, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.d_off, b.h_off, (n + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
@@ -584,15 +599,21 @@ int Server::turn_launch() {
       gather_kernel<<<n, 128, 0, s>>>(d_slots_, slot_len_, b.d_slot, b.d_off, static_cast<int>(n), b.d_events);
       e = cudaGetLastError();
     }
+    const uint64_t t1 = now_ns();
     if (e == cudaSuccess) e = ws_reserve(b.ws, precision_, n, lc_);
     if (e == cudaSuccess)
       e = ws_enqueue(b.ws, precision_, ref_, b.d_events, b.d_off, n, 1, b.d_cost, b.d_col, lc_, s, nullptr,
                      nullptr, nullptr);
+    const uint64_t t2 = now_ns();
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.h_cost, b.d_cost, n * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.h_col, b.d_col, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b.h_status, b.ws.ints + kIntStatus, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(b.done, s);
+    const uint64_t t3 = now_ns();
+    note_part(1, t1 - t0);
+    note_part(2, t2 - t1);
+    note_part(3, t3 - t2);
     if (e != cudaSuccess) return HARU_ECUDA;
     b.busy = true;
     n_batches_++;

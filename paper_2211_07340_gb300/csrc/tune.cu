@@ -64,7 +64,7 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   const LaunchCfg base = ctx->launch_cfg();
   const int auto_units = 4 * ctx->sms * 8;
-  const int warps_c[] = {4, 8};
+  const int warps_c[] = {4, 8, 12};
   const int tiles_c[] = {2048, 4096, 8192, 16384};
   const int units_c[] = {1, auto_units / 2, auto_units, 2 * auto_units};
   float best_ms = -1.0f;

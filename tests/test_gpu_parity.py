@@ -68,7 +68,7 @@ def test_sars_32x250_both_forms(haru, sars):
     assert (np.abs(j32[on] - qs.truth_end[on]) <= 8).mean() >= 0.9
 
 
-@pytest.mark.parametrize("tile,warps,stack", [(2048, 8, 1), (4096, 4, -1), (16384, 2, 1), (4096, 8, -1)])
+@pytest.mark.parametrize("tile,warps,stack", [(2048, 8, 1), (4096, 4, -1), (16384, 2, 1), (4096, 8, -1), (8192, 12, 1)])
 def test_ragged_sizes_span_tiles(haru, tile, warps, stack):
     rng = np.random.default_rng(tile + warps)
     N = 9_001  # several tiles plus a ragged tail
@@ -218,7 +218,7 @@ def test_autotuner_keeps_results(haru, sars):
         before = [ctx.sdtw_batch(p, qs.events, qs.offsets) for p in forms]
         for i, p in enumerate(forms):
             chosen = ctx.autotune(p, qs.events, qs.offsets)
-            assert chosen["warps_per_cta"] in (4, 8) and chosen["tile_cols"] in (2048, 4096, 8192, 16384)
+            assert chosen["warps_per_cta"] in (4, 8, 12) and chosen["tile_cols"] in (2048, 4096, 8192, 16384)
             c, j = ctx.sdtw_batch(p, qs.events, qs.offsets)
             np.testing.assert_array_equal(c, before[i][0])
             np.testing.assert_array_equal(j, before[i][1])
