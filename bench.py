@@ -269,6 +269,64 @@ def ref_sweep(haru, args, dev):
             "l2": "flushed between batches (512 MiB write)", "cpu_cores": os.cpu_count()}
 
 
+def run_signal(haru, args, ctx, dev, stream, flush, rank):
+    """The raw-signal path: 8,192 reads of int16 ADC samples (adaptor, then
+    pore-model levels under noise) through haru_sdtw_batch_signal (event
+    detection, adaptor trim, 250-event queries, int16 sDTW), replayed from a
+    CUDA graph; event detection alone is timed the same way, and its share of
+    the step is reported."""
+    import torch
+    g, m, k, R = synth.signal_workload("sars_signal_uneven_8192", seed=111 + 1000 * rank)
+    d_smp = torch.from_numpy(R.samples).to(dev)
+    d_off = torch.from_numpy(R.offsets.astype(np.int32)).to(dev)
+    cost = torch.empty(R.nreads, dtype=torch.float32, device=dev)
+    col = torch.empty(R.nreads, dtype=torch.int64, device=dev)
+    nev = torch.empty(R.nreads, dtype=torch.int32, device=dev)
+    p = ctx.event_params()
+    d_ev = torch.empty(R.nreads * p.max_events, dtype=torch.float32, device=dev)
+    d_eoff = torch.empty(R.nreads + 1, dtype=torch.int32, device=dev)
+    sh = stream.cuda_stream
+
+    def full():
+        ctx.sdtw_batch_signal_device(haru.HARU_INT16, d_smp, d_off, cost, col, nev, p, stream=sh, asynchronous=True)
+
+    def detect():
+        ctx.detect_events_device(d_smp, d_off, d_ev, d_eoff, p, stream=sh, asynchronous=True)
+
+    out = {}
+    for name, fn in (("step", full), ("detect", detect)):
+        with torch.cuda.stream(stream):
+            for _ in range(2):  # workspace growth outside capture
+                fn()
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times = []
+        for rep in range(args.warmup + args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0.record(stream)
+                graph.replay()
+                e1.record(stream)
+            stream.synchronize()
+            if rep >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        if ctx.last_status() != haru.HARU_OK:
+            raise haru.HaruError(ctx.last_status(), "signal " + name)
+        out[name] = float(np.mean(times))
+    n_ev = nev.cpu().numpy().astype(np.int64)
+    cells = float(n_ev.sum()) * ctx.ref_length
+    return {"value": cells / (out["step"] / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": out["step"],
+            "detect_ms": out["detect"], "detect_share": out["detect"] / out["step"],
+            "reads": R.nreads, "samples_per_step": int(R.samples.shape[0]),
+            "sample_bytes_per_step": int(R.samples.nbytes), "query_events_mean": float(n_ev.mean()),
+            "form": "int16", "note": "raw int16 ADC samples -> two-window t-test events (windows 3/6, "
+                                     "thresholds 1.40/9.00), 50 adaptor events trimmed, 250-event queries, "
+                                     "z-score, int16 sDTW; CUDA graph, L2 flushed"}
+
+
 def pick_threshold(costs, on_target):
     """Decision threshold from a labelled held-out set: the cost cut with the
     fewest misclassified queries (accept iff cost <= T); among equally good
@@ -412,9 +470,9 @@ def main():
     ap.add_argument("--nq", type=int, default=0, help="first nq queries only (profiling runs)")
     ap.add_argument("--units", type=int, default=0, help="work units target (0 = library default)")
     ap.add_argument("--fixed-len", type=int, default=0, help="profiling: every query this many events")
-    ap.add_argument("--forms", default="int16,fp32,acc32,span",
+    ap.add_argument("--forms", default="int16,fp32,acc32,span,signal",
                     help="forms to time: int16, fp32, acc32 (int16 inputs, 32-bit accumulation), span (FP32 with "
-                         "alignment start columns)")
+                         "alignment start columns), signal (raw samples: event detection then int16 sDTW)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the library defaults)")
     ap.add_argument("--workload", default=WORKLOAD, help="sars_uneven_8192 (default) or long_512x250")
@@ -580,6 +638,10 @@ def main():
         launches.append(5 * len(times))  # plan, statistics, pack, sweep, fix-up
     if "int16" in tuned:
         ctx.configure(**tuned["int16"])
+    signal = None
+    if "signal" in forms and args.workload == WORKLOAD:
+        signal = run_signal(haru, args, ctx, dev, stream, flush, rank)
+        launches.append(8 * (args.steps + args.steps))  # detect, scan, compact + the batch path; detect-only graph
 
     # End to end through the C ABI with host buffers: H2D of raw events and
     # offsets, the batch, D2H of costs and columns, every step.
@@ -666,6 +728,7 @@ def main():
                                 "note": "FP32 with each alignment's start column (haru_sdtw_batch_span): "
                                         "direct launches, default launch shape"}
                                if span_ms == span_ms else None),
+        "signal": signal,
         "int16_over_fp32": value / value32 if value32 == value32 else None,
         "int16_capped_queries": capped16,
         "prep_ms_per_step": ms16 - sweep16,

@@ -386,11 +386,14 @@ class Context:
                                             int(ev.shape[0]), int(t_arrival_ns), int(bool(last_chunk))))
 
     def stream_poll(self, max_results: int = 4096, timeout_us: int = 1000):
-        """Finished decisions as a list of haru_result (possibly empty)."""
-        buf = (haru_result * max_results)()
+        """Finished decisions as a list of haru_result (possibly empty). The
+        receive buffer is kept between calls (no allocation per poll)."""
+        buf = getattr(self, "_poll_buf", None)
+        if buf is None or len(buf) < max_results:
+            buf = self._poll_buf = (haru_result * max_results)()
         n = ctypes.c_uint32()
         check(lib().haru_stream_poll(self._h, buf, max_results, ctypes.byref(n), int(timeout_us)), "haru_stream_poll")
-        return [buf[i] for i in range(n.value)]
+        return [haru_result.from_buffer_copy(buf[i]) for i in range(n.value)]
 
     def stream_stats(self) -> dict:
         st = haru_stream_stats()

@@ -198,6 +198,11 @@ class Server {
   cudaStream_t up_stream_ = nullptr;
   cudaEvent_t up_done_ = nullptr;
   std::vector<BatchCtx> batches_;
+  // per-turn scratch of the worker, kept between turns so that a turn does
+  // not allocate once the vectors have grown
+  std::vector<CopyOp> ops_;
+  std::vector<uint64_t> finished_;
+  std::vector<haru_result> res_;
   LaunchCfg lc_;
   RefView ref_;
 
@@ -493,9 +498,11 @@ void Server::stats(haru_stream_stats *out) {
 // admitted read to its slot (one staged transfer and one scatter kernel).
 int Server::turn_upload() {
   drain_intake();
-  std::vector<CopyOp> ops;
+  std::vector<CopyOp> &ops = ops_;
+  ops.clear();
   size_t staged = 0;
-  std::vector<uint64_t> finished;
+  std::vector<uint64_t> &finished = finished_;
+  finished.clear();
   {
     std::lock_guard<std::mutex> lk(mu_);
     while (!admit_q_.empty() && !free_slots_.empty()) {
@@ -640,7 +647,8 @@ int Server::turn_complete() {
     const int st = *b.h_status;
     const float s = static_cast<float>(1 << ref_.scale_log2);
     const float thr = precision_ == HARU_INT16 ? std::floor(threshold_ * s) / s : threshold_;
-    std::vector<haru_result> res(b.reads.size());
+    std::vector<haru_result> &res = res_;
+    res.resize(b.reads.size());
     {
       std::lock_guard<std::mutex> lk(mu_);
       for (size_t i = 0; i < b.reads.size(); ++i) {
