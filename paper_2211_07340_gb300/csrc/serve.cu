@@ -178,7 +178,21 @@ class Server {
   std::atomic<size_t> host_events_{0};  // events held on the host (taken from the intake)
   std::mutex out_mu_;
   std::condition_variable cv_out_;
-  std::deque<haru_result> done_q_;
+  // finished results, a ring under out_mu_: the worker appends (and alone
+  // grows the storage), poll copies out and advances the head; no thread
+  // frees memory another thread allocated
+  std::vector<haru_result> out_buf_;
+  size_t out_head_ = 0, out_n_ = 0;
+  void push_out(const haru_result &o) {  // worker, out_mu_ held
+    if (out_n_ == out_buf_.size()) {
+      std::vector<haru_result> grown(std::max<size_t>(4096, 2 * out_buf_.size()));
+      for (size_t i = 0; i < out_n_; ++i) grown[i] = out_buf_[(out_head_ + i) % out_buf_.size()];
+      out_buf_.swap(grown);
+      out_head_ = 0;
+    }
+    out_buf_[(out_head_ + out_n_) % out_buf_.size()] = o;
+    ++out_n_;
+  }
   int error_ = HARU_OK;
 
   // device resources
@@ -433,7 +447,7 @@ void Server::take_chunk(const Chunk *c) {
       reads_.erase(it);
       {
         std::lock_guard<std::mutex> lo(out_mu_);
-        done_q_.push_back(o);
+        push_out(o);
       }
       n_decided_++;
       cv_out_.notify_all();
@@ -444,13 +458,13 @@ void Server::take_chunk(const Chunk *c) {
 int Server::poll(haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us) {
   *n_out = 0;
   std::unique_lock<std::mutex> lk(out_mu_);
-  if (done_q_.empty() && error_ == HARU_OK && timeout_us > 0)
-    cv_out_.wait_for(lk, std::chrono::microseconds(timeout_us),
-                     [&] { return !done_q_.empty() || error_ != HARU_OK; });
+  if (out_n_ == 0 && error_ == HARU_OK && timeout_us > 0)
+    cv_out_.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return out_n_ > 0 || error_ != HARU_OK; });
   uint32_t k = 0;
-  while (k < max && !done_q_.empty()) {
-    out[k++] = done_q_.front();
-    done_q_.pop_front();
+  while (k < max && out_n_ > 0) {
+    out[k++] = out_buf_[out_head_];
+    out_head_ = (out_head_ + 1) % out_buf_.size();
+    --out_n_;
   }
   *n_out = k;
   if (k == 0 && error_ != HARU_OK) return error_;
@@ -679,7 +693,7 @@ int Server::turn_complete() {
     b.busy = false;
     {
       std::lock_guard<std::mutex> lk(out_mu_);
-      for (auto &o : res) done_q_.push_back(o);
+      for (auto &o : res) push_out(o);
     }
     n_decided_ += res.size();
     cv_out_.notify_all();
@@ -691,6 +705,10 @@ void Server::worker() {
   if (cudaSetDevice(ctx_->device) != cudaSuccess) {
     fail(HARU_ECUDA);
     return;
+  }
+  {
+    std::lock_guard<std::mutex> lk(out_mu_);  // the result ring, allocated by this thread
+    if (out_buf_.empty()) out_buf_.resize(4096);
   }
   uint64_t t_prev = now_ns();
   long vcs0 = 0, ics0 = 0;
