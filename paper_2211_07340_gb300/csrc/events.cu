@@ -20,17 +20,17 @@
 // [trim, trim + max_events).
 //
 // Kernels: detect_kernel (one CTA per read: the read's samples in shared
-// memory, statistics over tiles of kEvTile positions with halos, peaks, an
-// ordered block-wide compaction of boundaries that stops once the query's
-// boundaries are known, then the event means), scan_kernel (CSR offsets of
-// the per-read event counts) and compact_kernel (strided -> CSR).
+// memory, statistics over tiles of kEvTile positions with halos, each thread
+// sliding its window sums along a run of positions; peaks compared on float
+// t^2 values with a margin that covers their rounding, falling back to the
+// exact integers when it cannot decide; an ordered block-wide compaction of
+// boundaries that stops once the query's boundaries are known; then the
+// event means), scan_kernel (CSR offsets of the per-read event counts) and
+// compact_kernel (strided -> CSR).
 
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <cstring>
-#include <mutex>
-#include <vector>
 
 #include "engine.h"
 
@@ -42,16 +42,17 @@ constexpr int kEvTile = 1024;                      // boundary positions per til
 constexpr int kEvPer = kEvTile / kEvThreads;       // consecutive positions per thread
 constexpr int kEvMaxW = 16;                        // longest window
 constexpr int kEvTpos = kEvTile + 4 * kEvMaxW;     // statistics per tile (halo w1 + w2 on each side)
+constexpr int kEvRun = (kEvTpos + kEvThreads - 1) / kEvThreads;  // statistics per thread (a contiguous run)
 constexpr int kEvLp = kEvTile + 2 * kEvMaxW;       // long-peak flags per tile (halo w1 on each side)
 static_assert(kEvTile % kEvThreads == 0 && kEvPer <= 32, "tile split");
 
-// Shared-memory layout of detect_kernel (bytes).
-constexpr size_t kSmX = 0;                                            // int16 samples
-constexpr size_t kSmStats = kSmX + HARU_MAX_READ_SAMPLES * sizeof(int16_t);  // 4 x kEvTpos uint64
-constexpr size_t kSmLp = kSmStats + 4 * kEvTpos * sizeof(unsigned long long);
-constexpr size_t kSmBounds = kSmLp + (kEvLp + 15) / 16 * 16;          // int bounds
-// boundaries are at least w_short + 1 >= 3 samples apart: at most n / 3 + 1
-constexpr size_t kSmBytes = kSmBounds + (HARU_MAX_READ_SAMPLES / 3 + 2) * sizeof(int);
+// Shared-memory layout of detect_kernel (bytes); the boundary list follows,
+// as many ints as the query needs (trim + max_events).
+constexpr size_t kSmX = 0;                                                  // int16 samples
+constexpr size_t kSmT = kSmX + HARU_MAX_READ_SAMPLES * sizeof(int16_t);     // 2 x kEvTpos float t^2
+constexpr size_t kSmLp = kSmT + 2 * kEvTpos * sizeof(float);
+constexpr size_t kSmBounds = kSmLp + (kEvLp + 15) / 16 * 16;
+size_t detect_smem_bytes(int need) { return kSmBounds + static_cast<size_t>(need) * sizeof(int); }
 
 struct EvArgs {
   const int16_t *samples;
@@ -59,67 +60,140 @@ struct EvArgs {
   uint32_t nreads;
   int w1, w2;
   unsigned long long tau1sq, tau2sq;  // (100 tau)^2
+  float tau1f, tau2f;                 // tau^2 as floats (for the fast path)
   int trim, maxev;
   float *out;        // [nreads][maxev]
   uint32_t *counts;  // nreads
   int *status;
 };
 
-// a * b as 128 bits (hi, lo): every product of a statistic's numerator
-// (< 2^45) or denominator (< 2^40) with another, or with a squared threshold.
+// a * b > c * d for 64-bit factors (128-bit products): every product of a
+// statistic's numerator (< 2^45) or denominator (< 2^40) with another, or
+// with a squared threshold.
 __device__ __forceinline__ bool mul_gt(unsigned long long a, unsigned long long b, unsigned long long c,
-                                       unsigned long long d) {  // a * b > c * d
+                                       unsigned long long d) {
   const unsigned long long h1 = __umul64hi(a, b), h2 = __umul64hi(c, d);
   return h1 > h2 || (h1 == h2 && a * b > c * d);
 }
 
-// Statistic of window w at position i (num, den; 0, 0 where undefined).
-__device__ __forceinline__ void tstat(const int16_t *x, int n, int w, int i, unsigned long long *num,
-                                      unsigned long long *den) {
-  if (i < w || i > n - w) {
-    *num = 0;
-    *den = 0;
-    return;
+// Window sums at position i: A, QA over [i - w, i), B, QB over [i, i + w).
+struct Win {
+  long long A, B, QA, QB;
+  __device__ __forceinline__ void direct(const int16_t *x, int w, int i) {
+    A = B = QA = QB = 0;
+    for (int k = i - w; k < i; ++k) {
+      const int v = x[k];
+      A += v;
+      QA += v * v;
+    }
+    for (int k = i; k < i + w; ++k) {
+      const int v = x[k];
+      B += v;
+      QB += v * v;
+    }
   }
-  long long A = 0, B = 0, QA = 0, QB = 0;
-  for (int k = i - w; k < i; ++k) {
-    const long long v = x[k];
-    A += v;
-    QA += v * v;
+  // from position i - 1 to i
+  __device__ __forceinline__ void slide(const int16_t *x, int w, int i) {
+    const int in_l = x[i - 1], out_l = x[i - 1 - w], in_r = x[i + w - 1];
+    A += in_l - out_l;
+    QA += in_l * in_l - out_l * out_l;
+    B += in_r - in_l;
+    QB += in_r * in_r - in_l * in_l;
   }
-  for (int k = i; k < i + w; ++k) {
-    const long long v = x[k];
-    B += v;
-    QB += v * v;
+  // t^2 = num / den (exact integers)
+  __device__ __forceinline__ void stat(int w, unsigned long long *num, unsigned long long *den) const {
+    const long long d = B - A;
+    long long D = static_cast<long long>(w) * (QA + QB) - A * A - B * B;
+    if (D < 1) D = 1;
+    *num = static_cast<unsigned long long>(static_cast<long long>(w) * d * d);
+    *den = static_cast<unsigned long long>(D);
   }
-  const long long d = B - A;
-  long long D = static_cast<long long>(w) * (QA + QB) - A * A - B * B;
-  if (D < 1) D = 1;
-  *num = static_cast<unsigned long long>(static_cast<long long>(w) * d * d);
-  *den = static_cast<unsigned long long>(D);
+};
+
+// t^2 of window w at position i, exactly (for the rare comparisons the
+// float values cannot decide).
+__device__ __noinline__ void exact_stat(const int16_t *x, int w, int i, unsigned long long *num,
+                                        unsigned long long *den) {
+  Win s;
+  s.direct(x, w, i);
+  s.stat(w, num, den);
 }
 
-// Peak test of statistic index j (num/den arrays of the tile): above the
-// threshold, strictly above the w defined statistics before it, at least the
-// w after it. The caller keeps j - w >= 0 and j + w < kEvTpos.
-__device__ __forceinline__ bool peak(const unsigned long long *num, const unsigned long long *den, int j, int w,
+// The float t^2 of a statistic carries a relative error below 2^-21 (the
+// numerator and denominator each rounded once to float, one correctly
+// rounded division), so two of them decide a comparison of the exact values
+// whenever they differ by more than the margin; otherwise the comparison is
+// redone on the exact integers.
+constexpr float kMarginUp = 1.0f + 1.0f / 262144.0f, kMarginDown = 1.0f - 1.0f / 262144.0f;  // 2^-18
+
+// t_i > t_j for positions qi, qj of window w (tf_* their float t^2, >= 0).
+__device__ __forceinline__ bool t_greater(const int16_t *x, int w, int qi, float ti, int qj, float tj) {
+  if (ti > tj * kMarginUp) return true;
+  if (ti < tj * kMarginDown) return false;
+  unsigned long long ni, di, nj, dj;
+  exact_stat(x, w, qi, &ni, &di);
+  exact_stat(x, w, qj, &nj, &dj);
+  return mul_gt(ni, dj, nj, di);
+}
+
+// t_i > tau, i.e. 10000 num > (100 tau)^2 den.
+__device__ __forceinline__ bool t_above(const int16_t *x, int w, int qi, float ti, float tauf,
+                                        unsigned long long tausq) {
+  if (ti > tauf * kMarginUp) return true;
+  if (ti < tauf * kMarginDown) return false;
+  unsigned long long ni, di;
+  exact_stat(x, w, qi, &ni, &di);
+  return mul_gt(ni, 10000ull, di, tausq);
+}
+
+// Peak test of statistic index j (position q) of a tile: above the threshold,
+// strictly above the w defined statistics before it, at least the w after
+// it. Undefined statistics hold -1. The caller keeps j - w >= 0 and
+// j + w < kEvTpos.
+__device__ __forceinline__ bool peak(const int16_t *x, const float *tf, int j, int q, int w, float tauf,
                                      unsigned long long tausq) {
-  const unsigned long long nj = num[j], dj = den[j];
-  if (dj == 0 || !mul_gt(nj, 10000ull, dj, tausq)) return false;
+  const float tj = tf[j];
+  if (tj < 0.0f || !t_above(x, w, q, tj, tauf, tausq)) return false;
   for (int k = 1; k <= w; ++k) {
-    const unsigned long long dl = den[j - k];
-    if (dl != 0 && !mul_gt(nj, dl, num[j - k], dj)) return false;  // need t_j > t_{j-k}
-    const unsigned long long dr = den[j + k];
-    if (dr != 0 && mul_gt(num[j + k], dj, nj, dr)) return false;   // need t_{j+k} <= t_j
+    const float tl = tf[j - k];
+    if (tl >= 0.0f && !t_greater(x, w, q, tj, q - k, tl)) return false;  // need t_q > t_{q-k}
+    const float tr = tf[j + k];
+    if (tr >= 0.0f && t_greater(x, w, q + k, tr, q, tj)) return false;   // need t_{q+k} <= t_q
   }
   return true;
 }
 
-__global__ void __launch_bounds__(kEvThreads) detect_kernel(EvArgs a) {
+// Statistics of window w at positions q = p0 - H + j for this thread's run
+// of j, sliding the window sums along the run.
+__device__ __forceinline__ void tile_stats(const int16_t *x, int n, int w, int p0, int H, int jmax, float *tf) {
+  Win s;
+  bool have = false;
+#pragma unroll
+  for (int r = 0; r < kEvRun; ++r) {
+    const int j = threadIdx.x * kEvRun + r;
+    if (j >= jmax) break;
+    const int q = p0 - H + j;
+    if (q < w || q > n - w) {
+      tf[j] = -1.0f;
+      have = false;
+      continue;
+    }
+    if (have)
+      s.slide(x, w, q);
+    else
+      s.direct(x, w, q);
+    have = true;
+    unsigned long long num, den;
+    s.stat(w, &num, &den);
+    tf[j] = __fdiv_rn(__ull2float_rn(num), __ull2float_rn(den));
+  }
+}
+
+// Four CTAs per SM (shared memory ~44 KB each with the default parameters).
+__global__ void __launch_bounds__(kEvThreads, 4) detect_kernel(EvArgs a) {
   extern __shared__ __align__(16) unsigned char sm[];
   int16_t *x = reinterpret_cast<int16_t *>(sm + kSmX);
-  unsigned long long *n1 = reinterpret_cast<unsigned long long *>(sm + kSmStats);
-  unsigned long long *d1 = n1 + kEvTpos, *n2 = d1 + kEvTpos, *d2 = n2 + kEvTpos;
+  float *t1 = reinterpret_cast<float *>(sm + kSmT), *t2 = t1 + kEvTpos;
   unsigned char *lp = sm + kSmLp;
   int *bounds = reinterpret_cast<int *>(sm + kSmBounds);
   __shared__ int warp_tot[kEvThreads / 32];
@@ -143,18 +217,12 @@ __global__ void __launch_bounds__(kEvThreads) detect_kernel(EvArgs a) {
   const int need = a.trim + a.maxev;  // boundaries b_1 .. b_need close the query's last event
   for (int p0 = 0; p0 < n; p0 += kEvTile) {
     // statistics at positions q = p0 - H + j, j in [0, kEvTile + 2H)
-    for (int j = tid; j < kEvTile + 2 * H; j += kEvThreads) {
-      const int q = p0 - H + j;
-      if (q < 0 || q > n) {
-        n1[j] = d1[j] = n2[j] = d2[j] = 0;
-      } else {
-        tstat(x, n, w1, q, &n1[j], &d1[j]);
-        tstat(x, n, w2, q, &n2[j], &d2[j]);
-      }
-    }
+    tile_stats(x, n, w1, p0, H, kEvTile + 2 * H, t1);
+    tile_stats(x, n, w2, p0, H, kEvTile + 2 * H, t2);
     __syncthreads();
-    // long-window peaks at q = p0 - w1 + j, j in [0, kEvTile + 2 w1)
-    for (int j = tid; j < kEvTile + 2 * w1; j += kEvThreads) lp[j] = peak(n2, d2, j + w2, w2, a.tau2sq) ? 1 : 0;
+    // long-window peaks at q = p0 - w1 + j, j in [0, kEvTile + 2 w1) (statistic index j + w2)
+    for (int j = tid; j < kEvTile + 2 * w1; j += kEvThreads)
+      lp[j] = peak(x, t2, j + w2, p0 - w1 + j, w2, a.tau2f, a.tau2sq) ? 1 : 0;
     __syncthreads();
     // boundaries among this thread's positions p0 + tid * kEvPer + u
     unsigned flags = 0;
@@ -165,7 +233,7 @@ __global__ void __launch_bounds__(kEvThreads) detect_kernel(EvArgs a) {
       if (p < 1 || p > n - 1) continue;
       const int jl = p - p0 + w1;  // its long-peak flag
       bool b = lp[jl] != 0;
-      if (!b && peak(n1, d1, p - p0 + H, w1, a.tau1sq)) {
+      if (!b && peak(x, t1, p - p0 + H, p, w1, a.tau1f, a.tau1sq)) {
         bool near = false;
         for (int k = -w1; k <= w1; ++k) near = near || lp[jl + k] != 0;
         b = !near;
@@ -175,7 +243,8 @@ __global__ void __launch_bounds__(kEvThreads) detect_kernel(EvArgs a) {
         ++cnt;
       }
     }
-    // ordered compaction: exclusive prefix of cnt over the block
+    // ordered compaction: exclusive prefix of cnt over the block; only the
+    // first `need` boundaries are kept (the query uses b_1 .. b_need)
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -194,7 +263,10 @@ __global__ void __launch_bounds__(kEvThreads) detect_kernel(EvArgs a) {
     int pos = s_nb + before + incl - cnt;
 #pragma unroll
     for (int u = 0; u < kEvPer; ++u)
-      if (flags & (1u << u)) bounds[pos++] = p0 + tid * kEvPer + u;
+      if (flags & (1u << u)) {
+        if (pos < need) bounds[pos] = p0 + tid * kEvPer + u;
+        ++pos;
+      }
     __syncthreads();
     if (tid == 0) s_nb += total;
     __syncthreads();
@@ -204,7 +276,7 @@ __global__ void __launch_bounds__(kEvThreads) detect_kernel(EvArgs a) {
   int K = n > 0 ? nb + 1 - a.trim : 0;  // events after the trim (an empty read has none)
   K = K < 0 ? 0 : (K > a.maxev ? a.maxev : K);
   for (int k = tid; k < K; k += kEvThreads) {
-    const int e = a.trim + k;
+    const int e = a.trim + k;  // e + 1 <= need: both ends are stored boundaries (or 0, n)
     const int lo = e == 0 ? 0 : bounds[e - 1];
     const int hi = e + 1 <= nb ? bounds[e] : n;
     long long s = 0;
@@ -283,12 +355,11 @@ cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uin
                            const haru_event_params &p, float *strided, uint32_t *counts, uint32_t *ev_off,
                            float *ev_csr, int *status, cudaStream_t s) {
   if (nreads == 0) return cudaSuccess;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmBytes));
-  });
-  if (attr != cudaSuccess) return attr;
+  const int need = static_cast<int>(p.trim_events + p.max_events);
+  const size_t smem = detect_smem_bytes(need);
+  cudaError_t e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
   EvArgs a;
   a.samples = d_samples;
   a.offsets = d_soff;
@@ -297,13 +368,15 @@ cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uin
   a.w2 = p.window_long;
   a.tau1sq = static_cast<unsigned long long>(p.threshold_short_centi) * p.threshold_short_centi;
   a.tau2sq = static_cast<unsigned long long>(p.threshold_long_centi) * p.threshold_long_centi;
+  a.tau1f = static_cast<float>(a.tau1sq) / 10000.0f;
+  a.tau2f = static_cast<float>(a.tau2sq) / 10000.0f;
   a.trim = static_cast<int>(p.trim_events);
   a.maxev = static_cast<int>(p.max_events);
   a.out = strided;
   a.counts = counts;
   a.status = status;
-  detect_kernel<<<nreads, kEvThreads, kSmBytes, s>>>(a);
-  cudaError_t e = cudaGetLastError();
+  detect_kernel<<<nreads, kEvThreads, smem, s>>>(a);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   scan_kernel<<<1, 1024, 0, s>>>(counts, nreads, ev_off);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -51,6 +51,9 @@ def edge_reads():
     levels = np.cumsum(rng.choice([-1, 1], 80) * rng.integers(1, 300, 80)) + 2000
     parts.append(np.repeat(levels, lengths).astype(np.int16))
     parts.append(synth.to_adc(rng.normal(90, 2.5, 3001)))
+    # equal statistics at neighbouring positions (the tie of the event oracle's
+    # pins), repeated: exercises the exact comparison behind the float one
+    parts.append(np.tile(np.array([100] * 20 + [150] + [200] * 20, np.int16), 30))
     _, _, _, R = synth.signal_workload("sars_signal_32x250", nreads=4, seed=57)
     parts += [R.read(r) for r in range(R.nreads)]
     long = synth.signal_workload("sars_signal_32x250", nreads=1, seed=58)[3].read(0)
