@@ -346,11 +346,17 @@ def pick_threshold(costs, on_target):
     return float(0.5 * (c[k - 1] + c[k]))
 
 
-def run_serving(haru, args, local, w, threshold, channels):
+def run_serving(haru, args, local, w, threshold, channels, signal=False):
     """Serve a simulated flow cell in real time; latency from the delivery of
-    the chunk that completes a read's 250-event prefix to its decision."""
+    the chunk that completes a read's 250-event prefix to its decision. With
+    signal=True the flow cell delivers raw int16 samples (400 per 100 ms
+    chunk) and the serving loop detects the events on the device; latency
+    then starts at the chunk after which the prefix's 250 events were final."""
     span = args.serve_warm + args.serve_seconds
-    chunks, q = synth.flowcell_schedule(channels, span, seed=105)
+    if signal:
+        chunks, q = synth.flowcell_signal_schedule(channels, span, seed=305)
+    else:
+        chunks, q = synth.flowcell_schedule(channels, span, seed=105)
     ctx = haru.Context(local, serve_precision=haru.HARU_INT16, threshold=threshold)
     ctx.ref_build(w.genome, w.model, w.k, scale_log2=6)
     results = []
@@ -369,12 +375,14 @@ def run_serving(haru, args, local, w, threshold, channels):
     gc.collect()
     gc.disable()
     try:
+        submit = ctx.stream_submit_signal if signal else ctx.stream_submit
         with ClockSampler(local, args.serve_clock_ms) as clk:
-            late = synth.replay(chunks, lambda c, t: ctx.stream_submit(c.read_id, c.channel, c.events, t, c.last))
+            late = synth.replay(chunks, lambda c, t: submit(c.read_id, c.channel, c.events, t, c.last))
     finally:
         gc.enable()
+    nreads = q.nreads if signal else q.nq
     deadline = time.monotonic() + 30
-    while len(results) < q.nq and time.monotonic() < deadline:
+    while len(results) < nreads and time.monotonic() < deadline:
         time.sleep(0.01)
     done.set()
     th.join()
@@ -386,9 +394,11 @@ def run_serving(haru, args, local, w, threshold, channels):
     lat = np.array([(r.t_done_ns - r.t_arrival_ns) / 1e6 for r in kept])
     lib_lat = np.array([(r.t_done_ns - r.t_received_ns) / 1e6 for r in kept])
     dec = {r.read_id: r.decision for r in results}
-    acc = float(np.mean([dec.get(i, 0) == int(q.on_target[i]) for i in range(q.nq)])) if q.nq else None
+    acc = float(np.mean([dec.get(i, 0) == int(q.on_target[i]) for i in range(nreads)])) if nreads else None
     N = 2 * (synth.SARS_COV_2_BASES - 5)
-    return {"channels": channels, "seconds": args.serve_seconds, "warmup_s": args.serve_warm, "reads": q.nq,
+    cells = float(sum(r.events for r in results)) * N
+    return {"channels": channels, "seconds": args.serve_seconds, "warmup_s": args.serve_warm, "reads": nreads,
+            "input": "raw int16 samples, events detected on the device" if signal else "event chunks",
             "decided": len(results), "precision": "int16", "threshold_z": threshold,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
@@ -398,7 +408,7 @@ def run_serving(haru, args, local, w, threshold, channels):
             "library_p50_ms": float(np.percentile(lib_lat, 50)) if lib_lat.size else None,
             "library_p99_ms": float(np.percentile(lib_lat, 99)) if lib_lat.size else None,
             "library_max_ms": float(lib_lat.max()) if lib_lat.size else None,
-            "decisions_per_s": len(results) / span, "gcups": len(results) * 250 * N / span / 1e9,
+            "decisions_per_s": len(results) / span, "gcups": cells / span / 1e9,
             "accept_eject_accuracy_vs_truth": acc, "batches": st["batches"], "max_batch": st["max_batch"],
             "max_concurrent_batches": st["max_concurrent"], "late_chunks": late, "clocks": clk.summary(),
             "stages": {"max_upload_ms": st["max_upload_ns"] / 1e6, "max_queue_ms": st["max_queue_ns"] / 1e6,
@@ -484,6 +494,9 @@ def main():
                     help="nvidia-smi sampling period during the serving runs (0 = none)")
     ap.add_argument("--stress-channels", type=int, default=4096,
                     help="second serving run at this many channels, same length (0 = skip)")
+    ap.add_argument("--signal-channels", type=int, default=512,
+                    help="serving run on raw samples (event detection on the device) at this many channels, "
+                         "same length (0 = skip)")
     ap.add_argument("--ref-sweep", action="store_true",
                     help="reference-length sweep (59,796 / 257,820 / 9,999,990 columns) instead of the benchmark")
     ap.add_argument("--sweep-reps", type=int, default=10)
@@ -745,6 +758,12 @@ def main():
         result["serving"] = run_serving(haru, args, local, w, thr, args.serve_channels)
         if args.stress_channels > 0:
             result["serving_stress"] = run_serving(haru, args, local, w, thr, args.stress_channels)
+        if args.signal_channels > 0:
+            # the threshold of raw-signal queries, fixed the same way on 1,024 held-out raw-signal reads
+            _, _, _, hs = synth.signal_workload("sars_signal_heldout_1024")
+            hsc, _, _ = ctx.sdtw_batch_signal(haru.HARU_FP32, hs.samples, hs.offsets)
+            thr_sig = pick_threshold(hsc.astype(np.float64), hs.on_target)
+            result["serving_signal"] = run_serving(haru, args, local, w, thr_sig, args.signal_channels, signal=True)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         ref_levels = oracle.ref_levels(w.genome, w.model, w.k)

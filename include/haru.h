@@ -71,6 +71,18 @@ extern "C" {
 
 typedef struct haru_ctx haru_ctx;
 
+/* Event detection on raw samples (see "Raw signal" below for the method). */
+#define HARU_MAX_READ_SAMPLES 16384 /* samples of one read's signal, at most */
+
+typedef struct {
+  int window_short;          /* samples per window of the short t-test, 2..16 (default 3) */
+  int window_long;           /* of the long t-test, window_short..16 (default 6) */
+  int threshold_short_centi; /* t threshold of the short window in hundredths, 1..10000 (default 140) */
+  int threshold_long_centi;  /* of the long window (default 900) */
+  uint32_t trim_events;      /* leading events dropped: the read adaptor (default 50, Section 4.1) */
+  uint32_t max_events;       /* events kept after the trim: the query prefix, 1..HARU_MAX_QUERY (default 250) */
+} haru_event_params;
+
 typedef struct {
   int warps_per_cta;        /* warps (queries or query pairs) sharing one reference tile stream: 2, 4, 8
                                or 12 (start-column batches run at most 8); other values = 8 */
@@ -94,6 +106,8 @@ typedef struct {
   int serve_spin_us;        /* serving: microseconds the worker keeps polling after its last piece of
                                work before it sleeps (a sleeping thread can be woken late on a busy
                                host); 0 = 2000, negative = never poll idle */
+  haru_event_params serve_events; /* serving raw samples (haru_stream_submit_signal): the event detector's
+                               parameters; max_events is replaced by serve_prefix; all zero = defaults */
 } haru_config;
 
 /* Fill *cfg with defaults. Returns HARU_OK, or HARU_EINVAL if cfg is NULL. */
@@ -191,17 +205,6 @@ int haru_sdtw_batch_span(haru_ctx *ctx, int precision, const float *events, cons
  * events [trim_events, trim_events + max_events): the adaptor's events are
  * dropped and the decision prefix kept. The event values are in ADC units;
  * the sDTW path z-scores each query (HARU_RAW behaviour). */
-#define HARU_MAX_READ_SAMPLES 16384 /* samples of one read's signal, at most */
-
-typedef struct {
-  int window_short;          /* samples per window of the short t-test, 2..16 (default 3) */
-  int window_long;           /* of the long t-test, window_short..16 (default 6) */
-  int threshold_short_centi; /* t threshold of the short window in hundredths, 1..10000 (default 140) */
-  int threshold_long_centi;  /* of the long window (default 900) */
-  uint32_t trim_events;      /* leading events dropped: the read adaptor (default 50, Section 4.1) */
-  uint32_t max_events;       /* events kept after the trim: the query prefix, 1..HARU_MAX_QUERY (default 250) */
-} haru_event_params;
-
 /* Fill *p with the defaults. Returns HARU_OK, or HARU_EINVAL if p is NULL. */
 int haru_event_params_default(haru_event_params *p);
 
@@ -268,6 +271,25 @@ typedef struct {
  * poll, then retry), HARU_ECUDA. */
 int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const float *events, uint32_t n,
                        uint64_t t_arrival_ns, int last_chunk);
+
+/* Append a chunk of raw int16 ADC samples (host pointer, n of them) to read
+ * read_id on channel: haru_stream_submit for a flow cell that delivers its
+ * raw signal. The read's samples go to a device slot (at most
+ * HARU_MAX_READ_SAMPLES are kept; a read that reaches them counts as ended).
+ * After each upload the serving loop runs the event detector (see "Raw
+ * signal": adaptor trim, serve_events parameters) over every read with new
+ * samples and counts its query events whose closing boundary is final: at
+ * least window_short + 2 window_long samples before the newest sample, where
+ * later samples can no longer move it. The decision prefix is complete once
+ * serve_prefix such events exist, or when the read ends (last_chunk = 1; its
+ * query is then every event after the trim). Either way the query equals
+ * what haru_sdtw_batch_signal computes on the read's whole signal. The
+ * latency clock starts at t_arrival_ns of the newest chunk the completing
+ * detection covered. A context serves either events or samples: whichever
+ * submit call comes first fixes it, and the other returns HARU_EINVAL.
+ * Errors as haru_stream_submit. */
+int haru_stream_submit_signal(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const int16_t *samples, uint32_t n,
+                              uint64_t t_arrival_ns, int last_chunk);
 
 /* Collect up to max finished decisions into out (host array), waiting up to
  * timeout_us microseconds for the first. *n_out = how many were written

@@ -48,6 +48,12 @@ class HaruError(RuntimeError):
         super().__init__(f"{what}: {name} ({code})" if what else f"{name} ({code})")
 
 
+class haru_event_params(ctypes.Structure):
+    _fields_ = [("window_short", ctypes.c_int), ("window_long", ctypes.c_int),
+                ("threshold_short_centi", ctypes.c_int), ("threshold_long_centi", ctypes.c_int),
+                ("trim_events", ctypes.c_uint32), ("max_events", ctypes.c_uint32)]
+
+
 class haru_config(ctypes.Structure):
     _fields_ = [
         ("warps_per_cta", ctypes.c_int),
@@ -62,13 +68,8 @@ class haru_config(ctypes.Structure):
         ("units_target", ctypes.c_int),
         ("stack_short", ctypes.c_int),
         ("serve_spin_us", ctypes.c_int),
+        ("serve_events", haru_event_params),
     ]
-
-
-class haru_event_params(ctypes.Structure):
-    _fields_ = [("window_short", ctypes.c_int), ("window_long", ctypes.c_int),
-                ("threshold_short_centi", ctypes.c_int), ("threshold_long_centi", ctypes.c_int),
-                ("trim_events", ctypes.c_uint32), ("max_events", ctypes.c_uint32)]
 
 
 class haru_batch_stats(ctypes.Structure):
@@ -127,6 +128,8 @@ _SIGS = {
     "haru_last_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_batch_stats)]),
     "haru_stream_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                           ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int]),
+    "haru_stream_submit_signal": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                                 ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int]),
     "haru_stream_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                         ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]),
     "haru_stream_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(haru_stream_stats)]),
@@ -384,6 +387,14 @@ class Context:
         ev = np.ascontiguousarray(events, dtype=np.float32)
         return int(lib().haru_stream_submit(self._h, int(read_id), int(channel), _ptr(ev) if ev.size else None,
                                             int(ev.shape[0]), int(t_arrival_ns), int(bool(last_chunk))))
+
+    def stream_submit_signal(self, read_id: int, channel: int, samples, t_arrival_ns: int,
+                             last_chunk: bool = False) -> int:
+        """Append a chunk of raw int16 ADC samples to a read; returns the status code."""
+        smp = np.ascontiguousarray(samples, dtype=np.int16)
+        return int(lib().haru_stream_submit_signal(self._h, int(read_id), int(channel),
+                                                   _ptr(smp) if smp.size else None, int(smp.shape[0]),
+                                                   int(t_arrival_ns), int(bool(last_chunk))))
 
     def stream_poll(self, max_results: int = 4096, timeout_us: int = 1000):
         """Finished decisions as a list of haru_result (possibly empty). The

@@ -116,6 +116,7 @@ int haru_config_default(haru_config *cfg) {
   cfg->serve_budget_bytes = 64u << 20;
   cfg->serve_max_batch = 1024;
   cfg->serve_prefix = 250;
+  haru::event_params_default(&cfg->serve_events);
   return HARU_OK;
 }
 

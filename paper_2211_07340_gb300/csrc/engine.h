@@ -114,6 +114,13 @@ bool event_params_valid(const haru_event_params &p);
 cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uint32_t nreads,
                            const haru_event_params &p, float *strided, uint32_t *counts, uint32_t *ev_off,
                            float *ev_csr, int *status, cudaStream_t s);
+// Detection over serving slots: read r's len[r] samples in slot slot[r]
+// (sample_stride per slot), its query events to event slot slot[r]
+// (event_stride floats per slot), counts[r] = events whose closing boundary
+// is at or before final_limit[r].
+cudaError_t enqueue_events_slots(const int16_t *samples, int sample_stride, const uint32_t *slot, const uint32_t *len,
+                                 const int *final_limit, uint32_t nreads, const haru_event_params &p, float *events,
+                                 int event_stride, uint32_t *counts, int *status, cudaStream_t s);
 
 // Record `e` on `s`; inside a stream capture, as an external event node so
 // its time can be read after every replay.

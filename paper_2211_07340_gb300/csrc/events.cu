@@ -62,9 +62,18 @@ struct EvArgs {
   unsigned long long tau1sq, tau2sq;  // (100 tau)^2
   float tau1f, tau2f;                 // tau^2 as floats (for the fast path)
   int trim, maxev;
-  float *out;        // [nreads][maxev]
+  float *out;        // [nreads][maxev] (CSR mode) or the event slots (slot mode)
   uint32_t *counts;  // nreads
   int *status;
+  // Slot mode (serving; slot != nullptr): read r's samples are
+  // samples[slot[r] * sample_stride ...] (len[r] of them), its events go to
+  // out[slot[r] * out_stride ...], and only events whose closing boundary
+  // lies at or before final_limit[r] are counted (a live read's later
+  // boundaries can still move as samples arrive).
+  const uint32_t *slot;
+  const uint32_t *len;
+  const int *final_limit;
+  int sample_stride, out_stride;
 };
 
 // a * b > c * d for 64-bit factors (128-bit products): every product of a
@@ -200,8 +209,18 @@ __global__ void __launch_bounds__(kEvThreads, 4) detect_kernel(EvArgs a) {
   __shared__ int s_nb;
   const uint32_t r = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t base = a.offsets[r];
-  const long len = static_cast<long>(a.offsets[r + 1]) - static_cast<long>(base);
+  size_t base;
+  long len;
+  float *out_row;
+  if (a.slot) {
+    base = static_cast<size_t>(a.slot[r]) * a.sample_stride;
+    len = a.len[r];
+    out_row = a.out + static_cast<size_t>(a.slot[r]) * a.out_stride;
+  } else {
+    base = a.offsets[r];
+    len = static_cast<long>(a.offsets[r + 1]) - static_cast<long>(base);
+    out_row = a.out + static_cast<size_t>(r) * a.maxev;
+  }
   if (len < 0 || len > HARU_MAX_READ_SAMPLES) {
     if (tid == 0) {
       report(a.status, HARU_EINVAL);
@@ -275,14 +294,21 @@ __global__ void __launch_bounds__(kEvThreads, 4) detect_kernel(EvArgs a) {
   const int nb = s_nb;
   int K = n > 0 ? nb + 1 - a.trim : 0;  // events after the trim (an empty read has none)
   K = K < 0 ? 0 : (K > a.maxev ? a.maxev : K);
+  if (a.final_limit) {  // slot mode: keep the events whose closing boundary is final
+    const int lim = a.final_limit[r];
+    while (K > 0) {
+      const int e = a.trim + K - 1;
+      if ((e + 1 <= nb ? bounds[e] : n) <= lim) break;
+      --K;
+    }
+  }
   for (int k = tid; k < K; k += kEvThreads) {
     const int e = a.trim + k;  // e + 1 <= need: both ends are stored boundaries (or 0, n)
     const int lo = e == 0 ? 0 : bounds[e - 1];
     const int hi = e + 1 <= nb ? bounds[e] : n;
     long long s = 0;
     for (int i = lo; i < hi; ++i) s += x[i];
-    a.out[static_cast<size_t>(r) * a.maxev + k] =
-        __double2float_rn(__ddiv_rn(static_cast<double>(s), static_cast<double>(hi - lo)));
+    out_row[k] = __double2float_rn(__ddiv_rn(static_cast<double>(s), static_cast<double>(hi - lo)));
   }
   if (tid == 0) a.counts[r] = static_cast<uint32_t>(K);
 }
@@ -375,12 +401,54 @@ cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uin
   a.out = strided;
   a.counts = counts;
   a.status = status;
+  a.slot = nullptr;
+  a.len = nullptr;
+  a.final_limit = nullptr;
+  a.sample_stride = a.out_stride = 0;
   detect_kernel<<<nreads, kEvThreads, smem, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   scan_kernel<<<1, 1024, 0, s>>>(counts, nreads, ev_off);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   compact_kernel<<<(nreads + 7) / 8, 256, 0, s>>>(strided, a.maxev, counts, ev_off, nreads, ev_csr);
+  return cudaGetLastError();
+}
+
+// Detection over serving slots (one launch for every read with new samples):
+// read r = 0..nreads-1 has len[r] samples in slot slot[r] of `samples`
+// (sample_stride per slot); its query events go to slot slot[r] of `events`
+// (event_stride floats per slot) and counts[r] is how many of them are
+// final (closing boundary at or before final_limit[r]).
+cudaError_t enqueue_events_slots(const int16_t *samples, int sample_stride, const uint32_t *slot, const uint32_t *len,
+                                 const int *final_limit, uint32_t nreads, const haru_event_params &p, float *events,
+                                 int event_stride, uint32_t *counts, int *status, cudaStream_t s) {
+  if (nreads == 0) return cudaSuccess;
+  const int need = static_cast<int>(p.trim_events + p.max_events);
+  const size_t smem = detect_smem_bytes(need);
+  cudaError_t e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  EvArgs a;
+  a.samples = samples;
+  a.offsets = nullptr;
+  a.nreads = nreads;
+  a.w1 = p.window_short;
+  a.w2 = p.window_long;
+  a.tau1sq = static_cast<unsigned long long>(p.threshold_short_centi) * p.threshold_short_centi;
+  a.tau2sq = static_cast<unsigned long long>(p.threshold_long_centi) * p.threshold_long_centi;
+  a.tau1f = static_cast<float>(a.tau1sq) / 10000.0f;
+  a.tau2f = static_cast<float>(a.tau2sq) / 10000.0f;
+  a.trim = static_cast<int>(p.trim_events);
+  a.maxev = static_cast<int>(p.max_events);
+  a.out = events;
+  a.counts = counts;
+  a.status = status;
+  a.slot = slot;
+  a.len = len;
+  a.final_limit = final_limit;
+  a.sample_stride = sample_stride;
+  a.out_stride = event_stride;
+  detect_kernel<<<nreads, kEvThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,15 @@
 //     a context is free, while earlier batches are still on the GPU;
 //   * finished batches are detected by event query, decided on the host
 //     (cost <= threshold) and handed to haru_stream_poll.
+// A context serves either event chunks (haru_stream_submit) or raw ADC
+// samples (haru_stream_submit_signal), fixed by its first submit. Samples go
+// to per-read device sample slots the same way; after each upload one
+// launch of the event detector covers every read with new samples and
+// writes its query events into the read's event slot, counting only the
+// events whose closing boundary is final (w_short + 2 w_long samples before
+// the newest sample, or anywhere once the read has ended). A read is
+// complete once serve_prefix final events exist, or when it ends, and then
+// goes through the same batches as an event read.
 // Every wait here is bounded: the loop sleeps at most 200 us between turns
 // and polls events without blocking.
 
@@ -29,6 +38,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <list>
+#include <unordered_set>
 
 #include "engine.h"
 
@@ -63,7 +73,8 @@ struct CopyOp {
   uint32_t count;
 };
 
-__global__ void scatter_kernel(const float *staging, const CopyOp *ops, int nops, float *slots, int slot_len) {
+template <class T>
+__global__ void scatter_kernel(const T *staging, const CopyOp *ops, int nops, T *slots, int slot_len) {
   const int op = blockIdx.x;
   if (op >= nops) return;
   const CopyOp o = ops[op];
@@ -88,9 +99,11 @@ class Server {
   explicit Server(haru_ctx *ctx) : ctx_(ctx) {}
   ~Server() { stop(); }
 
-  int start();
+  int start(int mode);
   void stop();
-  int submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t n, uint64_t t_arrival, int last);
+  int mode() const { return mode_; }
+  // ev: n floats (event mode) or n int16 samples (signal mode)
+  int submit(uint64_t read_id, uint32_t channel, const void *ev, uint32_t n, uint64_t t_arrival, int last);
   int poll(haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us);
   void stats(haru_stream_stats *out);
 
@@ -110,6 +123,22 @@ class Server {
     uint64_t t_received = 0;
     uint64_t t_queued = 0;
     uint64_t t_launched = 0;
+    // signal mode
+    std::vector<int16_t> host_smp;  // samples not yet on the device
+    uint32_t smp_dev = 0;           // samples in its sample slot
+    uint32_t smp_total = 0;         // samples accepted (<= HARU_MAX_READ_SAMPLES)
+    uint32_t smp_detected = 0;      // samples the latest finished detection covered
+    bool ended = false;             // last chunk seen (or the slot is full)
+    bool seen_last = false;         // the read's last chunk arrived
+    bool det_pending = false;       // a detection covering it is in flight
+    uint64_t t_arrival_last = 0, t_received_last = 0;  // the newest chunk's
+  };
+  // What a detection launch saw of a read (its result applies to that).
+  struct DetSnap {
+    uint64_t id;
+    uint32_t len;
+    bool ended;
+    uint64_t t_arrival, t_received;
   };
   struct BatchCtx {
     Workspace ws;
@@ -139,10 +168,12 @@ class Server {
     uint32_t channel;
     uint32_t n;
     int last;
-    float ev[1];  // n events (allocated past the struct)
+    float ev[1];  // n events, or n int16 samples in signal mode (allocated past the struct)
   };
 
   void worker();
+  int turn_detect();
+  void reject(std::unordered_map<uint64_t, Read>::iterator it);
   void drain_intake();
   void take_chunk(const Chunk *c);
   int turn_upload();
@@ -172,6 +203,13 @@ class Server {
   }
   std::atomic<size_t> intake_events_{0};
   std::unordered_map<uint64_t, Read> reads_;
+  // reads decided before their last chunk: later chunks are dropped, and the
+  // entry goes when the last chunk arrives (a flow cell keeps delivering a
+  // read's signal after the decision prefix)
+  std::unordered_set<uint64_t> decided_;
+  void forget(const Read &r) {  // worker, under mu_: the read leaves reads_ decided
+    if (!r.seen_last) decided_.insert(r.id);
+  }
   std::deque<uint64_t> admit_q_;        // reads waiting for a slot
   std::deque<uint64_t> ready_q_;        // admitted reads with complete prefix, uploaded
   std::vector<int> free_slots_;
@@ -217,6 +255,22 @@ class Server {
   std::vector<CopyOp> ops_;
   std::vector<uint64_t> finished_;
   std::vector<haru_result> res_;
+  std::vector<CopyOp> ops16_;
+  // signal mode: sample slots, staging, and one detection launch in flight
+  int mode_ = 0;  // 0 events, 1 raw samples
+  haru_event_params evp_{};
+  int margin_ = 0;               // samples past a boundary before it is final: w_short + 2 w_long
+  int16_t *d_smp_ = nullptr;     // [nslots][HARU_MAX_READ_SAMPLES]
+  int16_t *h_stage16_ = nullptr, *d_stage16_ = nullptr;
+  CopyOp *h_ops16_ = nullptr, *d_ops16_ = nullptr;
+  size_t stage16_cap_ = 0;
+  uint32_t *h_det_slot_ = nullptr, *h_det_len_ = nullptr, *h_det_cnt_ = nullptr;  // pinned
+  int *h_det_lim_ = nullptr;
+  uint32_t *d_det_slot_ = nullptr, *d_det_len_ = nullptr, *d_det_cnt_ = nullptr;
+  int *d_det_lim_ = nullptr, *d_det_status_ = nullptr;
+  cudaEvent_t det_done_ = nullptr;
+  bool det_busy_ = false;
+  std::vector<DetSnap> det_snap_;
   LaunchCfg lc_;
   RefView ref_;
 
@@ -245,8 +299,9 @@ class Server {
   }
 };
 
-int Server::start() {
+int Server::start(int mode) {
   const haru_config &c = ctx_->cfg;
+  mode_ = mode;
   prefix_ = c.serve_prefix ? static_cast<int>(c.serve_prefix) : 250;
   if (prefix_ < 1 || prefix_ > HARU_MAX_QUERY) return HARU_EINVAL;
   slot_len_ = (prefix_ + 31) / 32 * 32;
@@ -254,8 +309,18 @@ int Server::start() {
   spin_ns_ = c.serve_spin_us < 0 ? 0 : 1000ull * static_cast<uint64_t>(c.serve_spin_us ? c.serve_spin_us : 2000);
   precision_ = c.serve_precision == HARU_FP32 ? HARU_FP32 : HARU_INT16;
   threshold_ = c.threshold;
+  if (mode_ == 1) {
+    evp_ = c.serve_events;
+    if (evp_.window_short == 0 && evp_.window_long == 0) event_params_default(&evp_);
+    evp_.max_events = static_cast<uint32_t>(prefix_);  // the query is the decision prefix
+    if (!event_params_valid(evp_)) return HARU_EINVAL;
+    margin_ = evp_.window_short + 2 * evp_.window_long;
+  }
   const size_t budget = c.serve_budget_bytes ? c.serve_budget_bytes : (64u << 20);
-  nslots_ = static_cast<int>(std::min<size_t>(budget / (static_cast<size_t>(slot_len_) * sizeof(float)), 1u << 22));
+  // an admitted read holds an event slot, and in signal mode a sample slot too
+  const size_t per_slot = static_cast<size_t>(slot_len_) * sizeof(float) +
+                          (mode_ == 1 ? static_cast<size_t>(HARU_MAX_READ_SAMPLES) * sizeof(int16_t) : 0);
+  nslots_ = static_cast<int>(std::min<size_t>(budget / per_slot, 1u << 22));
   if (nslots_ < 1) return HARU_ENOMEM;
   lc_ = ctx_->launch_cfg();
   ref_ = ctx_->ref_view();
@@ -270,6 +335,26 @@ int Server::start() {
   if (e == cudaSuccess) e = cudaMallocHost(&h_ops_, ops_cap_ * sizeof(CopyOp));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&up_stream_, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&up_done_, cudaEventDisableTiming);
+  if (mode_ == 1) {
+    stage16_cap_ = std::min<size_t>(static_cast<size_t>(std::max(nslots_, 64)) * 1024, (16u << 20) / sizeof(int16_t));
+    const size_t nd = static_cast<size_t>(nslots_);
+    if (e == cudaSuccess) e = cudaMalloc(&d_smp_, nd * HARU_MAX_READ_SAMPLES * sizeof(int16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_stage16_, stage16_cap_ * sizeof(int16_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_stage16_, stage16_cap_ * sizeof(int16_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_ops16_, ops_cap_ * sizeof(CopyOp));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_ops16_, ops_cap_ * sizeof(CopyOp));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_det_slot_, nd * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_det_len_, nd * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_det_lim_, nd * sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&h_det_cnt_, nd * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_det_slot_, nd * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_det_len_, nd * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_det_lim_, nd * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_det_cnt_, nd * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_det_status_, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&det_done_, cudaEventDisableTiming);
+    det_snap_.reserve(nd);
+  }
   const int nb = 3;
   batches_.resize(nb);
   for (auto &b : batches_) {
@@ -332,6 +417,18 @@ void Server::stop() {
   if (h_ops_) cudaFreeHost(h_ops_);
   if (up_done_) cudaEventDestroy(up_done_);
   if (up_stream_) cudaStreamDestroy(up_stream_);
+  void *dsig[] = {d_smp_, d_stage16_, d_ops16_, d_det_slot_, d_det_len_, d_det_lim_, d_det_cnt_, d_det_status_};
+  for (void *q : dsig)
+    if (q) cudaFree(q);
+  void *hsig[] = {h_stage16_, h_ops16_, h_det_slot_, h_det_len_, h_det_lim_, h_det_cnt_};
+  for (void *q : hsig)
+    if (q) cudaFreeHost(q);
+  if (det_done_) cudaEventDestroy(det_done_);
+  d_smp_ = d_stage16_ = h_stage16_ = nullptr;
+  d_ops16_ = h_ops16_ = nullptr;
+  d_det_slot_ = d_det_len_ = d_det_cnt_ = h_det_slot_ = h_det_len_ = h_det_cnt_ = nullptr;
+  d_det_lim_ = d_det_status_ = h_det_lim_ = nullptr;
+  det_done_ = nullptr;
   d_slots_ = d_stage_ = h_stage_ = nullptr;
   d_ops_ = h_ops_ = nullptr;
   up_done_ = nullptr;
@@ -344,22 +441,24 @@ void Server::fail(int code) {
   cv_out_.notify_all();
 }
 
-int Server::submit(uint64_t read_id, uint32_t channel, const float *ev, uint32_t n, uint64_t t_arrival, int last) {
+int Server::submit(uint64_t read_id, uint32_t channel, const void *ev, uint32_t n, uint64_t t_arrival, int last) {
   {
     std::lock_guard<std::mutex> lk(out_mu_);
     if (error_ != HARU_OK) return error_;
   }
   if (n > 0 && !ev) return HARU_EINVAL;
   free_list(garbage_.exchange(nullptr, std::memory_order_acquire));
-  if (intake_events_.load() + host_events_.load() + n > stage_cap_ * 4) return HARU_EBUSY;
-  Chunk *c = static_cast<Chunk *>(std::malloc(offsetof(Chunk, ev) + sizeof(float) * std::max<uint32_t>(n, 1)));
+  const size_t cap = mode_ == 1 ? stage16_cap_ : stage_cap_;
+  if (intake_events_.load() + host_events_.load() + n > cap * 4) return HARU_EBUSY;
+  const size_t elem = mode_ == 1 ? sizeof(int16_t) : sizeof(float);
+  Chunk *c = static_cast<Chunk *>(std::malloc(offsetof(Chunk, ev) + std::max<size_t>(elem * n, sizeof(float))));
   if (!c) return HARU_ENOMEM;
   c->read_id = read_id;
   c->t_arrival = t_arrival;
   c->channel = channel;
   c->n = n;
   c->last = last;
-  if (n) std::memcpy(c->ev, ev, sizeof(float) * n);
+  if (n) std::memcpy(c->ev, ev, elem * n);
   intake_events_ += n;
   c->t_received = now_ns();
   Chunk *head = intake_.load(std::memory_order_relaxed);
@@ -399,8 +498,44 @@ void Server::drain_intake() {
   if (dt > max_drain_) max_drain_ = dt;
 }
 
-// Worker, under mu_: append a chunk's events to its read (up to the prefix).
+// Worker, under mu_: decide a read without the GPU (its prefix has no
+// z-score or no alignment) and drop it.
+void Server::reject(std::unordered_map<uint64_t, Read>::iterator it) {
+  Read &r = it->second;
+  haru_result o;
+  std::memset(&o, 0, sizeof(o));
+  o.read_id = r.id;
+  o.channel = r.channel;
+  o.status = HARU_EINVAL;
+  o.events = r.total;
+  o.end_col = -1;
+  o.t_arrival_ns = r.t_arrival;
+  o.t_done_ns = now_ns();
+  o.t_received_ns = r.t_received;
+  host_events_ -= r.host.size() + r.host_smp.size();
+  if (r.slot >= 0) free_slots_.push_back(r.slot);
+  auto qi = std::find(admit_q_.begin(), admit_q_.end(), r.id);
+  if (qi != admit_q_.end()) admit_q_.erase(qi);
+  forget(r);
+  reads_.erase(it);
+  {
+    std::lock_guard<std::mutex> lo(out_mu_);
+    push_out(o);
+  }
+  n_decided_++;
+  cv_out_.notify_all();
+}
+
+// Worker, under mu_: append a chunk to its read: events up to the prefix, or
+// samples up to a sample slot.
 void Server::take_chunk(const Chunk *c) {
+  if (!decided_.empty()) {
+    auto d = decided_.find(c->read_id);
+    if (d != decided_.end()) {
+      if (c->last) decided_.erase(d);
+      return;
+    }
+  }
   auto it = reads_.find(c->read_id);
   if (it == reads_.end()) {
     Read r;
@@ -411,7 +546,20 @@ void Server::take_chunk(const Chunk *c) {
     n_submitted_++;
   }
   Read &r = it->second;
+  if (c->last) r.seen_last = true;
   if (r.complete) return;  // later chunks of a decided prefix are not needed
+  if (mode_ == 1) {
+    if (r.ended) return;
+    const int16_t *smp = reinterpret_cast<const int16_t *>(c->ev);
+    const uint32_t take = std::min<uint32_t>(c->n, static_cast<uint32_t>(HARU_MAX_READ_SAMPLES) - r.smp_total);
+    r.host_smp.insert(r.host_smp.end(), smp, smp + take);
+    host_events_ += take;
+    r.smp_total += take;
+    r.t_arrival_last = c->t_arrival;
+    r.t_received_last = c->t_received;
+    if (c->last || r.smp_total >= static_cast<uint32_t>(HARU_MAX_READ_SAMPLES)) r.ended = true;
+    return;
+  }
   const float *ev = c->ev;
   const uint32_t take = std::min<uint32_t>(c->n, static_cast<uint32_t>(prefix_) - r.total);
   for (uint32_t i = 0; i < take; ++i) {
@@ -428,30 +576,8 @@ void Server::take_chunk(const Chunk *c) {
     r.complete = true;
     r.t_arrival = c->t_arrival;
     r.t_received = c->t_received;
-    if (r.bad || r.total < 2 || !(r.hi > r.lo) || r.total > static_cast<uint32_t>(ref_.N)) {
-      // no z-score or no alignment for this prefix: decided (eject) without the GPU
-      haru_result o;
-      std::memset(&o, 0, sizeof(o));
-      o.read_id = r.id;
-      o.channel = r.channel;
-      o.status = HARU_EINVAL;
-      o.events = r.total;
-      o.end_col = -1;
-      o.t_arrival_ns = r.t_arrival;
-      o.t_done_ns = now_ns();
-      o.t_received_ns = r.t_received;
-      host_events_ -= r.host.size();
-      if (r.slot >= 0) free_slots_.push_back(r.slot);
-      auto qi = std::find(admit_q_.begin(), admit_q_.end(), r.id);
-      if (qi != admit_q_.end()) admit_q_.erase(qi);
-      reads_.erase(it);
-      {
-        std::lock_guard<std::mutex> lo(out_mu_);
-        push_out(o);
-      }
-      n_decided_++;
-      cv_out_.notify_all();
-    }
+    // no z-score or no alignment for this prefix: decided (eject) without the GPU
+    if (r.bad || r.total < 2 || !(r.hi > r.lo) || r.total > static_cast<uint32_t>(ref_.N)) reject(it);
   }
 }
 
@@ -517,6 +643,7 @@ int Server::turn_upload() {
   size_t staged = 0;
   std::vector<uint64_t> &finished = finished_;
   finished.clear();
+  ops16_.clear();
   {
     std::lock_guard<std::mutex> lk(mu_);
     while (!admit_q_.empty() && !free_slots_.empty()) {
@@ -527,6 +654,19 @@ int Server::turn_upload() {
     }
     for (auto &kv : reads_) {
       Read &r = kv.second;
+      if (mode_ == 1) {  // raw samples to the read's sample slot
+        if (r.slot < 0 || r.host_smp.empty()) continue;
+        const size_t cnt = r.host_smp.size();
+        if (staged + cnt > stage16_cap_ || ops16_.size() >= ops_cap_) break;
+        std::memcpy(h_stage16_ + staged, r.host_smp.data(), cnt * sizeof(int16_t));
+        ops16_.push_back(CopyOp{static_cast<uint32_t>(r.slot), r.smp_dev, static_cast<uint32_t>(staged),
+                                static_cast<uint32_t>(cnt)});
+        staged += cnt;
+        r.smp_dev += static_cast<uint32_t>(cnt);
+        host_events_ -= cnt;
+        r.host_smp.clear();
+        continue;
+      }
       if (r.slot < 0 || r.host.empty()) continue;
       const size_t cnt = r.host.size();
       if (staged + cnt > stage_cap_ || ops.size() >= ops_cap_) break;
@@ -542,10 +682,32 @@ int Server::turn_upload() {
     // reads completed earlier whose events were already on the device
     for (auto &kv : reads_) {
       Read &r = kv.second;
-      if (r.slot >= 0 && r.complete && !r.queued && r.host.empty() && r.on_device == r.total &&
+      if (mode_ == 0 && r.slot >= 0 && r.complete && !r.queued && r.host.empty() && r.on_device == r.total &&
           std::find(finished.begin(), finished.end(), r.id) == finished.end())
         finished.push_back(r.id);
     }
+  }
+  if (!ops16_.empty()) {
+    std::memcpy(h_ops16_, ops16_.data(), ops16_.size() * sizeof(CopyOp));
+    cudaError_t e = cudaMemcpyAsync(d_stage16_, h_stage16_, staged * sizeof(int16_t), cudaMemcpyHostToDevice,
+                                    up_stream_);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_ops16_, h_ops16_, ops16_.size() * sizeof(CopyOp), cudaMemcpyHostToDevice, up_stream_);
+    if (e == cudaSuccess) {
+      scatter_kernel<int16_t><<<static_cast<unsigned>(ops16_.size()), 128, 0, up_stream_>>>(
+          d_stage16_, d_ops16_, static_cast<int>(ops16_.size()), d_smp_, HARU_MAX_READ_SAMPLES);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(up_done_, up_stream_);
+    const uint64_t ts = now_ns();
+    if (e == cudaSuccess) {
+      while ((e = cudaEventQuery(up_done_)) == cudaErrorNotReady) {
+        if (now_ns() - ts > lc_.wait_ns) return HARU_ETIMEDOUT;
+      }
+    }
+    const uint64_t dts = now_ns() - ts;
+    if (dts > max_sync_) max_sync_ = dts;
+    if (e != cudaSuccess) return HARU_ECUDA;
   }
   if (!ops.empty()) {
     std::memcpy(h_ops_, ops.data(), ops.size() * sizeof(CopyOp));
@@ -554,9 +716,8 @@ int Server::turn_upload() {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_ops_, h_ops_, ops.size() * sizeof(CopyOp), cudaMemcpyHostToDevice, up_stream_);
     if (e == cudaSuccess) {
-      scatter_kernel<<<static_cast<unsigned>(ops.size()), 64, 0, up_stream_>>>(d_stage_, d_ops_,
-                                                                               static_cast<int>(ops.size()),
-                                                                               d_slots_, slot_len_);
+      scatter_kernel<float><<<static_cast<unsigned>(ops.size()), 64, 0, up_stream_>>>(
+          d_stage_, d_ops_, static_cast<int>(ops.size()), d_slots_, slot_len_);
       e = cudaGetLastError();
     }
     // the staging buffers are reused next turn: wait for this transfer
@@ -586,6 +747,80 @@ int Server::turn_upload() {
       }
     }
   }
+  return HARU_OK;
+}
+
+// Signal mode: take the counts of a finished detection launch (reads with
+// serve_prefix final events, or ended reads, are complete and queued), then
+// launch the detector over every admitted read with samples it has not
+// covered. One launch is in flight at a time; the samples it reads were
+// uploaded (and waited for) before it, and later uploads write past them.
+int Server::turn_detect() {
+  if (mode_ != 1) return HARU_OK;
+  if (det_busy_) {
+    const cudaError_t q = cudaEventQuery(det_done_);
+    if (q == cudaErrorNotReady) return HARU_OK;
+    if (q != cudaSuccess) return HARU_ECUDA;
+    det_busy_ = false;
+    std::lock_guard<std::mutex> lk(mu_);
+    const uint64_t tq = now_ns();
+    for (size_t i = 0; i < det_snap_.size(); ++i) {
+      const DetSnap &d = det_snap_[i];
+      auto it = reads_.find(d.id);
+      if (it == reads_.end()) continue;
+      Read &r = it->second;
+      r.det_pending = false;
+      r.smp_detected = d.len;
+      const uint32_t cnt = h_det_cnt_[i];
+      if (cnt < static_cast<uint32_t>(prefix_) && !d.ended) continue;
+      r.complete = true;
+      r.t_arrival = d.t_arrival;
+      r.t_received = d.t_received;
+      r.total = cnt;
+      r.on_device = cnt;
+      if (cnt < 2) {
+        reject(it);
+        continue;
+      }
+      r.queued = true;
+      r.t_queued = tq;
+      ready_q_.push_back(r.id);
+    }
+  }
+  uint32_t n = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu_);
+    det_snap_.clear();
+    // a live read can only complete once it has (trim + prefix) events of at
+    // least w_short + 1 samples each, plus the finality margin
+    const uint32_t least = (evp_.trim_events + static_cast<uint32_t>(prefix_)) *
+                               static_cast<uint32_t>(evp_.window_short + 1) + static_cast<uint32_t>(margin_);
+    for (auto &kv : reads_) {
+      Read &r = kv.second;
+      if (r.slot < 0 || r.complete || r.det_pending || !r.host_smp.empty()) continue;
+      const bool ended = r.ended && r.smp_dev == r.smp_total;
+      if (!ended && (r.smp_dev <= r.smp_detected || r.smp_dev < least)) continue;
+      h_det_slot_[n] = static_cast<uint32_t>(r.slot);
+      h_det_len_[n] = r.smp_dev;
+      h_det_lim_[n] = ended ? static_cast<int>(r.smp_dev) : static_cast<int>(r.smp_dev) - margin_;
+      det_snap_.push_back(DetSnap{r.id, r.smp_dev, ended, r.t_arrival_last, r.t_received_last});
+      r.det_pending = true;
+      ++n;
+    }
+  }
+  if (n == 0) return HARU_OK;
+  cudaStream_t s = up_stream_;
+  cudaError_t e = cudaMemcpyAsync(d_det_slot_, h_det_slot_, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_det_len_, h_det_len_, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_det_lim_, h_det_lim_, n * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_det_status_, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = enqueue_events_slots(d_smp_, HARU_MAX_READ_SAMPLES, d_det_slot_, d_det_len_, d_det_lim_, n, evp_, d_slots_,
+                             slot_len_, d_det_cnt_, d_det_status_, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_det_cnt_, d_det_cnt_, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaEventRecord(det_done_, s);
+  if (e != cudaSuccess) return HARU_ECUDA;
+  det_busy_ = true;
   return HARU_OK;
 }
 
@@ -687,6 +922,7 @@ int Server::turn_complete() {
         const uint64_t host_share = stage > exec_ns ? stage - exec_ns : 0;
         if (host_share > max_notice_) max_notice_ = host_share;
         free_slots_.push_back(r.slot);
+        forget(r);
         reads_.erase(it);
       }
     }
@@ -731,6 +967,7 @@ void Server::worker() {
     int rc = turn_complete();
     const uint64_t t1 = now_ns();
     if (rc == HARU_OK) rc = turn_upload();
+    if (rc == HARU_OK) rc = turn_detect();
     const uint64_t t2 = now_ns();
     if (rc == HARU_OK) rc = turn_launch();
     const uint64_t t3 = now_ns();
@@ -742,7 +979,7 @@ void Server::worker() {
       std::unique_lock<std::mutex> lk(mu_);
       bool busy = false;
       for (auto &b : batches_) busy = busy || b.busy;
-      const bool work = !ready_q_.empty() || host_events_ > 0 || intake_.load() != nullptr;
+      const bool work = !ready_q_.empty() || host_events_ > 0 || intake_.load() != nullptr || det_busy_;
       if (work || busy || !reads_.empty()) t_work = t3;
       // poll (no sleep) while reads are in progress or within the spin window
       if (!work && t3 - t_work >= spin_ns_)
@@ -759,10 +996,12 @@ void server_destroy(Server *s) { delete s; }
 
 }  // namespace haru
 
-extern "C" {
+namespace {
 
-int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const float *events, uint32_t n,
-                       uint64_t t_arrival_ns, int last_chunk) {
+// The context's serving loop, started in `mode` (0 events, 1 raw samples) by
+// the first submit; a submit of the other kind is HARU_EINVAL.
+int serve_submit(haru_ctx *ctx, int mode, uint64_t read_id, uint32_t channel, const void *data, uint32_t n,
+                 uint64_t t_arrival_ns, int last_chunk) {
   if (!ctx) return HARU_EINVAL;
   haru::Server *srv = nullptr;
   {
@@ -772,7 +1011,7 @@ int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const 
     if (!ctx->server) {
       auto *s = new (std::nothrow) haru::Server(ctx);
       if (!s) return HARU_ENOMEM;
-      const int rc = s->start();
+      const int rc = s->start(mode);
       if (rc != HARU_OK) {
         delete s;
         return rc;
@@ -781,7 +1020,22 @@ int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const 
     }
     srv = ctx->server;
   }
-  return srv->submit(read_id, channel, events, n, t_arrival_ns, last_chunk);
+  if (srv->mode() != mode) return HARU_EINVAL;
+  return srv->submit(read_id, channel, data, n, t_arrival_ns, last_chunk);
+}
+
+}  // namespace
+
+extern "C" {
+
+int haru_stream_submit(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const float *events, uint32_t n,
+                       uint64_t t_arrival_ns, int last_chunk) {
+  return serve_submit(ctx, 0, read_id, channel, events, n, t_arrival_ns, last_chunk);
+}
+
+int haru_stream_submit_signal(haru_ctx *ctx, uint64_t read_id, uint32_t channel, const int16_t *samples, uint32_t n,
+                              uint64_t t_arrival_ns, int last_chunk) {
+  return serve_submit(ctx, 1, read_id, channel, samples, n, t_arrival_ns, last_chunk);
 }
 
 int haru_stream_poll(haru_ctx *ctx, haru_result *out, uint32_t max, uint32_t *n_out, uint32_t timeout_us) {

@@ -270,11 +270,13 @@ def signal_workload(name: str, nreads: int | None = None, seed: int | None = Non
     sars_signal_32x250      32 reads whose trimmed prefixes hold ~250 events
     sars_signal_uneven_8192 8,192 reads, genome levels uniform in [100, 500]
                             plus a margin, half on-target
+    sars_signal_heldout_1024 1,024 reads as sars_signal_32x250 (threshold set)
     """
     model = pore_model(6)
     g_on = genome(SARS_COV_2_BASES, SEED_GENOME_ON)
     g_off = genome(SARS_COV_2_BASES, SEED_GENOME_OFF)
-    table = {"sars_signal_32x250": (32, 110, None), "sars_signal_uneven_8192": (8192, 111, (100, 500))}
+    table = {"sars_signal_32x250": (32, 110, None), "sars_signal_uneven_8192": (8192, 111, (100, 500)),
+             "sars_signal_heldout_1024": (1024, 113, None)}
     n_default, s_default, span = table[name]
     n = n_default if nreads is None else nreads
     s = s_default if seed is None else seed
@@ -360,8 +362,8 @@ class FlowCellChunk:
     t: float  # seconds since the start of the run
     read_id: int
     channel: int
-    events: np.ndarray  # float32 raw currents
-    last: bool  # this chunk completes the decision prefix
+    events: np.ndarray  # float32 raw event currents, or int16 ADC samples (raw-signal schedules)
+    last: bool  # this chunk completes the decision prefix (raw-signal schedules: ends the read)
 
 
 def flowcell_schedule(channels: int, duration_s: float, seed: int, prefix_events: int = 250,
@@ -417,6 +419,60 @@ def flowcell_schedule(channels: int, duration_s: float, seed: int, prefix_events
     ev = np.concatenate(prefixes).astype(np.float32) if prefixes else np.zeros(0, np.float32)
     q = Queries(ev, off, np.array(on_list, dtype=bool), np.array(truth, dtype=np.int64))
     return chunks, q
+
+
+def flowcell_signal_schedule(channels: int, duration_s: float, seed: int, prefix_events: int = 250,
+                             chunk_s: float = 0.1, idle_mean_s: float = 0.5, accept_mean_s: float = 10.0,
+                             on_fraction: float = 0.2):
+    """Open-loop arrival schedule of a simulated flow cell that delivers raw
+    samples: as flowcell_schedule, but every read is a raw int16 ADC signal
+    (the adaptor, then ~1.25 x prefix_events + 16 pore-model levels; see
+    make_signal_reads) delivered in chunks of SAMPLE_RATE_HZ * chunk_s
+    samples; the read's last chunk carries `last`. A read on the target
+    genome keeps the channel busy for Exp(accept_mean_s) more seconds after
+    its signal ends; other reads free it at once.
+
+    Returns (chunks sorted by time, SignalReads of every read's whole
+    signal indexed by read_id)."""
+    rng = np.random.default_rng(seed)
+    model = pore_model(6)
+    g_on = genome(SARS_COV_2_BASES, SEED_GENOME_ON)
+    g_off = genome(SARS_COV_2_BASES, SEED_GENOME_OFF)
+    s_on, s_off = _Strands(g_on, model, 6), _Strands(g_off, model, 6)
+    per_chunk = int(round(SAMPLE_RATE_HZ * chunk_s))
+    n_levels = prefix_events + prefix_events // 4 + 16
+    chunks, parts, poss, on_list = [], [], [], []
+    read_id = 0
+    for ch in range(channels):
+        t = rng.exponential(idle_mean_s)
+        while t < duration_s:
+            on = bool(rng.random() < on_fraction)
+            src = s_on if on else s_off
+            strand = int(rng.integers(0, 2))
+            levels = src.fwd if strand == 0 else src.rev
+            start = int(rng.integers(0, levels.shape[0] - n_levels))
+            idx = np.arange(start, start + n_levels)
+            idx = idx[rng.random(idx.shape[0]) >= 0.1]
+            ad = rng.normal(75.0, 8.0, size=ADAPTOR_LEVELS)
+            a_smp, a_pos = _signal(rng, ad, np.full(ADAPTOR_LEVELS, -1, np.int64), 4, 10.0, 2.5)
+            gpos = (strand * src.fwd.shape[0] + idx) if on else np.full(idx.shape[0], -1, np.int64)
+            g_smp, g_pos = _signal(rng, levels[idx], gpos.astype(np.int64), 4, 10.0, 2.5)
+            smp = np.concatenate([a_smp, g_smp])
+            n_chunks = -(-smp.shape[0] // per_chunk)
+            for c in range(n_chunks):
+                chunks.append(FlowCellChunk(t + (c + 1) * chunk_s, read_id, ch, smp[c * per_chunk:(c + 1) * per_chunk],
+                                            c == n_chunks - 1))
+            parts.append(smp)
+            poss.append(np.concatenate([a_pos, g_pos]))
+            on_list.append(on)
+            t = t + n_chunks * chunk_s + (rng.exponential(accept_mean_s) if on else 0.0) + rng.exponential(idle_mean_s)
+            read_id += 1
+    chunks.sort(key=lambda c: (c.t, c.channel))
+    off = np.zeros(read_id + 1, dtype=np.uint32)
+    off[1:] = np.cumsum([p.shape[0] for p in parts])
+    smp = np.concatenate(parts).astype(np.int16) if parts else np.zeros(0, np.int16)
+    pos = np.concatenate(poss).astype(np.int64) if poss else np.zeros(0, np.int64)
+    return chunks, SignalReads(smp, off, np.array(on_list, dtype=bool), pos)
 
 
 def replay(chunks, submit, speed: float = 1.0, stop=None):

@@ -33,7 +33,7 @@ def ref():
     return oracle.ref_levels(synth.genome(synth.SARS_COV_2_BASES, synth.SEED_GENOME_ON), synth.pore_model(6), 6)
 
 
-def run_schedule(ctx, chunks, speed):
+def run_schedule(ctx, chunks, speed, signal=False):
     results = []
     done = threading.Event()
 
@@ -45,6 +45,8 @@ def run_schedule(ctx, chunks, speed):
     th.start()
 
     def submit(c, t):
+        if signal:
+            return ctx.stream_submit_signal(c.read_id, c.channel, c.events, t, c.last)
         return ctx.stream_submit(c.read_id, c.channel, c.events, t, c.last)
 
     synth.replay(chunks, submit, speed=speed)
@@ -125,3 +127,38 @@ def test_stage_counters_and_idle_sleeping_worker(haru, ref):
     assert all(r.t_arrival_ns <= r.t_received_ns <= r.t_done_ns for r in got.values())
     assert st["reads_decided"] == len(got) and st["batches"] >= 1
     assert st["max_gpu_ns"] > 0 and st["max_turn_gap_ns"] > 0
+
+
+@pytest.mark.parametrize("prec,budget", [(1, 64 << 20), (0, 64 << 20), (1, 12 * 34 * 1024)])
+def test_signal_decisions_match_batch(haru, ref, prec, budget):
+    """A flow cell that delivers raw samples: every decision equals the
+    raw-signal batch path on the read's whole signal (detection's final
+    events do not depend on how the signal was chunked) and the oracle's
+    events through the oracle's sDTW; a small budget (12 slots) makes reads
+    wait for admission."""
+    chunks, R = synth.flowcell_signal_schedule(48, 4.0, seed=205)
+    with haru.Context(serve_precision=prec, serve_budget_bytes=budget, threshold=60.0) as ctx:
+        ctx.ref_load(ref)
+        res = run_schedule(ctx, chunks, speed=4.0, signal=True)
+        stats = ctx.stream_stats()
+        assert len(res) == R.nreads, (len(res), R.nreads, stats)
+        by_id = {r.read_id: r for r in res}
+        assert sorted(by_id) == list(range(R.nreads))
+        assert all(r.status == 0 for r in res)
+        cost, col, nev = ctx.sdtw_batch_signal(prec, R.samples, R.offsets)
+        # a context serving samples refuses event chunks
+        assert ctx.stream_submit(10 ** 9, 0, np.ones(4, np.float32), 0, True) == haru.HARU_EINVAL
+    if budget < 64 << 20:
+        assert stats["slots"] == 12
+    thr = np.floor(60.0 * 64) / 64 if prec == 1 else 60.0
+    for i in range(R.nreads):
+        r = by_id[i]
+        assert r.cost == cost[i] and r.end_col == col[i] and r.events == nev[i], i
+        assert r.decision == int(r.cost <= thr)
+        assert r.t_done_ns >= r.t_arrival_ns
+    oev, ooff = oracle.signal_events(R.samples, R.offsets)
+    np.testing.assert_array_equal(nev, np.diff(ooff.astype(np.int64)))
+    o = oracle.batch(oracle.PREC_I16 if prec == 1 else oracle.PREC_F32, ref, oev, ooff)
+    np.testing.assert_array_equal(col, o.col)
+    np.testing.assert_array_equal(cost.astype(np.float64), o.cost if prec == 1 else
+                                  o.cost.astype(np.float32).astype(np.float64))
