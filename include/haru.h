@@ -397,7 +397,10 @@ int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, c
  * haru_sdtw_batch; HARU_ON_DEVICE and HARU_RAW are honoured) under every
  * combination of warps per CTA {4, 8, 12}, tile width {2048, 4096, 8192, 16384}
  * and work-unit target {1 (no reference segments), auto / 2, auto,
- * 2 x auto}, keep the fastest (minimum of two timed runs each) in the context's configuration
+ * 2 x auto}, then, at the best of those, every stack_short rule (auto,
+ * always, never: 32-lane strips or stacked 16-lane strips of twice the rows
+ * per lane for queries of <= 256 events), keep the fastest (minimum of two
+ * timed runs each) in the context's configuration
  * for later batches, and copy the resulting configuration to *chosen (may be
  * NULL). The strip height is fixed by each query's length. Results of the
  * trial runs are discarded. Errors: as haru_sdtw_batch. */

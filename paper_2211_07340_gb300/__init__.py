@@ -423,7 +423,8 @@ class Context:
         check(lib().haru_autotune(self._h, int(precision), _ptr(events), _ptr(offsets), nq, flags,
                                   ctypes.byref(cfg)), "haru_autotune")
         self.config = cfg
-        return {"warps_per_cta": cfg.warps_per_cta, "tile_cols": cfg.tile_cols, "units_target": cfg.units_target}
+        return {"warps_per_cta": cfg.warps_per_cta, "tile_cols": cfg.tile_cols, "units_target": cfg.units_target,
+                "stack_short": cfg.stack_short}
 
     def probe_peak(self, precision: int) -> float:
         """Measured cells/s ceiling of the form's cell update (no data movement)."""

@@ -3,8 +3,10 @@
 //
 // Tuned: warps per CTA (queries or pairs sharing one reference tile stream),
 // reference tile width and the work-unit target (how finely sweeps are cut
-// into verified reference segments; 1 = never cut). The strip height is not
-// a free choice here: S = floor(M / 32) + 1 rows per
+// into verified reference segments; 1 = never cut), then at the best of
+// those the strip geometry of queries of <= 256 events (32-lane strips or
+// stacked 16-lane strips with twice the rows per lane). Beyond that the
+// strip height is not a free choice: S = floor(M / 32) + 1 rows per
 // lane (at most 16) is the smallest strip that holds a query with a pad row
 // on top, and a taller one only adds padding.
 
@@ -69,34 +71,49 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
   const int units_c[] = {1, auto_units / 2, auto_units, 2 * auto_units};
   float best_ms = -1.0f;
   LaunchCfg best = base;
+  // One trial: the minimum of two timed runs after one warm-up; kept if fastest.
+  auto trial = [&](const LaunchCfg &lc) {
+    if (e != cudaSuccess) return;
+    e = ws_reserve(ctx->ws, precision, nq, lc);
+    float ms_min = -1.0f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess)
+        e = ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, t_cost, t_col, lc, s, nullptr,
+                       nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && rep > 0 && (ms_min < 0.0f || ms < ms_min)) ms_min = ms;
+    }
+    int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, ctx->ws.ints + kIntStatus, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && st == HARU_OK && ms_min > 0.0f && (best_ms < 0.0f || ms_min < best_ms)) {
+      best_ms = ms_min;
+      best = lc;
+    }
+  };
+  // Launch shape first, at the context's stacking rule ...
   for (int w : warps_c)
     for (int t : tiles_c)
       for (int u : units_c) {
-        if (e != cudaSuccess) break;
         LaunchCfg lc = base;
         lc.warps = w;
         lc.tile = t;
         lc.units_target = u;
-        e = ws_reserve(ctx->ws, precision, nq, lc);
-        float ms_min = -1.0f;
-        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
-          e = cudaEventRecord(e0, s);
-          if (e == cudaSuccess)
-            e = ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, t_cost, t_col, lc, s,
-                           nullptr, nullptr);
-          if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-          float ms = 0.0f;
-          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-          if (e == cudaSuccess && rep > 0 && (ms_min < 0.0f || ms < ms_min)) ms_min = ms;
-        }
-        int st = 0;
-        if (e == cudaSuccess) e = cudaMemcpy(&st, ctx->ws.ints + kIntStatus, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && st == HARU_OK && ms_min > 0.0f && (best_ms < 0.0f || ms_min < best_ms)) {
-          best_ms = ms_min;
-          best = lc;
-        }
+        trial(lc);
       }
+  // ... then the strip geometry of short queries at that shape: 32-lane
+  // strips of S = floor(M / 32) + 1 rows per lane, or stacked 16-lane strips
+  // of floor(M / 16) + 1 rows (stack_short: auto, always, never).
+  const LaunchCfg shape = best;
+  for (int st : {0, 1, -1}) {
+    if (st == shape.stack_short) continue;
+    LaunchCfg lc = shape;
+    lc.stack_short = st;
+    trial(lc);
+  }
   cudaFree(t_ev);
   cudaFree(t_off);
   cudaFree(t_cost);
@@ -111,6 +128,7 @@ extern "C" int haru_autotune(haru_ctx *ctx, int precision, const float *events, 
   ctx->cfg.warps_per_cta = best.warps;
   ctx->cfg.tile_cols = best.tile;
   ctx->cfg.units_target = best.units_target;
+  ctx->cfg.stack_short = best.stack_short;
   if (chosen) *chosen = ctx->cfg;
   return HARU_OK;
 }
