@@ -508,16 +508,10 @@ struct StripF32Span {
         const int pu = k ? P[a][k - 1] : pup;
         const float dg = k ? G[b][k - 1] : gprev;
         const int pd = k ? P[b][k - 1] : pprev;
-        // The start of the preferred minimum predecessor: up, else diagonal,
-        // else left. Costs are non-negative floats, whose bit patterns order
-        // as unsigned integers: two DPX minima that also report whether their
-        // first operand won (ties included) pick the cost and the start.
-        bool up_wins, ud_wins;
-        const unsigned m1 = __vibmin_u32(__float_as_uint(up), __float_as_uint(dg), &up_wins);
-        const int s1 = up_wins ? pu : pd;
-        const unsigned m = __vibmin_u32(m1, __float_as_uint(G[a][k]), &ud_wins);
-        G[b][k] = __fmaf_rn(fabsf(d), W[k], __uint_as_float(m));
-        P[b][k] = ud_wins ? s1 : P[a][k];
+        const float m = fmin3f(up, dg, G[a][k]);
+        // The start of the preferred minimum predecessor: up, else diagonal, else left.
+        G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
+        P[b][k] = sel_eq(up, m, pu, sel_eq(dg, m, pd, P[a][k]));
       }
       gprev = gup;
       pprev = pup;
