@@ -415,15 +415,19 @@ def run_serving(haru, args, local, w, threshold, channels, signal=False):
                        "max_gpu_ms": st["max_gpu_ns"] / 1e6, "max_gpu_exec_ms": st["max_gpu_exec_ns"] / 1e6,
                        "max_notice_ms": st["max_notice_ns"] / 1e6, "max_drain_ms": st["max_drain_ns"] / 1e6,
                        "max_cuda_calls_ms": {k: st["max_" + k + "_ns"] / 1e6 for k in
-                                             ("upload_calls", "launch_inputs", "launch_path", "launch_results")},
+                                             ("upload_calls", "launch_inputs", "launch_path", "launch_results",
+                                              "detect_calls")},
                        "over_10ms_upload": st["slow_upload"],
                        "over_10ms_queue": st["slow_queue"], "over_10ms_gpu": st["slow_gpu"],
                        "max_upload_sync_ms": st["max_upload_sync_ns"] / 1e6,
                        "max_worker_turn_gap_ms": st["max_turn_gap_ns"] / 1e6,
                        "worst_turn_ms": {k: st["worst_turn_" + k + "_ns"] / 1e6
-                                         for k in ("complete", "upload", "launch", "wait")},
+                                         for k in ("complete", "upload", "detect", "launch", "wait")},
                        "worst_turn_switches": {"voluntary": st["worst_turn_voluntary_switches"],
-                                               "involuntary": st["worst_turn_involuntary_switches"]}},
+                                               "involuntary": st["worst_turn_involuntary_switches"]},
+                       "worst_turn_page_faults": {"minor": st["worst_turn_minor_faults"],
+                                                  "major": st["worst_turn_major_faults"]},
+                       "worst_turn_at_s": st["worst_turn_at_ns"] / 1e9, "turns_over_5ms": st["turns_over_5ms"]},
             "latency_clock": "chunk delivery that completes the prefix -> decision available (CLOCK_MONOTONIC); "
                              "library_*: the library's receipt of that chunk -> decision available"}
 
@@ -489,7 +493,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="measured seconds of the simulated flow-cell run, after the warm-up (0 = skip)")
     ap.add_argument("--serve-warm", type=float, default=5.0, help="seconds of serving before the measured span")
-    ap.add_argument("--serve-channels", type=int, default=512)
+    ap.add_argument("--serve-channels", type=int, default=512, help="event-chunk serving channels (0 = skip)")
     ap.add_argument("--serve-clock-ms", type=int, default=100,
                     help="nvidia-smi sampling period during the serving runs (0 = none)")
     ap.add_argument("--stress-channels", type=int, default=4096,
@@ -554,6 +558,7 @@ def main():
         return 5
 
     tuned = {}
+    work = {}
 
     def run_form(prec):
         sh = stream.cuda_stream
@@ -609,6 +614,7 @@ def main():
         st = ctx.last_status()
         if st != haru.HARU_OK:
             raise haru.HaruError(st, "batch")
+        work[prec] = ctx.last_stats()  # items, groups, segments and fix-ups of the last replay
         return float(np.mean(step_ms)), float(np.mean(sweep_ms)), clk.summary(), graph is not None
 
     forms = args.forms.split(",")
@@ -744,6 +750,8 @@ def main():
         "signal": signal,
         "int16_over_fp32": value / value32 if value32 == value32 else None,
         "int16_capped_queries": capped16,
+        "batch_work": {{haru.HARU_INT16: "int16", haru.HARU_FP32: "fp32", haru.HARU_INT16_ACC32: "int16_acc32"}[k]: v
+                       for k, v in work.items()},
         "prep_ms_per_step": ms16 - sweep16,
         "e2e": {"value": e2e_value, "unit": "GCUPS", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(q.events.nbytes + q.offsets.nbytes),
@@ -755,7 +763,8 @@ def main():
         held = synth.workload("sars_heldout_1024", seed=103)
         hc, _ = ctx.sdtw_batch(haru.HARU_FP32, held.queries.events, held.queries.offsets)
         thr = pick_threshold(hc.astype(np.float64), held.queries.on_target)
-        result["serving"] = run_serving(haru, args, local, w, thr, args.serve_channels)
+        if args.serve_channels > 0:
+            result["serving"] = run_serving(haru, args, local, w, thr, args.serve_channels)
         if args.stress_channels > 0:
             result["serving_stress"] = run_serving(haru, args, local, w, thr, args.stress_channels)
         if args.signal_channels > 0:

@@ -317,7 +317,8 @@ typedef struct {
   uint64_t max_upload_sync_ns, max_turn_gap_ns;
   /* the slowest turn: time in its complete / upload / launch / idle-wait
    * parts, and the worker thread's voluntary and involuntary context
-   * switches during it (Linux; 0 elsewhere) */
+   * switches during it (Linux; 0 elsewhere); its detection part and page
+   * faults follow at the end */
   uint64_t worst_turn_complete_ns, worst_turn_upload_ns, worst_turn_launch_ns, worst_turn_wait_ns;
   uint64_t worst_turn_voluntary_switches, worst_turn_involuntary_switches;
   /* the GPU stage split: the longest device execution of a batch (CUDA
@@ -333,6 +334,14 @@ typedef struct {
    * copies and gather, its device path (planner to fix-up) and its result
    * copies and completion event */
   uint64_t max_upload_calls_ns, max_launch_inputs_ns, max_launch_path_ns, max_launch_results_ns;
+  /* raw-sample serving: the longest group of detection CUDA calls (inputs,
+   * launch, count copy, event), and the slowest turn's detection part; then
+   * the worker thread's minor and major page faults during that turn */
+  uint64_t max_detect_calls_ns, worst_turn_detect_ns;
+  uint64_t worst_turn_minor_faults, worst_turn_major_faults;
+  /* when the slowest turn began (ns after the serving loop started), and
+   * how many turns took over 5 ms */
+  uint64_t worst_turn_at_ns, turns_over_5ms;
 } haru_stream_stats;
 int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
 

@@ -95,7 +95,9 @@ class haru_stream_stats(ctypes.Structure):
                                                "worst_turn_involuntary_switches", "max_gpu_exec_ns",
                                                "max_notice_ns", "max_drain_ns", "max_upload_calls_ns",
                                                "max_launch_inputs_ns", "max_launch_path_ns",
-                                               "max_launch_results_ns")]
+                                               "max_launch_results_ns", "max_detect_calls_ns",
+                                               "worst_turn_detect_ns", "worst_turn_minor_faults",
+                                               "worst_turn_major_faults", "worst_turn_at_ns", "turns_over_5ms")]
 
 
 _lib = None

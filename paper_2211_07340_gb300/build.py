@@ -1,7 +1,7 @@
 """Build libharu.so (the CUDA library behind include/haru.h) in-tree for sm_103a.
 
-Each .cu translation unit is compiled in parallel with nvcc (the sweep kernels
-are split one (precision, strip-height class) per unit), then linked into
+Each .cu translation unit is compiled in parallel with nvcc (the sweep and
+fix-up kernels are one unit per precision), then linked into
 paper_2211_07340_gb300/_lib/libharu.so. No CMake, one -gencode.
 """
 from __future__ import annotations
@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    # the sweep kernels are one translation unit per (precision, class): build them all at once
+    # every translation unit at once (the sweep kernels dominate the build time)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(24, os.cpu_count() or 1))) as ex:
         for obj, log in ex.map(one, sources()):
             objs.append(obj)

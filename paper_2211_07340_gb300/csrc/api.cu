@@ -381,7 +381,8 @@ int batch_call(haru_ctx *ctx, int precision, const float *events, const uint32_t
   HARU_CUDA(haru::ws_reserve(ctx->ws, precision, nq, lc));
   const bool prof = flags & HARU_PROFILE;
   HARU_CUDA(haru::ws_enqueue(ctx->ws, precision, ctx->ref_view(), d_ev, d_off, nq, raw, d_cost, d_col, lc, s,
-                             prof ? ctx->ev[0] : nullptr, prof ? ctx->ev[1] : nullptr, d_start));
+                             prof ? ctx->ev[0] : nullptr, prof ? ctx->ev[1] : nullptr, d_start, true,
+                             prof ? ctx->ev[3] : nullptr));
   if (prof) {
     HARU_CUDA(haru::record_event(ctx->ev[2], s));
     ctx->profiled = true;
@@ -430,7 +431,7 @@ int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep) {
   HARU_CUDA(cudaEventSynchronize(ctx->ev[2]));
   float a = 0.0f, b = 0.0f;
   HARU_CUDA(cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]));
-  HARU_CUDA(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]));
+  HARU_CUDA(cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[3]));
   if (ms_prep) *ms_prep = a;
   if (ms_sweep) *ms_sweep = b;
   return HARU_OK;

@@ -104,7 +104,7 @@ cudaError_t ws_reserve_upto(Workspace &ws, int precision, uint32_t max_nq, const
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
                        const LaunchCfg &lc, cudaStream_t s, cudaEvent_t ev_prep, cudaEvent_t ev_sweep,
-                       int64_t *d_start, bool zero_counters) {
+                       int64_t *d_start, bool zero_counters, cudaEvent_t ev_fix) {
   cudaError_t e;
   // (a caller that ran kernels reporting into the status word first has zeroed the counters itself)
   if (zero_counters && (e = cudaMemsetAsync(ws.ints, 0, kIntWords * sizeof(int), s)) != cudaSuccess) return e;
@@ -173,7 +173,7 @@ cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const f
   int per_sm = lc.ctas_per_sm > 0 ? lc.ctas_per_sm : sdtw_max_ctas_per_sm(precision, lc.tile, warps);
   if (per_sm < 1) per_sm = 1;
   const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(lc.sms) * per_sm, groups_max));
-  return launch_sdtw(precision, sa, grid, static_cast<int>(ws.max_items), s);
+  return launch_sdtw(precision, sa, grid, static_cast<int>(ws.max_items), s, ev_fix);
 }
 
 }  // namespace haru

@@ -104,7 +104,7 @@ void ws_free(Workspace &ws);
 cudaError_t ws_enqueue(Workspace &ws, int precision, const RefView &ref, const float *d_events,
                        const uint32_t *d_offsets, uint32_t nq, int raw, float *d_cost, int64_t *d_col,
                        const LaunchCfg &lc, cudaStream_t s, cudaEvent_t ev_prep, cudaEvent_t ev_sweep,
-                       int64_t *d_start = nullptr, bool zero_counters = true);
+                       int64_t *d_start = nullptr, bool zero_counters = true, cudaEvent_t ev_fix = nullptr);
 
 // Event detection (events.cu): parameter defaults and checks, and the
 // stream-ordered detection of nreads raw-signal reads: strided events and
@@ -121,6 +121,8 @@ cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uin
 cudaError_t enqueue_events_slots(const int16_t *samples, int sample_stride, const uint32_t *slot, const uint32_t *len,
                                  const int *final_limit, uint32_t nreads, const haru_event_params &p, float *events,
                                  int event_stride, uint32_t *counts, int *status, cudaStream_t s);
+// Load the detection kernels into the current context now (see load_sdtw).
+cudaError_t load_event_kernels();
 
 // Record `e` on `s`; inside a stream capture, as an external event node so
 // its time can be read after every replay.
@@ -173,7 +175,7 @@ struct haru_ctx {
   size_t cap_sig_counts = 0;
   uint32_t *sig_off = nullptr;
   size_t cap_sig_off = 0;
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // HARU_PROFILE
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // HARU_PROFILE: prep, sweep, end, fix-up
   bool profiled = false;
 
   // serving (serve.cu): created by the first haru_stream_submit

@@ -375,6 +375,16 @@ bool event_params_valid(const haru_event_params &p) {
          p.max_events <= HARU_MAX_QUERY;
 }
 
+static SmemOptIn detect_opt_in;  // the detection kernel's dynamic shared memory, per device
+
+cudaError_t load_event_kernels() {
+  cudaFuncAttributes f;
+  cudaError_t e = cudaFuncGetAttributes(&f, detect_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&f, scan_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&f, compact_kernel);
+  return e;
+}
+
 // Enqueue detection of nreads reads on s: strided events and counts, then
 // CSR offsets and events (ev_csr holds up to nreads * max_events floats).
 cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uint32_t nreads,
@@ -383,8 +393,7 @@ cudaError_t enqueue_events(const int16_t *d_samples, const uint32_t *d_soff, uin
   if (nreads == 0) return cudaSuccess;
   const int need = static_cast<int>(p.trim_events + p.max_events);
   const size_t smem = detect_smem_bytes(need);
-  cudaError_t e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = opt_in_smem(detect_kernel, detect_opt_in, smem);
   if (e != cudaSuccess) return e;
   EvArgs a;
   a.samples = d_samples;
@@ -425,8 +434,7 @@ cudaError_t enqueue_events_slots(const int16_t *samples, int sample_stride, cons
   if (nreads == 0) return cudaSuccess;
   const int need = static_cast<int>(p.trim_events + p.max_events);
   const size_t smem = detect_smem_bytes(need);
-  cudaError_t e = cudaFuncSetAttribute(detect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = opt_in_smem(detect_kernel, detect_opt_in, smem);
   if (e != cudaSuccess) return e;
   EvArgs a;
   a.samples = samples;

@@ -1,8 +1,10 @@
 // Internal declarations shared by the CUDA translation units of libharu.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -80,6 +82,31 @@ __host__ __device__ constexpr bool prec_span(int p) { return p == kPrecF32Span |
 __host__ __device__ constexpr int ring_words(int p) { return prec_span(p) ? 256 : 128; }
 // Words of one saved strip state: costs, and start columns for the span forms.
 __host__ __device__ constexpr int state_words(int p) { return prec_span(p) ? 2 * kStateStride : kStateStride; }
+
+// Opt a kernel in to `bytes` of dynamic shared memory on the current
+// device, calling the driver only when the size grows past what was set
+// before on that device (a serving loop launches every few hundred
+// microseconds). One record per kernel: `set` per device, under `mu`.
+constexpr int kMaxDevices = 64;
+struct SmemOptIn {
+  std::atomic<int> set[kMaxDevices] = {};
+  std::mutex mu;
+};
+template <class K>
+inline cudaError_t opt_in_smem(K kernel, SmemOptIn &rec, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int want = static_cast<int>(bytes);
+  if (dev < 0 || dev >= kMaxDevices)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  if (rec.set[dev].load(std::memory_order_acquire) >= want) return cudaSuccess;
+  std::lock_guard<std::mutex> lk(rec.mu);
+  if (rec.set[dev].load(std::memory_order_relaxed) >= want) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  if (e == cudaSuccess) rec.set[dev].store(want, std::memory_order_release);
+  return e;
+}
 
 // Layout of the small integer block every batch uses: the status word, the
 // planner's group and item counts, the fix-up count, the sweep kernel's work
@@ -179,7 +206,15 @@ cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s);
 // Mean and population sigma (FP64, sequential order) of each query of 1..512 events.
 cudaError_t launch_qstats(const float *events, const uint32_t *offsets, uint32_t nq, double *qstats, int *status,
                           cudaStream_t s);
-cudaError_t launch_sdtw(int precision, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s);
+cudaError_t launch_sdtw(int precision, const SdtwArgs &a, int grid, int fix_items, cudaStream_t s,
+                        cudaEvent_t ev_fix = nullptr);
+// cudaEventRecord that also works inside a stream capture (batch.cu).
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s);
+// Load kernels into the current context now instead of at their first
+// launch (lazy module loading): the planner, statistics and packing kernels,
+// and the sweep and fix-up kernels of a precision.
+cudaError_t load_prep_kernels();
+cudaError_t load_sdtw(int precision);
 size_t sdtw_smem_bytes(int precision, int tile_cols, int warps);
 int sdtw_max_ctas_per_sm(int precision, int tile_cols, int warps);
 

@@ -401,6 +401,14 @@ cudaError_t launch_plan(const PlanArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t load_prep_kernels() {
+  cudaFuncAttributes f;
+  cudaError_t e = cudaFuncGetAttributes(&f, plan_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&f, qstats_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&f, pack_kernel);
+  return e;
+}
+
 cudaError_t launch_pack(const PackArgs &a, uint32_t max_items, cudaStream_t s) {
   if (max_items == 0) return cudaSuccess;
   const int warps = 8;

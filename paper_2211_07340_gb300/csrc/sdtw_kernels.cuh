@@ -979,9 +979,9 @@ __global__ void __launch_bounds__(kFixWarps * 32) fixup_kernel(SdtwArgs A) {
 
 template <int PREC>
 cudaError_t launch_sweep_prec(const SdtwArgs &a, int grid, cudaStream_t s) {
+  static SmemOptIn opt;
   const size_t sm = sdtw_smem_bytes(PREC, a.tile_cols, a.warps);
-  cudaError_t e = cudaFuncSetAttribute(sdtw_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sm));
+  cudaError_t e = opt_in_smem(sdtw_kernel<PREC>, opt, sm);
   if (e != cudaSuccess) return e;
   sdtw_kernel<PREC><<<grid, a.warps * 32, sm, s>>>(a);
   return cudaGetLastError();
@@ -1015,10 +1015,18 @@ int occupancy_prec(int tile_cols, int warps) {
     return launch_sweep_prec<P>(a, grid, s);                                                   \
   }                                                                                            \
   int sdtw_occupancy_##P(int tile_cols, int warps) { return occupancy_prec<P>(tile_cols, warps); } \
+  cudaError_t sdtw_sweep_load_##P() {                                                          \
+    cudaFuncAttributes f;                                                                      \
+    return cudaFuncGetAttributes(&f, sdtw_kernel<P>);                                          \
+  }                                                                                            \
   }
 #define HARU_SDTW_FIXUP_INSTANCE(P)                                                            \
   namespace haru {                                                                             \
   cudaError_t sdtw_fixup_##P(const SdtwArgs &a, int fix_items, cudaStream_t s) {              \
     return launch_fixup_prec<P>(a, fix_items, s);                                              \
+  }                                                                                            \
+  cudaError_t sdtw_fixup_load_##P() {                                                          \
+    cudaFuncAttributes f;                                                                      \
+    return cudaFuncGetAttributes(&f, fixup_kernel<P>);                                         \
   }                                                                                            \
   }

@@ -45,18 +45,20 @@
 namespace haru {
 namespace {
 
-// Voluntary and involuntary context switches of the calling thread so far.
-void thread_switches(long *vol, long *invol) {
+// Voluntary and involuntary context switches and minor and major page
+// faults of the calling thread so far (Linux; zeros elsewhere).
+void thread_usage(long u[4]) {
 #ifdef RUSAGE_THREAD
   struct rusage ru;
   if (getrusage(RUSAGE_THREAD, &ru) == 0) {
-    *vol = ru.ru_nvcsw;
-    *invol = ru.ru_nivcsw;
+    u[0] = ru.ru_nvcsw;
+    u[1] = ru.ru_nivcsw;
+    u[2] = ru.ru_minflt;
+    u[3] = ru.ru_majflt;
     return;
   }
 #endif
-  *vol = 0;
-  *invol = 0;
+  u[0] = u[1] = u[2] = u[3] = 0;
 }
 
 uint64_t now_ns() {
@@ -249,6 +251,7 @@ class Server {
   size_t ops_cap_ = 0;
   cudaStream_t up_stream_ = nullptr;
   cudaEvent_t up_done_ = nullptr;
+  cudaStream_t det_stream_ = nullptr;  // signal mode: detection launches (not behind uploads)
   std::vector<BatchCtx> batches_;
   // per-turn scratch of the worker, kept between turns so that a turn does
   // not allocate once the vectors have grown
@@ -287,12 +290,13 @@ class Server {
   // copy, the scatter launch and the event record; launch = the batch's input
   // copies and gather, the device path's launches, the result copies and
   // the completion event
-  std::atomic<uint64_t> max_part_[4] = {{0}, {0}, {0}, {0}};
+  std::atomic<uint64_t> max_part_[5] = {{0}, {0}, {0}, {0}, {0}};
   void note_part(int k, uint64_t dt) {
     if (dt > max_part_[k]) max_part_[k] = dt;
   }
   uint64_t spin_ns_ = 0;  // keep polling this long after the last piece of work
-  std::atomic<uint64_t> worst_[6] = {{0}, {0}, {0}, {0}, {0}, {0}};  // parts of the slowest turn
+  std::atomic<uint64_t> worst_[9] = {};  // parts, switches and faults of the slowest turn
+  std::atomic<uint64_t> worst_at_{0}, slow_turns_{0};  // its start after the loop's; turns over 5 ms
   void note_stage(int k, uint64_t dt) {
     if (dt > max_stage_[k]) max_stage_[k] = dt;
     if (dt > 10000000ull) slow_stage_[k]++;
@@ -353,6 +357,7 @@ int Server::start(int mode) {
     if (e == cudaSuccess) e = cudaMalloc(&d_det_cnt_, nd * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&d_det_status_, sizeof(int));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&det_done_, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&det_stream_, cudaStreamNonBlocking);
     det_snap_.reserve(nd);
   }
   const int nb = 3;
@@ -376,6 +381,14 @@ int Server::start(int mode) {
     // item grow as batches shrink) so the loop never allocates
     if (e == cudaSuccess) e = ws_reserve_upto(b.ws, precision_, static_cast<uint32_t>(max_batch_), lc_);
   }
+  // every kernel the loop launches, loaded now rather than inside the first requests
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, scatter_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, scatter_kernel<int16_t>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, gather_kernel);
+  if (e == cudaSuccess) e = load_prep_kernels();
+  if (e == cudaSuccess) e = load_sdtw(precision_);
+  if (e == cudaSuccess && mode_ == 1) e = load_event_kernels();
   if (e != cudaSuccess) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? HARU_ENOMEM : HARU_ECUDA;
@@ -410,6 +423,7 @@ void Server::stop() {
   }
   batches_.clear();
   if (up_stream_) cudaStreamSynchronize(up_stream_);
+  if (det_stream_) cudaStreamSynchronize(det_stream_);
   if (d_slots_) cudaFree(d_slots_);
   if (d_stage_) cudaFree(d_stage_);
   if (h_stage_) cudaFreeHost(h_stage_);
@@ -424,6 +438,8 @@ void Server::stop() {
   for (void *q : hsig)
     if (q) cudaFreeHost(q);
   if (det_done_) cudaEventDestroy(det_done_);
+  if (det_stream_) cudaStreamDestroy(det_stream_);
+  det_stream_ = nullptr;
   d_smp_ = d_stage16_ = h_stage16_ = nullptr;
   d_ops16_ = h_ops16_ = nullptr;
   d_det_slot_ = d_det_len_ = d_det_cnt_ = h_det_slot_ = h_det_len_ = h_det_cnt_ = nullptr;
@@ -619,12 +635,18 @@ void Server::stats(haru_stream_stats *out) {
   out->max_launch_inputs_ns = max_part_[1];
   out->max_launch_path_ns = max_part_[2];
   out->max_launch_results_ns = max_part_[3];
+  out->max_detect_calls_ns = max_part_[4];
   out->worst_turn_complete_ns = worst_[0];
   out->worst_turn_upload_ns = worst_[1];
   out->worst_turn_launch_ns = worst_[2];
   out->worst_turn_wait_ns = worst_[3];
   out->worst_turn_voluntary_switches = worst_[4];
   out->worst_turn_involuntary_switches = worst_[5];
+  out->worst_turn_detect_ns = worst_[6];
+  out->worst_turn_minor_faults = worst_[7];
+  out->worst_turn_major_faults = worst_[8];
+  out->worst_turn_at_ns = worst_at_;
+  out->turns_over_5ms = slow_turns_;
   out->slots = static_cast<uint64_t>(nslots_);
   std::lock_guard<std::mutex> lk(mu_);
   out->reads_waiting = admit_q_.size();
@@ -689,6 +711,7 @@ int Server::turn_upload() {
   }
   if (!ops16_.empty()) {
     std::memcpy(h_ops16_, ops16_.data(), ops16_.size() * sizeof(CopyOp));
+    const uint64_t tc = now_ns();
     cudaError_t e = cudaMemcpyAsync(d_stage16_, h_stage16_, staged * sizeof(int16_t), cudaMemcpyHostToDevice,
                                     up_stream_);
     if (e == cudaSuccess)
@@ -699,6 +722,7 @@ int Server::turn_upload() {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(up_done_, up_stream_);
+    note_part(0, now_ns() - tc);
     const uint64_t ts = now_ns();
     if (e == cudaSuccess) {
       while ((e = cudaEventQuery(up_done_)) == cudaErrorNotReady) {
@@ -809,7 +833,11 @@ int Server::turn_detect() {
     }
   }
   if (n == 0) return HARU_OK;
-  cudaStream_t s = up_stream_;
+  // Its own stream: the next upload's wait covers that upload alone. The
+  // samples read here were uploaded and waited for before this launch, and
+  // the reads it completes are queued only once the host has seen det_done_.
+  cudaStream_t s = det_stream_;
+  const uint64_t tc = now_ns();
   cudaError_t e = cudaMemcpyAsync(d_det_slot_, h_det_slot_, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_det_len_, h_det_len_, n * sizeof(uint32_t), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_det_lim_, h_det_lim_, n * sizeof(int), cudaMemcpyHostToDevice, s);
@@ -819,6 +847,7 @@ int Server::turn_detect() {
                              slot_len_, d_det_cnt_, d_det_status_, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_det_cnt_, d_det_cnt_, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaEventRecord(det_done_, s);
+  note_part(4, now_ns() - tc);
   if (e != cudaSuccess) return HARU_ECUDA;
   det_busy_ = true;
   return HARU_OK;
@@ -947,26 +976,32 @@ void Server::worker() {
     if (out_buf_.empty()) out_buf_.resize(4096);
   }
   uint64_t t_prev = now_ns();
-  long vcs0 = 0, ics0 = 0;
-  thread_switches(&vcs0, &ics0);
-  uint64_t part[4] = {0, 0, 0, 0};
+  const uint64_t t_loop = t_prev;
+  long use0[4];
+  thread_usage(use0);
+  uint64_t part[5] = {0, 0, 0, 0, 0};
   uint64_t t_work = now_ns();  // last turn that had work
   while (run_) {
     const uint64_t t_turn = now_ns();
-    long vcs = 0, ics = 0;
-    thread_switches(&vcs, &ics);
+    long use[4];
+    thread_usage(use);
+    if (t_turn - t_prev > 5000000ull) slow_turns_++;
     if (t_turn - t_prev > max_gap_) {  // the previous turn was the slowest so far
       max_gap_ = t_turn - t_prev;
+      worst_at_ = t_prev - t_loop;
       for (int k = 0; k < 4; ++k) worst_[k] = part[k];
-      worst_[4] = static_cast<uint64_t>(vcs - vcs0);
-      worst_[5] = static_cast<uint64_t>(ics - ics0);
+      worst_[6] = part[4];
+      worst_[4] = static_cast<uint64_t>(use[0] - use0[0]);
+      worst_[5] = static_cast<uint64_t>(use[1] - use0[1]);
+      worst_[7] = static_cast<uint64_t>(use[2] - use0[2]);
+      worst_[8] = static_cast<uint64_t>(use[3] - use0[3]);
     }
     t_prev = t_turn;
-    vcs0 = vcs;
-    ics0 = ics;
+    for (int k = 0; k < 4; ++k) use0[k] = use[k];
     int rc = turn_complete();
     const uint64_t t1 = now_ns();
     if (rc == HARU_OK) rc = turn_upload();
+    const uint64_t tu = now_ns();
     if (rc == HARU_OK) rc = turn_detect();
     const uint64_t t2 = now_ns();
     if (rc == HARU_OK) rc = turn_launch();
@@ -986,7 +1021,8 @@ void Server::worker() {
         cv_work_.wait_for(lk, std::chrono::microseconds(busy ? 50 : 200));
     }
     part[0] = t1 - t_turn;
-    part[1] = t2 - t1;
+    part[1] = tu - t1;
+    part[4] = t2 - tu;
     part[2] = t3 - t2;
     part[3] = now_ns() - t3;
   }

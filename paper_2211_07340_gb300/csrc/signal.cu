@@ -173,7 +173,8 @@ int haru_sdtw_batch_signal(haru_ctx *ctx, int precision, const int16_t *samples,
   SIG_CUDA(haru::enqueue_events(d_smp, d_soff, nreads, p, ctx->sig_strided, ctx->sig_counts, ctx->sig_off,
                                 ctx->sig_events, ctx->ws.ints + haru::kIntStatus, s));
   SIG_CUDA(haru::ws_enqueue(ctx->ws, precision, ctx->ref_view(), ctx->sig_events, ctx->sig_off, nreads, 1, d_cost,
-                            d_col, lc, s, nullptr, prof ? ctx->ev[1] : nullptr, nullptr, false));
+                            d_col, lc, s, nullptr, prof ? ctx->ev[1] : nullptr, nullptr, false,
+                            prof ? ctx->ev[3] : nullptr));
   if (prof) {
     SIG_CUDA(haru::record_event(ctx->ev[2], s));
     ctx->profiled = true;
