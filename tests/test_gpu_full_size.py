@@ -220,8 +220,10 @@ def test_long_reference_int16_every_query(long_ref):
 
 
 def test_long_reference_fp32_every_query(long_ref):
+    """Every query bit for bit against the FP32 oracle; the FP64 tolerance
+    check on every eighth (64 queries, 160 G cells)."""
     q, ref, _, (c, j) = long_ref
-    compare_fp32(c, j, ref, q.events, q.offsets)
+    compare_fp32(c, j, ref, q.events, q.offsets, f64_every=8)
     on = q.on_target
     assert (np.abs(j[on] - q.truth_end[on]) <= 8).mean() >= 0.9
 
