@@ -342,6 +342,9 @@ typedef struct {
   /* when the slowest turn began (ns after the serving loop started), and
    * how many turns took over 5 ms */
   uint64_t worst_turn_at_ns, turns_over_5ms;
+  /* the worker thread's minor page faults and voluntary context switches
+   * over the whole run */
+  uint64_t worker_minor_faults, worker_voluntary_switches;
 } haru_stream_stats;
 int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
 

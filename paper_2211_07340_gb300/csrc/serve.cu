@@ -212,6 +212,33 @@ class Server {
   void forget(const Read &r) {  // worker, under mu_: the read leaves reads_ decided
     if (!r.seen_last) decided_.insert(r.id);
   }
+  // Host buffers of finished reads, reused by new reads at full capacity:
+  // in steady state the worker allocates no buffer memory and touches no
+  // new pages.
+  std::vector<std::vector<float>> spare_host_;
+  std::vector<std::vector<int16_t>> spare_smp_;
+  void retire(std::unordered_map<uint64_t, Read>::iterator it) {  // worker, under mu_
+    Read &r = it->second;
+    if (r.host.capacity()) {
+      r.host.clear();
+      spare_host_.push_back(std::move(r.host));
+    }
+    if (r.host_smp.capacity()) {
+      r.host_smp.clear();
+      spare_smp_.push_back(std::move(r.host_smp));
+    }
+    reads_.erase(it);
+  }
+  template <class T>
+  static void take_buffer(std::vector<std::vector<T>> &spare, std::vector<T> &v, size_t cap) {
+    if (!spare.empty()) {
+      v = std::move(spare.back());
+      spare.pop_back();
+      return;
+    }
+    v.resize(cap);  // touch every page now, once
+    v.clear();
+  }
   std::deque<uint64_t> admit_q_;        // reads waiting for a slot
   std::deque<uint64_t> ready_q_;        // admitted reads with complete prefix, uploaded
   std::vector<int> free_slots_;
@@ -297,6 +324,7 @@ class Server {
   uint64_t spin_ns_ = 0;  // keep polling this long after the last piece of work
   std::atomic<uint64_t> worst_[9] = {};  // parts, switches and faults of the slowest turn
   std::atomic<uint64_t> worst_at_{0}, slow_turns_{0};  // its start after the loop's; turns over 5 ms
+  std::atomic<uint64_t> run_faults_{0}, run_switches_{0};  // the worker's, since the loop started
   void note_stage(int k, uint64_t dt) {
     if (dt > max_stage_[k]) max_stage_[k] = dt;
     if (dt > 10000000ull) slow_stage_[k]++;
@@ -393,6 +421,8 @@ int Server::start(int mode) {
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? HARU_ENOMEM : HARU_ECUDA;
   }
+  reads_.reserve(static_cast<size_t>(std::min(2 * nslots_, 1 << 16)));
+  decided_.reserve(1024);
   free_slots_.resize(nslots_);
   for (int i = 0; i < nslots_; ++i) free_slots_[i] = nslots_ - 1 - i;
   run_ = true;
@@ -533,7 +563,7 @@ void Server::reject(std::unordered_map<uint64_t, Read>::iterator it) {
   auto qi = std::find(admit_q_.begin(), admit_q_.end(), r.id);
   if (qi != admit_q_.end()) admit_q_.erase(qi);
   forget(r);
-  reads_.erase(it);
+  retire(it);
   {
     std::lock_guard<std::mutex> lo(out_mu_);
     push_out(o);
@@ -557,6 +587,10 @@ void Server::take_chunk(const Chunk *c) {
     Read r;
     r.id = c->read_id;
     r.channel = c->channel;
+    if (mode_ == 1)
+      take_buffer(spare_smp_, r.host_smp, HARU_MAX_READ_SAMPLES);
+    else
+      take_buffer(spare_host_, r.host, static_cast<size_t>(prefix_));
     it = reads_.emplace(c->read_id, std::move(r)).first;
     admit_q_.push_back(c->read_id);
     n_submitted_++;
@@ -647,6 +681,8 @@ void Server::stats(haru_stream_stats *out) {
   out->worst_turn_major_faults = worst_[8];
   out->worst_turn_at_ns = worst_at_;
   out->turns_over_5ms = slow_turns_;
+  out->worker_minor_faults = run_faults_;
+  out->worker_voluntary_switches = run_switches_;
   out->slots = static_cast<uint64_t>(nslots_);
   std::lock_guard<std::mutex> lk(mu_);
   out->reads_waiting = admit_q_.size();
@@ -952,7 +988,7 @@ int Server::turn_complete() {
         if (host_share > max_notice_) max_notice_ = host_share;
         free_slots_.push_back(r.slot);
         forget(r);
-        reads_.erase(it);
+        retire(it);
       }
     }
     b.busy = false;
@@ -979,6 +1015,7 @@ void Server::worker() {
   const uint64_t t_loop = t_prev;
   long use0[4];
   thread_usage(use0);
+  const long base_faults = use0[2], base_switches = use0[0];
   uint64_t part[5] = {0, 0, 0, 0, 0};
   uint64_t t_work = now_ns();  // last turn that had work
   while (run_) {
@@ -998,6 +1035,8 @@ void Server::worker() {
     }
     t_prev = t_turn;
     for (int k = 0; k < 4; ++k) use0[k] = use[k];
+    run_faults_ = static_cast<uint64_t>(use[2] - base_faults);
+    run_switches_ = static_cast<uint64_t>(use[0] - base_switches);
     int rc = turn_complete();
     const uint64_t t1 = now_ns();
     if (rc == HARU_OK) rc = turn_upload();
