@@ -435,7 +435,9 @@ def run_serving(haru, args, local, w, threshold, channels, signal=False):
                                                   "major": st["worst_turn_major_faults"]},
                        "worst_turn_at_s": st["worst_turn_at_ns"] / 1e9, "turns_over_5ms": st["turns_over_5ms"],
                        "worker_minor_faults": st["worker_minor_faults"],
-                       "worker_voluntary_switches": st["worker_voluntary_switches"]},
+                       "worker_voluntary_switches": st["worker_voluntary_switches"],
+                       "max_lock_wait_ms": st["max_lock_wait_ns"] / 1e6,
+                       "max_upload_host_ms": st["max_upload_host_ns"] / 1e6},
             "latency_clock": "chunk delivery that completes the prefix -> decision available (CLOCK_MONOTONIC); "
                              "library_*: the library's receipt of that chunk -> decision available"}
 

@@ -345,6 +345,9 @@ typedef struct {
   /* the worker thread's minor page faults and voluntary context switches
    * over the whole run */
   uint64_t worker_minor_faults, worker_voluntary_switches;
+  /* the longest wait of the worker for a lock another thread held, and the
+   * longest locked host pass of an upload turn (staging the chunks) */
+  uint64_t max_lock_wait_ns, max_upload_host_ns;
 } haru_stream_stats;
 int haru_stream_get_stats(haru_ctx *ctx, haru_stream_stats *out);
 

@@ -98,7 +98,8 @@ class haru_stream_stats(ctypes.Structure):
                                                "max_launch_results_ns", "max_detect_calls_ns",
                                                "worst_turn_detect_ns", "worst_turn_minor_faults",
                                                "worst_turn_major_faults", "worst_turn_at_ns", "turns_over_5ms",
-                                               "worker_minor_faults", "worker_voluntary_switches")]
+                                               "worker_minor_faults", "worker_voluntary_switches",
+                                               "max_lock_wait_ns", "max_upload_host_ns")]
 
 
 _lib = None

@@ -166,8 +166,7 @@ struct RingStore {
 
 template <int S>
 struct Geo {
-  static constexpr int U = (S % 2 == 0) ? S : 2 * S;    // steps per unrolled chunk (register renaming period)
-  static constexpr int F = (32 / U) > 0 ? (32 / U) : 1; // chunks per tracking flush
+  static constexpr int U = (S % 2 == 0) ? S : 2 * S;  // steps per unrolled chunk (register renaming period)
 };
 
 // ---------------------------------------------------------------- INT16 --
@@ -517,7 +516,7 @@ struct StripF32Span {
       pprev = pup;
       if (tracked) {
         ring[e0 + u] = __float_as_uint(G[b][S - 1]);
-        ring[128 + e0 + u] = static_cast<uint32_t>(P[b][S - 1]);
+        ring[2 * flush_words(kPrecF32Span) + e0 + u] = static_cast<uint32_t>(P[b][S - 1]);
       }
     }
   }
@@ -530,7 +529,7 @@ struct TrackF32Span {
   __device__ TrackF32Span() : best(__builtin_huge_valf()), col(-1), start(-1) {}
   __device__ __forceinline__ void add(const uint32_t *rg, int j, long c) {
     const float f = __uint_as_float(rg[j]);
-    if (f < best) { best = f; col = c; start = static_cast<int>(rg[128 + j]); }
+    if (f < best) { best = f; col = c; start = static_cast<int>(rg[2 * flush_words(kPrecF32Span) + j]); }
   }
   __device__ __forceinline__ void reduce(int width) {  // over aligned groups of `width` lanes
     for (int o = width >> 1; o > 0; o >>= 1) {
@@ -673,23 +672,30 @@ struct GlobalTiles {
 // save_start / save_final: where to store the state before step t_own and
 // before step t_end (nullptr: not stored). stk: a stacked item (lanes 0..15
 // and 16..31 are two strips; each lane tracks its own stack's last row).
-// `ring` holds kRingWords words per warp: two flush buffers of 64, the upper
-// stack's (or the whole strip's) entries first, the lower stack's at +32;
-// forms that carry start columns keep them 128 words further on.
+// `ring` holds ring_words() words per warp: two flush buffers of W =
+// flush_words() words, each filled by the strip's tracked lane between two
+// scans (or half by each stack's, the lower stack's at +W/2); forms that
+// carry start columns keep them 2W further on. Each flush scans W/32
+// entries per lane.
 // Returns false on abort.
 template <int FORM, int S, class Src>
 __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<FORM, S>::Track &tr, Src &src,
                           int TS, long t_start, long t_own, long t_end, bool fresh, long N, uint32_t *save_start,
                           uint32_t *save_final, uint32_t *ring, int lane, bool stk) {
-  constexpr int U = Geo<S>::U, F = Geo<S>::F;
+  constexpr int U = Geo<S>::U;
+  constexpr int W = flush_words(FORM == kFormI16 ? HARU_INT16 : HARU_FP32);
+  // chunks between two flushes: a stack's entries fill its share of a buffer
+  constexpr int kWhole = W / U > 0 ? W / U : 1;
+  constexpr int kHalf = W / 2 / U > 0 ? W / 2 / U : 1;
+  constexpr int nscan = W / 32;
+  const int F = stk ? kHalf : kWhole;
   // ng: 0 on a lane that starts a stack from the free-start row; nr: 0 on
   // lane 0, which injects the reference (it flows on through every lane)
   const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u, nr = lane != 0 ? 1u : 0u;
   const bool tracked = lane == 31 || (stk && lane == 15);
-  const int soff = stk && lane >= 16 ? 32 : 0;
+  const int soff = stk && lane >= 16 ? W / 2 : 0;
   const int top = stk && lane >= 16 ? 16 * S : 0;  // first row of this lane's stack
   const long last_row = (stk && lane < 16 ? 16L : 32L) * S - 1;
-  const int nscan = stk ? 2 : 1;
   const long k_first = t_start / TS;
   const int K = static_cast<int>((t_end + TS - 1) / TS - k_first);
   int fl = 0, buf = 0;
@@ -708,14 +714,14 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
     const uint32_t *tref = tile + (lo - tk0);
     for (int o = 0; o < n; o += U) {
       if (o == own_at) st.save(save_start, lane);
-      uint32_t *rg = ring + buf * 64 + soff;
+      uint32_t *rg = ring + buf * W + soff;
       const uint32_t *ref = nr ? zw : tref + o;
       const int tabs = static_cast<int>(lo) + o;
       st.chunk(ref, lane, rg, fl * U, ng, nr, tracked, tabs, top);
       if (++fl == F || (last_tile && o + U >= n)) {
         __syncwarp();
         for (int r = 0; r < nscan; ++r) {  // entry j = step tflush + j of this lane's stack
-          const int j = stk ? (lane & 15) + 16 * r : lane;
+          const int j = stk ? (lane & 15) + 16 * r : lane + 32 * r;
           if (j < fl * U) {
             const long t = tflush + j;
             const long c = t - last_row;

@@ -29,6 +29,7 @@
 // and polls events without blocking.
 
 #include <cuda_runtime.h>
+#include <pthread.h>
 #include <sys/resource.h>
 
 #include <algorithm>
@@ -325,6 +326,22 @@ class Server {
   std::atomic<uint64_t> worst_[9] = {};  // parts, switches and faults of the slowest turn
   std::atomic<uint64_t> worst_at_{0}, slow_turns_{0};  // its start after the loop's; turns over 5 ms
   std::atomic<uint64_t> run_faults_{0}, run_switches_{0};  // the worker's, since the loop started
+  // The worker's lock acquisitions, timed: the longest wait for a lock that
+  // another thread held, and the longest locked host pass of an upload turn.
+  std::atomic<uint64_t> max_lock_wait_{0}, max_upload_host_{0};
+  struct TimedLock {
+    std::mutex &m;
+    TimedLock(std::mutex &mu, std::atomic<uint64_t> &longest) : m(mu) {
+      if (m.try_lock()) return;
+      const uint64_t t0 = now_ns();
+      m.lock();
+      const uint64_t dt = now_ns() - t0;
+      if (dt > longest) longest = dt;
+    }
+    ~TimedLock() { m.unlock(); }
+    TimedLock(const TimedLock &) = delete;
+    TimedLock &operator=(const TimedLock &) = delete;
+  };
   void note_stage(int k, uint64_t dt) {
     if (dt > max_stage_[k]) max_stage_[k] = dt;
     if (dt > 10000000ull) slow_stage_[k]++;
@@ -529,7 +546,7 @@ void Server::drain_intake() {
     list = nx;
   }
   {
-    std::lock_guard<std::mutex> lk(mu_);
+    TimedLock lk(mu_, max_lock_wait_);
     for (Chunk *c = ord; c; c = c->next) {
       take_chunk(c);
       intake_events_ -= c->n;
@@ -565,7 +582,7 @@ void Server::reject(std::unordered_map<uint64_t, Read>::iterator it) {
   forget(r);
   retire(it);
   {
-    std::lock_guard<std::mutex> lo(out_mu_);
+    TimedLock lo(out_mu_, max_lock_wait_);
     push_out(o);
   }
   n_decided_++;
@@ -683,6 +700,8 @@ void Server::stats(haru_stream_stats *out) {
   out->turns_over_5ms = slow_turns_;
   out->worker_minor_faults = run_faults_;
   out->worker_voluntary_switches = run_switches_;
+  out->max_lock_wait_ns = max_lock_wait_;
+  out->max_upload_host_ns = max_upload_host_;
   out->slots = static_cast<uint64_t>(nslots_);
   std::lock_guard<std::mutex> lk(mu_);
   out->reads_waiting = admit_q_.size();
@@ -702,8 +721,9 @@ int Server::turn_upload() {
   std::vector<uint64_t> &finished = finished_;
   finished.clear();
   ops16_.clear();
+  const uint64_t th = now_ns();
   {
-    std::lock_guard<std::mutex> lk(mu_);
+    TimedLock lk(mu_, max_lock_wait_);
     while (!admit_q_.empty() && !free_slots_.empty()) {
       Read &r = reads_[admit_q_.front()];
       admit_q_.pop_front();
@@ -744,6 +764,10 @@ int Server::turn_upload() {
           std::find(finished.begin(), finished.end(), r.id) == finished.end())
         finished.push_back(r.id);
     }
+  }
+  {
+    const uint64_t dh = now_ns() - th;
+    if (dh > max_upload_host_) max_upload_host_ = dh;
   }
   if (!ops16_.empty()) {
     std::memcpy(h_ops16_, ops16_.data(), ops16_.size() * sizeof(CopyOp));
@@ -796,7 +820,7 @@ int Server::turn_upload() {
     if (e != cudaSuccess) return HARU_ECUDA;
   }
   if (!finished.empty()) {
-    std::lock_guard<std::mutex> lk(mu_);
+    TimedLock lk(mu_, max_lock_wait_);
     const uint64_t tq = now_ns();
     for (uint64_t id : finished) {
       Read &r = reads_[id];
@@ -822,7 +846,7 @@ int Server::turn_detect() {
     if (q == cudaErrorNotReady) return HARU_OK;
     if (q != cudaSuccess) return HARU_ECUDA;
     det_busy_ = false;
-    std::lock_guard<std::mutex> lk(mu_);
+    TimedLock lk(mu_, max_lock_wait_);
     const uint64_t tq = now_ns();
     for (size_t i = 0; i < det_snap_.size(); ++i) {
       const DetSnap &d = det_snap_[i];
@@ -849,7 +873,7 @@ int Server::turn_detect() {
   }
   uint32_t n = 0;
   {
-    std::lock_guard<std::mutex> lk(mu_);
+    TimedLock lk(mu_, max_lock_wait_);
     det_snap_.clear();
     // a live read can only complete once it has (trim + prefix) events of at
     // least w_short + 1 samples each, plus the finality margin
@@ -895,7 +919,7 @@ int Server::turn_launch() {
     if (b.busy) continue;
     uint32_t n = 0;
     {
-      std::lock_guard<std::mutex> lk(mu_);
+      TimedLock lk(mu_, max_lock_wait_);
       if (ready_q_.empty()) return HARU_OK;
       b.reads.clear();
       b.h_off[0] = 0;
@@ -964,7 +988,7 @@ int Server::turn_complete() {
     std::vector<haru_result> &res = res_;
     res.resize(b.reads.size());
     {
-      std::lock_guard<std::mutex> lk(mu_);
+      TimedLock lk(mu_, max_lock_wait_);
       for (size_t i = 0; i < b.reads.size(); ++i) {
         auto it = reads_.find(b.reads[i]);
         Read &r = it->second;
@@ -993,7 +1017,7 @@ int Server::turn_complete() {
     }
     b.busy = false;
     {
-      std::lock_guard<std::mutex> lk(out_mu_);
+      TimedLock lk(out_mu_, max_lock_wait_);
       for (auto &o : res) push_out(o);
     }
     n_decided_ += res.size();
@@ -1003,12 +1027,15 @@ int Server::turn_complete() {
 }
 
 void Server::worker() {
+#ifdef __linux__
+  pthread_setname_np(pthread_self(), "haru-serve");  // findable in /proc and by debuggers
+#endif
   if (cudaSetDevice(ctx_->device) != cudaSuccess) {
     fail(HARU_ECUDA);
     return;
   }
   {
-    std::lock_guard<std::mutex> lk(out_mu_);  // the result ring, allocated by this thread
+    TimedLock lk(out_mu_, max_lock_wait_);  // the result ring, allocated by this thread
     if (out_buf_.empty()) out_buf_.resize(4096);
   }
   uint64_t t_prev = now_ns();
