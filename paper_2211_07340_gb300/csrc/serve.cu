@@ -82,7 +82,7 @@ int touch_code_pages(struct dl_phdr_info *info, size_t, void *arg) {
   volatile unsigned char sink = 0;
   for (int i = 0; i < info->dlpi_phnum; ++i) {
     const ElfW(Phdr) &ph = info->dlpi_phdr[i];
-    if (ph.p_type != PT_LOAD || !(ph.p_flags & PF_X)) continue;
+    if (ph.p_type != PT_LOAD || !(ph.p_flags & PF_X) || !(ph.p_flags & PF_R)) continue;  // readable code only
     const unsigned char *p = reinterpret_cast<const unsigned char *>(info->dlpi_addr + ph.p_vaddr);
     for (size_t o = 0; o < ph.p_memsz; o += page) sink = static_cast<unsigned char>(sink ^ p[o]);
   }
