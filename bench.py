@@ -333,6 +333,24 @@ def run_signal(haru, args, ctx, dev, stream, flush, rank):
                                      "z-score, int16 sDTW; CUDA graph, L2 flushed"}
 
 
+def process_thp_off():
+    """This process only: no transparent huge pages (PR_SET_THP_DISABLE, which
+    its children inherit) and no MADV_HUGEPAGE on numpy's large arrays. On a
+    kernel with 64 KB base pages a huge page is 512 MB, and faults on
+    hugepage-advised memory compact (migrate) other pages of the process."""
+    import ctypes
+    try:
+        libc = ctypes.CDLL(None, use_errno=True)
+        libc.prctl(41, 1, 0, 0, 0)  # PR_SET_THP_DISABLE
+    except (OSError, AttributeError):
+        pass
+    try:
+        from numpy._core import multiarray
+        multiarray._set_madvise_hugepage(False)
+    except (ImportError, AttributeError):
+        pass
+
+
 def pick_threshold(costs, on_target):
     """Decision threshold from a labelled held-out set: the cost cut with the
     fewest misclassified queries (accept iff cost <= T); among equally good
@@ -515,7 +533,11 @@ def main():
                     help="reference-length sweep (59,796 / 257,820 / 9,999,990 columns) instead of the benchmark")
     ap.add_argument("--sweep-reps", type=int, default=10)
     ap.add_argument("--sweep-cpu-s", type=float, default=3.0, help="oracle seconds per reference in --ref-sweep")
+    ap.add_argument("--thp", choices=["on", "off"], default="on",
+                    help="off: no transparent huge pages for this process (prctl) and none requested by numpy")
     args = ap.parse_args()
+    if args.thp == "off":
+        process_thp_off()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
