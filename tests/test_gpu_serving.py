@@ -127,6 +127,11 @@ def test_stage_counters_and_idle_sleeping_worker(haru, ref):
     assert all(r.t_arrival_ns <= r.t_received_ns <= r.t_done_ns for r in got.values())
     assert st["reads_decided"] == len(got) and st["batches"] >= 1
     assert st["max_gpu_ns"] > 0 and st["max_turn_gap_ns"] > 0
+    # (read while the worker keeps turning, so only bounds that a later turn
+    # cannot break): the slowest turn started inside the loop's run
+    assert 0 <= st["worst_turn_at_ns"] < 60 * 10 ** 9
+    assert st["max_upload_host_ns"] > 0 and st["max_upload_calls_ns"] > 0
+    assert st["max_detect_calls_ns"] == 0  # event chunks: no detection launches
 
 
 @pytest.mark.parametrize("prec,budget", [(1, 64 << 20), (0, 64 << 20), (1, 12 * 34 * 1024)])
