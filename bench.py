@@ -519,7 +519,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use the library defaults)")
     ap.add_argument("--workload", default=WORKLOAD, help="sars_uneven_8192 (default) or long_512x250")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
-                    help="measured seconds of the simulated flow-cell run, after the warm-up (0 = skip)")
+                    help="measured seconds of the simulated flow-cell run, after the warm-up (0 = skip; N = 1 only)")
     ap.add_argument("--serve-warm", type=float, default=5.0, help="seconds of serving before the measured span")
     ap.add_argument("--serve-channels", type=int, default=512, help="event-chunk serving channels (0 = skip)")
     ap.add_argument("--serve-clock-ms", type=int, default=100,
@@ -799,7 +799,9 @@ def main():
         "clocks": clocks,
         "gpu_launches": int(sum(launches)),
     }
-    if args.serve_seconds > 0 and args.workload == WORKLOAD:
+    # decision latency is a one-GPU property: the serving legs run at N = 1
+    # only, so a scaling run holds its GPUs for the batch legs alone
+    if args.serve_seconds > 0 and args.workload == WORKLOAD and world == 1:
         held = synth.workload("sars_heldout_1024", seed=103)
         hc, _ = ctx.sdtw_batch(haru.HARU_FP32, held.queries.events, held.queries.offsets)
         thr = pick_threshold(hc.astype(np.float64), held.queries.on_target)
