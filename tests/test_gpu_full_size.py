@@ -145,6 +145,14 @@ def test_precision_study_4096x250_and_heldout(haru):
         compare_int16(*res[(name, "i16", 6)], ref, qq.events, qq.offsets, scale_log2=6)
         for k in (5, 6):
             compare_int16(*res[(name, "i32", k)], ref, qq.events, qq.offsets, scale_log2=k, prec=oracle.PREC_I32)
+    # every other scale of the sweep, both integer forms, on a fixed sample of
+    # 256 test queries (the scales the paper's accuracy figure spans)
+    sample = np.arange(0, q.nq, q.nq // 256)[:256]
+    for k in (1, 2, 3, 4, 5, 7):
+        compare_int16(*res[("test", "i16", k)], ref, q.events, q.offsets, scale_log2=k, idx=sample)
+    for k in (1, 2, 3, 4, 7):
+        compare_int16(*res[("test", "i32", k)], ref, q.events, q.offsets, scale_log2=k, idx=sample,
+                      prec=oracle.PREC_I32)
     _, o64 = compare_fp32(*res[("test", "f32")], ref, q.events, q.offsets)
     _, h64 = compare_fp32(*res[("held", "f32")], ref, hq.events, hq.offsets)
     thr = bench.pick_threshold(h64.cost, hq.on_target)
@@ -187,7 +195,8 @@ def test_precision_study_4096x250_and_heldout(haru):
               "int16_acc32_scale64": err(*res[("test", "i32", 6)]),
               "truth_accuracy_fp64": float(np.mean(d64 == q.on_target)),
               "scale_sweep_vs_fp32": sweep,
-              "bit_exact": "int16 2^6 and wide 2^5, 2^6 on all 4,096 + 1,024 queries"}
+              "bit_exact": "int16 2^6 and wide 2^5, 2^6 on all 4,096 + 1,024 queries; both forms at every "
+                           "other scale 2^1..2^7 on 256 of the 4,096"}
     out = os.environ.get("HARU_PRECISION_REPORT")
     if out:
         with open(out, "w") as f:
