@@ -31,6 +31,13 @@ int cuda_fail(haru_ctx *c, cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_);  \
   } while (0)
 
+// Free a reference image allocated with its kRefFront front pad, given the
+// pointer to its column 0 (nullptr: nothing).
+template <class T>
+void free_ref_image(T *col0) {
+  if (col0) cudaFree(col0 - haru::kRefFront);
+}
+
 int pick_warps(const haru_config &cfg) {
   int w = cfg.warps_per_cta;
   if (w != 2 && w != 4 && w != 8 && w != 12) w = 8;
@@ -190,12 +197,13 @@ void haru_destroy(haru_ctx *ctx) {
     ctx->server = nullptr;
   }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  void *ptrs[] = {ctx->ref_z,     ctx->img16,       ctx->img32,       ctx->stats,      ctx->partials,
-                  ctx->d_events,  ctx->d_offsets,   ctx->d_cost,      ctx->d_col,      ctx->d_start,
-                  ctx->d_samples, ctx->d_soff,      ctx->sig_strided, ctx->sig_events, ctx->sig_counts,
-                  ctx->sig_off};
+  void *ptrs[] = {ctx->ref_z,     ctx->stats,       ctx->partials,    ctx->d_events,   ctx->d_offsets,
+                  ctx->d_cost,    ctx->d_col,       ctx->d_start,     ctx->d_samples,  ctx->d_soff,
+                  ctx->sig_strided, ctx->sig_events, ctx->sig_counts, ctx->sig_off};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  free_ref_image(ctx->img16);
+  free_ref_image(ctx->img32);
   haru::ws_free(ctx->ws);
   for (auto e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -206,24 +214,29 @@ void haru_destroy(haru_ctx *ctx) {
 size_t haru_ref_length(const haru_ctx *ctx) { return ctx ? ctx->N : 0; }
 
 // Normalise/quantise `x_dev` (n floats on the device) into the reference store.
+// Each image is kRefFront zero words, then columns 0 .. N - 1, then kRefPad
+// zero words; the context keeps the pointer to column 0.
 static int ref_install(haru_ctx *ctx, const float *x_dev, size_t n, int normalize, int scale_log2) {
   cudaStream_t s = ctx->stream;
   const size_t img_len = n + haru::kRefPad;
-  float *z = nullptr, *i32 = nullptr;
-  uint32_t *i16 = nullptr;
+  const size_t all = static_cast<size_t>(haru::kRefFront) + img_len;
+  float *z = nullptr, *i32b = nullptr;
+  uint32_t *i16b = nullptr;
   cudaError_t e = cudaMalloc(&z, n * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&i16, img_len * sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&i32, img_len * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&i16b, all * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&i32b, all * sizeof(float));
   if (e != cudaSuccess) {
-    cudaFree(z); cudaFree(i16); cudaFree(i32);
+    cudaFree(z); cudaFree(i16b); cudaFree(i32b);
     cudaGetLastError();
     return HARU_ENOMEM;
   }
+  uint32_t *i16 = i16b + haru::kRefFront;
+  float *i32 = i32b + haru::kRefFront;
   const size_t nb = (n + 4095) / 4096;
   HARU_CUDA(grow(&ctx->partials, &ctx->partials_cap, nb));
   HARU_CUDA(cudaMemsetAsync(ctx->ws.ints, 0, sizeof(int), s));
-  HARU_CUDA(cudaMemsetAsync(i16, 0, img_len * sizeof(uint32_t), s));
-  HARU_CUDA(cudaMemsetAsync(i32, 0, img_len * sizeof(float), s));
+  HARU_CUDA(cudaMemsetAsync(i16b, 0, all * sizeof(uint32_t), s));
+  HARU_CUDA(cudaMemsetAsync(i32b, 0, all * sizeof(float), s));
   if (normalize) HARU_CUDA(haru::launch_zscore_stats(x_dev, n, ctx->partials, ctx->stats, ctx->ws.ints, s));
   HARU_CUDA(haru::launch_ref_finish(x_dev, n, ctx->stats, normalize, scale_log2, z, i16, i32, img_len,
                                     ctx->ws.ints, s));
@@ -231,10 +244,12 @@ static int ref_install(haru_ctx *ctx, const float *x_dev, size_t n, int normaliz
   HARU_CUDA(cudaMemcpyAsync(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost, s));
   HARU_CUDA(cudaStreamSynchronize(s));
   if (st != HARU_OK) {
-    cudaFree(z); cudaFree(i16); cudaFree(i32);
+    cudaFree(z); cudaFree(i16b); cudaFree(i32b);
     return st;
   }
-  cudaFree(ctx->ref_z); cudaFree(ctx->img16); cudaFree(ctx->img32);
+  cudaFree(ctx->ref_z);
+  free_ref_image(ctx->img16);
+  free_ref_image(ctx->img32);
   ctx->ref_z = z;
   ctx->img16 = i16;
   ctx->img32 = i32;

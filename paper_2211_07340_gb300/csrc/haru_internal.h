@@ -72,6 +72,12 @@ constexpr int kCap = HARU_INT16_CAP;
 // skew of the tallest strip (32 * 16) plus one whole tile.
 constexpr int kMaxTile = 16384;
 constexpr long kRefPad = 32 * kMaxS + kMaxTile + 64;
+// Zero columns in front of column 0 of the device reference images: lane l
+// of a strip reads the reference at column t - l * S (up to 31 * kMaxS
+// behind the warp's step), and a tile's copy starts this many columns before
+// the tile.
+constexpr long kRefFront = 512;
+static_assert(kRefFront >= 31 * kMaxS && kRefFront % 16 == 0, "front pad: the largest lane lag, whole 64-byte lines");
 
 // Internal precisions of the sweep kernels beyond the public HARU_FP32,
 // HARU_INT16 and HARU_INT16_ACC32: the FP32 and wide forms that also carry
@@ -159,7 +165,8 @@ __host__ __device__ inline void seg_bounds(int S, int nseg, int seg, long N, lon
 }
 
 struct SdtwArgs {
-  const void *ref_img;     // INT16: uint32 (r | r << 16); FP32: float. >= N + kRefPad words
+  const void *ref_img;     // INT16: uint32 (r | r << 16); FP32: float. Column 0 of N + kRefPad words,
+                           // kRefFront zero words before it
   long N;                  // reference length (columns)
   const uint32_t *img;     // item images, kImgStride words each
   const Item *items;

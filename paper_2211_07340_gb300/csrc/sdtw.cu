@@ -25,9 +25,10 @@ HARU_SDTW_DECLARE(3)
 HARU_SDTW_DECLARE(4)
 
 size_t sdtw_smem_bytes(int precision, int tile_cols, int warps) {
-  // Shared header, per-warp tracking rings, 32 zero words, two tile slots
-  return 128 + static_cast<size_t>(warps) * ring_words(precision) * 4 + 32 * 4 +
-         2 * static_cast<size_t>(tile_cols) * 4;
+  // Shared header, per-warp tracking rings, two tile slots (each with the
+  // kRefFront columns before its tile)
+  return 128 + static_cast<size_t>(warps) * ring_words(precision) * 4 +
+         2 * static_cast<size_t>(tile_cols + kRefFront) * 4;
 }
 
 namespace {

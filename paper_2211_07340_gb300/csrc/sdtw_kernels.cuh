@@ -9,9 +9,11 @@
 // one oblique column: the S cells of a lane in one step are independent
 // (instruction-level parallelism S), a cell reads
 //   up   = row i-1 at step t-1,  diag = row i-1 at step t-2,  left = row i at step t-1,
-// and each step one value (the bottom row's cost) and the reference sample
-// it used cross from lane l-1 to lane l by __shfl_up_sync. Lane 0 injects
-// reference sample t and the free-start row gamma(0, .) = 0. A sweep is
+// and each step one value (the bottom row's cost) crosses from lane l-1 to
+// lane l by __shfl_up_sync; lane 0 takes the free-start row gamma(0, .) = 0.
+// Each lane reads its row 0's reference sample, column t - l*S, from the
+// shared tile itself, and the sample moves down the lane's rows by register
+// renaming (the oblique column's reference stream, Fig. 5). A sweep is
 // N + 32*S - 1 steps, the paper's N + M - 1 (Section 4.3) for the padded
 // height. Pad rows sit above the query and hold exactly 0, the free-start
 // boundary row, so the last query row is always lane 31's last register.
@@ -35,10 +37,11 @@
 // The result is always the plain DP's.
 //
 // The reference streams through shared memory: every CTA sweeps a group of
-// warps (same S, same segment) over the same columns; tiles of T_S columns
-// are fetched by cp.async.bulk (TMA) into a two-slot ring guarded by
-// mbarriers. The warp that releases a slot last issues the copy of the tile
-// two ahead.
+// warps (same S, same segment) over the same columns; tiles of T_S columns,
+// each with the kRefFront columns before it (the lanes lag the warp's step by
+// up to 31 * S columns), are fetched by cp.async.bulk (TMA) into a two-slot
+// ring guarded by mbarriers. The warp that releases a slot last issues the
+// copy of the tile two ahead.
 //
 // The last-row minimum and its first column (Algorithm 1's final scan,
 // Algorithm 2's per-column compare) are tracked through a small per-warp
@@ -123,18 +126,22 @@ __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
   return d;
 }
 
-// Reference sample of step u of a chunk, read 4 (or 2) at a time: `ref` is
-// 16-byte (8-byte) aligned whenever U is a multiple of 4 (2).
-template <int U>
-struct RefWindow {
+// This lane's reference sample of step u of a chunk, read A at a time. The
+// lane's window starts at column t0 - lane * S, a multiple of A (4 when the
+// strip height S is a multiple of 4, 2 when it is even, else 1; the chunk's
+// first step t0 is a multiple of U, which A divides), so every vector load is
+// aligned.
+template <int S>
+struct LaneWindow {
+  static constexpr int A = S % 4 == 0 ? 4 : (S % 2 == 0 ? 2 : 1);
   uint4 v4;
   uint2 v2;
   __device__ __forceinline__ uint32_t get(const uint32_t *ref, int u) {
-    if constexpr (U % 4 == 0) {
+    if constexpr (A == 4) {
       if (u % 4 == 0) v4 = reinterpret_cast<const uint4 *>(ref)[u / 4];
       const int c = u % 4;
       return c == 0 ? v4.x : (c == 1 ? v4.y : (c == 2 ? v4.z : v4.w));
-    } else if constexpr (U % 2 == 0) {
+    } else if constexpr (A == 2) {
       if (u % 2 == 0) v2 = reinterpret_cast<const uint2 *>(ref)[u / 2];
       return (u % 2 == 0) ? v2.x : v2.y;
     } else {
@@ -240,25 +247,22 @@ struct StripI16 {
   }
 
   __device__ __forceinline__ void chunk(const uint32_t *ref, int lane, uint32_t *ring, int e0, uint32_t ng,
-                                        uint32_t nr, bool tracked, int, int) {
+                                        bool tracked, int, int) {
     constexpr int U = Geo<S>::U;
-    RefWindow<U> win;
+    LaneWindow<S> win;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int p = (S - (u % S)) % S;
       const int a = (u + 1) & 1;
       const int b = u & 1;
       uint32_t gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
-      uint32_t rin = __shfl_up_sync(kFull, Rr[p], 1);
-      const uint32_t rv = win.get(ref, u);
       // A stack's first lane needs the free-start row, 0, above it. Strips
       // of fewer than kMaxS rows per lane are planned with a pad row on top
       // of every stack, which stays 0 whatever comes from above (its own
       // previous value, 0, is in the minimum), so only full-height strips
       // put the zero in.
       if constexpr (S == kMaxS) gup = imad(gup, ng, 0u);
-      rin = imad(rin, nr, rv);  // lane 0: reference sample t (other lanes read zeros)
-      Rr[p] = rin;
+      Rr[p] = win.get(ref, u);  // row 0's reference: column t - lane * S
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
         const uint32_t r = Rr[(p + k) % S];
@@ -324,15 +328,21 @@ struct StripF32 {
       W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
     }
   }
-  __device__ __forceinline__ void fresh(long, int, uint32_t) {
-    const float kBig = 1.0e30f;  // stands for +inf; sums of these stay finite
+  // As if the reference began at the current step, as in the int16 strip:
+  // every row, pad rows included, holds kBig (+inf; sums of these stay
+  // finite), and the row above a stack's top row held the free-start 0 one
+  // step back. The top row turns 0 at step 0, each pad row below at its own
+  // first column, and a real row stays at kBig or above until its first
+  // column whatever reference samples its lane reads before the start.
+  __device__ __forceinline__ void fresh(long, int, uint32_t ng) {
+    const float kBig = 1.0e30f;
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-      G[0][k] = W[k] != 0.0f ? kBig : 0.0f;
-      G[1][k] = G[0][k];
-      Rr[k] = kBig;  // columns before the start: distance ~1e30 for real rows, weight 0 for pad rows
+      G[0][k] = kBig;
+      G[1][k] = kBig;
+      Rr[k] = 0.0f;
     }
-    gprev = 0.0f;
+    gprev = ng ? kBig : 0.0f;
   }
   __device__ __forceinline__ void restore(const uint32_t *st, const uint32_t *gref, long t, int lane, uint32_t ng) {
 #pragma unroll
@@ -353,9 +363,9 @@ struct StripF32 {
   }
 
   __device__ __forceinline__ void chunk(const uint32_t *ref, int lane, uint32_t *ring, int e0, uint32_t ng,
-                                        uint32_t nr, bool tracked, int, int) {
+                                        bool tracked, int, int) {
     constexpr int U = Geo<S>::U;
-    RefWindow<U> win;
+    LaneWindow<S> win;
     RingStore<U> out;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -363,14 +373,11 @@ struct StripF32 {
       const int a = (u + 1) & 1;
       const int b = u & 1;
       float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
-      float rin = __shfl_up_sync(kFull, Rr[p], 1);
-      const float rv = ref_value(win.get(ref, u));
       // The free-start row above a stack's first lane: a pad row on top of
       // the stack (weight 0, value 0) keeps it for strips of fewer than
       // kMaxS rows per lane, as in the int16 strip.
       if constexpr (S == kMaxS) gup = ng ? gup : 0.0f;
-      rin = nr ? rin : rv;  // lane 0: reference sample t
-      Rr[p] = rin;
+      Rr[p] = ref_value(win.get(ref, u));  // row 0's reference: column t - lane * S
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
         const float r = Rr[(p + k) % S];
@@ -438,20 +445,24 @@ struct StripF32Span {
       W[k] = __uint_as_float(img[(S + k) * 32 + lane]);
     }
   }
-  // Before step t_start: row i = lane * S + k held its column t_start - 1 - i
-  // (and t_start - 2 - i one step earlier) as the start of a pad row's path.
-  __device__ __forceinline__ void fresh(long t_start, int lane, uint32_t) {
+  // As in StripF32: every row starts at kBig and the free-start zero reaches
+  // each row at its first column (a stack's top row takes the injected row
+  // above it, 0 with the current column, every step), so each pad row passes
+  // down its own column from then on. Before step t_start row i = lane * S +
+  // k held column t_start - 1 - i (t_start - 2 - i one step earlier); those
+  // starts belong to values at kBig, which no finite cost takes.
+  __device__ __forceinline__ void fresh(long t_start, int lane, uint32_t ng) {
     const float kBig = 1.0e30f;
 #pragma unroll
     for (int k = 0; k < S; ++k) {
-      G[0][k] = W[k] != 0.0f ? kBig : 0.0f;
-      G[1][k] = G[0][k];
-      Rr[k] = kBig;
+      G[0][k] = kBig;
+      G[1][k] = kBig;
+      Rr[k] = 0.0f;
       const int i = lane * S + k;
       P[1][k] = static_cast<int>(t_start) - 1 - i;
       P[0][k] = static_cast<int>(t_start) - 2 - i;
     }
-    gprev = 0.0f;
+    gprev = ng ? kBig : 0.0f;
     pprev = static_cast<int>(t_start) - 1 - lane * S;  // the row above row 0 at step t_start - 2
   }
   // States hold G (2S rows of 32 words) then P (2S rows).
@@ -483,9 +494,9 @@ struct StripF32Span {
   // this lane's stack (0, or 16 * S in the lower stack). The ring's start
   // columns sit 128 words after the costs.
   __device__ __forceinline__ void chunk(const uint32_t *ref, int lane, uint32_t *ring, int e0, uint32_t ng,
-                                        uint32_t nr, bool tracked, int t0, int top) {
+                                        bool tracked, int t0, int top) {
     constexpr int U = Geo<S>::U;
-    RefWindow<U> win;
+    LaneWindow<S> win;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int p = (S - (u % S)) % S;
@@ -493,12 +504,9 @@ struct StripF32Span {
       const int b = u & 1;
       float gup = __shfl_up_sync(kFull, G[a][S - 1], 1);
       int pup = __shfl_up_sync(kFull, P[a][S - 1], 1);
-      float rin = __shfl_up_sync(kFull, Rr[p], 1);
-      const float rv = ref_value(win.get(ref, u));
       gup = ng ? gup : 0.0f;             // a stack's first lane: the free-start row, 0 ...
       pup = ng ? pup : t0 + u - top;      // ... whose row processed column t - top at step t - 1
-      rin = nr ? rin : rv;                // lane 0: reference sample t
-      Rr[p] = rin;
+      Rr[p] = ref_value(win.get(ref, u));  // row 0's reference: column t - lane * S
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
         const float r = Rr[(p + k) % S];
@@ -601,11 +609,13 @@ struct Shared {
 };
 
 // Reference tiles streamed into shared memory by TMA (the sweep kernel).
+// Slot of tile k: the kRefFront columns before the tile, then its
+// tile_cols columns, so a lane that reads up to 31 * S columns behind the
+// warp's step finds its samples in the current slot.
 struct TileStream {
   Shared *sh;
-  char *slots;                 // two slots of tile_cols words
-  const uint32_t *zero_words;  // kZeroWords zero words in shared memory
-  const char *src;             // reference image
+  char *slots;                 // two slots of tile_cols + kRefFront words
+  const char *src;             // reference image (column 0; kRefFront zero words before it)
   int tile_cols;               // T_S
   int k_first;                 // first global tile of this group's steps
   int K;                       // tiles in this group's sweep
@@ -616,11 +626,15 @@ struct TileStream {
   __device__ void issue(int k) {  // one thread
     const int gk = sh->tile_base + k;
     const int slot = gk & 1;
-    const unsigned bytes = static_cast<unsigned>(tile_cols) * 4u;
+    const unsigned words = static_cast<unsigned>(tile_cols + kRefFront);
+    const unsigned bytes = words * 4u;
+    // from column (k_first + k) * tile_cols - kRefFront >= -kRefFront: the
+    // image's front pad; 16-byte aligned (tile_cols and kRefFront are
+    // multiples of 4 words)
+    const long first = static_cast<long>(k_first + k) * tile_cols - kRefFront;
     fence_proxy_async();
     mbar_expect_tx(&sh->full[slot], bytes);
-    tma_load_1d(slots + static_cast<size_t>(slot) * tile_cols * 4,
-                src + static_cast<size_t>(k_first + k) * tile_cols * 4, bytes, &sh->full[slot]);
+    tma_load_1d(slots + static_cast<size_t>(slot) * words * 4, src + first * 4, bytes, &sh->full[slot]);
     sh->uses[slot] += 1;
   }
   __device__ const uint32_t *acquire(int k) {  // whole warp
@@ -631,9 +645,8 @@ struct TileStream {
       sh->abort = 1;
       return nullptr;
     }
-    return reinterpret_cast<const uint32_t *>(slots + static_cast<size_t>(slot) * tile_cols * 4);
+    return reinterpret_cast<const uint32_t *>(slots + static_cast<size_t>(slot) * (tile_cols + kRefFront) * 4);
   }
-  __device__ __forceinline__ const uint32_t *zeros() const { return zero_words; }
   __device__ void release(int k) {  // lane 0 of a warp
     const int gk = sh->tile_base + k;
     const int slot = gk & 1;
@@ -647,21 +660,16 @@ struct TileStream {
   }
 };
 
-// Words of zeros that lanes other than lane 0 read in place of the
-// reference window (only lane 0 injects reference samples), so the
-// injection is one multiply-add: rin * (lane != 0) + sample-or-zero.
-constexpr int kZeroWords = 32;
-__device__ __align__(16) const uint32_t kGlobalZeros[kZeroWords] = {0};
-
-// The reference read straight from global memory (the fix-up kernel).
+// The reference read straight from global memory (the fix-up kernel), in
+// the same layout as a tile slot: the pointer of tile k is at the column
+// kRefFront before the tile (inside the image's front pad for tile 0).
 struct GlobalTiles {
   const uint32_t *img;
   int tile_cols;
   long k_first;
   __device__ __forceinline__ const uint32_t *acquire(int k) {
-    return img + static_cast<size_t>(k_first + k) * tile_cols;
+    return img + ((k_first + k) * tile_cols - kRefFront);
   }
-  __device__ __forceinline__ const uint32_t *zeros() const { return kGlobalZeros; }
   __device__ __forceinline__ void release(int) {}
 };
 
@@ -689,9 +697,8 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
   constexpr int kHalf = W / 2 / U > 0 ? W / 2 / U : 1;
   constexpr int nscan = W / 32;
   const int F = stk ? kHalf : kWhole;
-  // ng: 0 on a lane that starts a stack from the free-start row; nr: 0 on
-  // lane 0, which injects the reference (it flows on through every lane)
-  const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u, nr = lane != 0 ? 1u : 0u;
+  // ng: 0 on a lane that starts a stack from the free-start row
+  const uint32_t ng = (stk ? (lane & 15) : lane) != 0 ? 1u : 0u;
   const bool tracked = lane == 31 || (stk && lane == 15);
   const int soff = stk && lane >= 16 ? W / 2 : 0;
   const int top = stk && lane >= 16 ? 16 * S : 0;  // first row of this lane's stack
@@ -700,7 +707,6 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
   const int K = static_cast<int>((t_end + TS - 1) / TS - k_first);
   int fl = 0, buf = 0;
   long tflush = t_start;
-  const uint32_t *zw = src.zeros();
   for (int k = 0; k < K; ++k) {
     const uint32_t *tile = src.acquire(k);
     if (!tile) return false;
@@ -711,13 +717,15 @@ __device__ bool run_steps(typename FormOf<FORM, S>::Strip &st, typename FormOf<F
     const int n = static_cast<int>(hi - lo);
     const int own_at = (save_start && t_own >= lo && t_own < hi) ? static_cast<int>(t_own - lo) : -1;
     const bool last_tile = t_end <= tk0 + TS;
-    const uint32_t *tref = tile + (lo - tk0);
+    // this lane's reference window of the chunk at o: columns from
+    // lo + o - lane * S, found at (column - tk0 + kRefFront) in the slot;
+    // lane * S <= 31 * kMaxS <= kRefFront keeps it inside the slot
+    const uint32_t *tref = tile + (kRefFront + (lo - tk0) - static_cast<long>(lane) * S);
     for (int o = 0; o < n; o += U) {
       if (o == own_at) st.save(save_start, lane);
       uint32_t *rg = ring + buf * W + soff;
-      const uint32_t *ref = nr ? zw : tref + o;
       const int tabs = static_cast<int>(lo) + o;
-      st.chunk(ref, lane, rg, fl * U, ng, nr, tracked, tabs, top);
+      st.chunk(tref + o, lane, rg, fl * U, ng, tracked, tabs, top);
       if (++fl == F || (last_tile && o + U >= n)) {
         __syncwarp();
         for (int r = 0; r < nscan; ++r) {  // entry j = step tflush + j of this lane's stack
@@ -799,12 +807,10 @@ template <int PREC>
 __global__ void __launch_bounds__(prec_span(PREC) ? 256 : 384, 1) sdtw_kernel(SdtwArgs A) {
   extern __shared__ __align__(128) unsigned char smem[];
   Shared *sh = reinterpret_cast<Shared *>(smem);
-  // layout: Shared (128 B) | per-warp tracking rings | zero words | two tile slots
+  // layout: Shared (128 B) | per-warp tracking rings | two tile slots
   uint32_t *rings = reinterpret_cast<uint32_t *>(smem + 128);
   constexpr int kRing = ring_words(PREC);
-  uint32_t *zero_words = reinterpret_cast<uint32_t *>(smem + 128 + A.warps * kRing * 4);
-  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * kRing * 4 + kZeroWords * 4);
-  if (threadIdx.x < kZeroWords) zero_words[threadIdx.x] = 0u;
+  char *slots = reinterpret_cast<char *>(smem + 128 + A.warps * kRing * 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(&sh->full[0], 1);
@@ -831,7 +837,6 @@ __global__ void __launch_bounds__(prec_span(PREC) ? 256 : 384, 1) sdtw_kernel(Sd
     TileStream ts;
     ts.sh = sh;
     ts.slots = slots;
-    ts.zero_words = zero_words;
     ts.src = reinterpret_cast<const char *>(A.ref_img);
     ts.tile_cols = TS;
     ts.k_first = static_cast<int>(t_start / TS);
