@@ -42,7 +42,7 @@ struct LaunchCfg {
 };
 
 // Warps per CTA that the kernels of `precision` run: the start-column forms
-// hold ~240 registers a thread and launch at most 8 warps; the others fit
+// hold over 200 registers a thread and launch at most 8 warps; the others fit
 // 12 warps (3 per scheduler) in an SM's register file.
 inline int kernel_warps(int precision, const LaunchCfg &lc) {
   return prec_span(precision) && lc.warps > 8 ? 8 : lc.warps;
