@@ -59,7 +59,7 @@ struct Best {
 
 // Per-item register image: [2][S][32] 32-bit words (INT16: packed query
 // codes q and their negations -q, both -4095 on pad rows; FP32: query
-// samples and row weights, 1 on real rows and 0 on pad rows).
+// samples (0 on pad rows) and row weights, -1 on real rows and 0 on pad rows).
 constexpr int kImgStride = 2 * 16 * 32;
 // A saved strip state: the last two oblique columns, [2][S][32] words (the
 // start-column forms follow them with their start columns, as many words).

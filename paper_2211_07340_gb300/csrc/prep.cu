@@ -384,9 +384,12 @@ __global__ void pack_kernel(PackArgs a) {
         w0 |= (static_cast<uint32_t>(qv) & 0xffffu) << (16 * h);
         w1 |= (static_cast<uint32_t>(nv) & 0xffffu) << (16 * h);
       } else {
-        // FP32: the z-value; exact form: the int16 code as a float; weight 0 on pad rows
+        // FP32: the z-value; exact form: the int16 code as a float; the row
+        // weight the sweep multiplies the reference sample by: -1 on real
+        // rows (fma(r, -1, q) = q - r, rounded once), 0 on pad rows (which
+        // hold q = 0, so their distance is 0)
         w0 = __float_as_uint(codes ? (real ? static_cast<float>(quantise(z, s)) : 0.0f) : z);
-        w1 = __float_as_uint(real ? 1.0f : 0.0f);
+        w1 = __float_as_uint(real ? -1.0f : 0.0f);
       }
     }
     img[k * 32 + lane] = w0;

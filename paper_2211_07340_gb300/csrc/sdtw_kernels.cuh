@@ -24,7 +24,7 @@
 // INT16 form: two queries share a warp, one per 16-bit half (DPX
 // __viaddmax_s16x2_relu for |q - r|, __vimin3_u16x2, and __viaddmin_u16x2 on
 // the rows that saturate at CAP); pad rows hold 0. FP32 form: one query per warp, 3-input min.f32,
-// pad rows have weight 0 in gamma = fma(|q - r|, w, min3).
+// gamma = |d| + min3 with d = fma(r, w, q): w = -1 on real rows, 0 on pad rows (and q = 0 there).
 //
 // Segments. The steps of one query are cut into segments that run as
 // independent work units. Segment s > 0 starts V steps early from a fresh
@@ -381,11 +381,14 @@ struct StripF32 {
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
         const float r = Rr[(p + k) % S];
-        const float d = __fsub_rn(Q[k], r);
+        // q - r rounded once on real rows (weight -1), exactly 0 on pad rows
+        // (weight 0, q = 0); off the critical path, so the cost update that
+        // depends on the minimum is a plain add
+        const float d = __fmaf_rn(r, W[k], Q[k]);
         const float up = k ? G[a][k - 1] : gup;
         const float dg = k ? G[b][k - 1] : gprev;
         const float m = fmin3f(up, dg, G[a][k]);
-        G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
+        G[b][k] = __fadd_rn(fabsf(d), m);
       }
       gprev = gup;
       out.put(ring, e0, u, tracked, __float_as_uint(G[b][S - 1]));
@@ -510,14 +513,14 @@ struct StripF32Span {
 #pragma unroll
       for (int k = S - 1; k >= 0; --k) {
         const float r = Rr[(p + k) % S];
-        const float d = __fsub_rn(Q[k], r);
+        const float d = __fmaf_rn(r, W[k], Q[k]);  // q - r on real rows, 0 on pad rows
         const float up = k ? G[a][k - 1] : gup;
         const int pu = k ? P[a][k - 1] : pup;
         const float dg = k ? G[b][k - 1] : gprev;
         const int pd = k ? P[b][k - 1] : pprev;
         const float m = fmin3f(up, dg, G[a][k]);
         // The start of the preferred minimum predecessor: up, else diagonal, else left.
-        G[b][k] = __fmaf_rn(fabsf(d), W[k], m);
+        G[b][k] = __fadd_rn(fabsf(d), m);
         P[b][k] = sel_eq(up, m, pu, sel_eq(dg, m, pd, P[a][k]));
       }
       gprev = gup;
