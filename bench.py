@@ -92,7 +92,8 @@ def alu_peak_gcups(sms: int, clock_mhz: float, form: str = "int16") -> float:
     the saturating rows' viaddmin is charged to the first pipe and is left
     out of this minimum): 2 warp-instructions/clk/SM per pipe and 4
     issued/clk/SM both give 64 cells/clk/SM. FP32: 3 instructions per cell
-    (sub, 3-input min, fma) at one warp-instruction per clock per scheduler:
+    (the distance fma, 3-input min, add) at one warp-instruction per clock
+    per scheduler:
     128 / 3 = 42.7 cells/clk/SM.
     """
     per_clk = 64.0 if form == "int16" else 128.0 / 3.0
@@ -773,8 +774,8 @@ def main():
                  "median_ms_per_step": medians.get(haru.HARU_FP32, (None, None))[0], "dtype": "f32",
                  "roofline": {"bound": "alu", "kernel": "sdtw_kernel<FP32>", "achieved": ach32, "peak": peak32,
                               "unit": "GCUPS", "frac": ach32 / peak32, "traffic": profiled_traffic("fp32"),
-                              "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (3 issue slots per cell: sub, "
-                                            f"3-input min, fma at 4 warp-instr/clk/SM) x {max_mhz:.0f} MHz",
+                              "peak_basis": f"{sms} SMs x 42.67 cells/clk/SM (3 issue slots per cell: distance fma, "
+                                            f"3-input min, add at 4 warp-instr/clk/SM) x {max_mhz:.0f} MHz",
                               "peak_probe": probe32, "frac_of_probe": ach32 / probe32,
                               **dram_rate(profiled_traffic("fp32"), cells, ach32)},
                  "clocks": clocks32},
