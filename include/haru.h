@@ -49,7 +49,7 @@ extern "C" {
 #define HARU_EINVAL (-1)    /* bad argument: empty/NaN/Inf input, M = 0, M > N, M too long, bad scale */
 #define HARU_ENOREF (-2)    /* no reference loaded */
 #define HARU_ENOMEM (-3)    /* device or host allocation failed, or admission budget exceeded */
-#define HARU_EBUSY (-4)     /* serving queue full: poll, then retry */
+#define HARU_EBUSY (-4)     /* serving queue full: poll, then retry; or a reference change on a serving context */
 #define HARU_ETIMEDOUT (-5) /* a bounded wait (device or host) gave up */
 #define HARU_ECUDA (-6)     /* a CUDA runtime error (sticky per context) */
 
@@ -132,8 +132,12 @@ void haru_destroy(haru_ctx *ctx);
  *   (Section 4.1; population sigma, double-precision sums).
  * normalize = 0: levels are already z-scores.
  * scale_log2 = k in [1, 7]: int16 quantisation scale 2^k (Section 4.3 uses 2^5).
- * Replaces any previous reference. Errors: HARU_EINVAL (n = 0, non-finite
- * value, zero spread, bad k), HARU_ENOMEM, HARU_ECUDA. */
+ * Replaces any previous reference; a failed call leaves the previous one in
+ * place. A context that serves (after its first haru_stream_submit or
+ * haru_stream_submit_signal) keeps the reference its serving loop started
+ * with until haru_destroy: HARU_EBUSY (serve another reference from another
+ * context). Errors: HARU_EINVAL (n = 0, non-finite value, zero spread, bad
+ * k), HARU_ENOMEM, HARU_EBUSY, HARU_ECUDA. */
 int haru_ref_load(haru_ctx *ctx, const float *levels, size_t n, int normalize, int scale_log2);
 
 /* Build the reference on the device from a genome (Sections 2.2 and 4.1):
@@ -141,8 +145,9 @@ int haru_ref_load(haru_ctx *ctx, const float *levels, size_t n, int normalize, i
  * indexed by the base-4 k-mer code (first base most significant). The signal
  * is the forward strand's k-mer levels followed by the reverse complement's,
  * 2 * (n_bases - k + 1) values, then z-scored and quantised as in
- * haru_ref_load. Host pointers. Errors: HARU_EINVAL (k not in 1..12, genome
- * shorter than k, base > 3), HARU_ENOMEM, HARU_ECUDA. */
+ * haru_ref_load (HARU_EBUSY on a serving context, as there). Host pointers.
+ * Errors: HARU_EINVAL (k not in 1..12, genome shorter than k, base > 3),
+ * HARU_ENOMEM, HARU_EBUSY, HARU_ECUDA. */
 int haru_ref_build(haru_ctx *ctx, const uint8_t *bases, size_t n_bases, const float *kmer_levels, int k,
                    int scale_log2);
 
@@ -263,8 +268,10 @@ typedef struct {
  * read_id on channel. t_arrival_ns is the caller's CLOCK_MONOTONIC time of
  * delivery (it starts the decision-latency clock when this chunk completes
  * the prefix). last_chunk = 1 ends the read: a shorter prefix is decided as
- * is. Chunks after the prefix is complete are ignored. The call copies the
- * events and hands them to the serving thread without waiting on it (a
+ * is. Chunks after the prefix is complete are ignored, and so are the
+ * events of a chunk beyond the first serve_prefix (no read can use more).
+ * The call copies the events and hands them to the serving thread without
+ * waiting on it (a
  * lock-free list), so a submitter is never held up by the serving loop and
  * vice versa. The first call starts the serving thread. Errors: HARU_EINVAL,
  * HARU_ENOREF, HARU_ENOMEM, HARU_EBUSY (too many events waiting on the host:

@@ -133,7 +133,7 @@ const char *haru_strerror(int code) {
     case HARU_EINVAL: return "invalid argument";
     case HARU_ENOREF: return "no reference loaded";
     case HARU_ENOMEM: return "out of memory or admission budget";
-    case HARU_EBUSY: return "serving queue full";
+    case HARU_EBUSY: return "busy (serving queue full, or the reference of a serving context)";
     case HARU_ETIMEDOUT: return "bounded wait timed out";
     case HARU_ECUDA: return "CUDA error";
     default: return "unknown error";
@@ -233,19 +233,22 @@ static int ref_install(haru_ctx *ctx, const float *x_dev, size_t n, int normaliz
   uint32_t *i16 = i16b + haru::kRefFront;
   float *i32 = i32b + haru::kRefFront;
   const size_t nb = (n + 4095) / 4096;
-  HARU_CUDA(grow(&ctx->partials, &ctx->partials_cap, nb));
-  HARU_CUDA(cudaMemsetAsync(ctx->ws.ints, 0, sizeof(int), s));
-  HARU_CUDA(cudaMemsetAsync(i16b, 0, all * sizeof(uint32_t), s));
-  HARU_CUDA(cudaMemsetAsync(i32b, 0, all * sizeof(float), s));
-  if (normalize) HARU_CUDA(haru::launch_zscore_stats(x_dev, n, ctx->partials, ctx->stats, ctx->ws.ints, s));
-  HARU_CUDA(haru::launch_ref_finish(x_dev, n, ctx->stats, normalize, scale_log2, z, i16, i32, img_len,
-                                    ctx->ws.ints, s));
   int st = 0;
-  HARU_CUDA(cudaMemcpyAsync(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HARU_CUDA(cudaStreamSynchronize(s));
-  if (st != HARU_OK) {
+  e = grow(&ctx->partials, &ctx->partials_cap, nb);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ints, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(i16b, 0, all * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(i32b, 0, all * sizeof(float), s);
+  if (e == cudaSuccess && normalize)
+    e = haru::launch_zscore_stats(x_dev, n, ctx->partials, ctx->stats, ctx->ws.ints, s);
+  if (e == cudaSuccess)
+    e = haru::launch_ref_finish(x_dev, n, ctx->stats, normalize, scale_log2, z, i16, i32, img_len, ctx->ws.ints, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, ctx->ws.ints, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || st != HARU_OK) {  // the previous reference stays in place
+    const int rc = e != cudaSuccess ? cuda_fail(ctx, e) : st;
+    cudaStreamSynchronize(s);
     cudaFree(z); cudaFree(i16b); cudaFree(i32b);
-    return st;
+    return rc;
   }
   cudaFree(ctx->ref_z);
   free_ref_image(ctx->img16);
@@ -262,6 +265,7 @@ int haru_ref_load(haru_ctx *ctx, const float *levels, size_t n, int normalize, i
   if (!ctx) return HARU_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->sticky) return ctx->sticky;
+  if (ctx->server) return HARU_EBUSY;  // the serving loop holds the reference it started with
   if (!levels || n == 0 || scale_log2 < 1 || scale_log2 > 7) return HARU_EINVAL;
   if (n > (size_t)1 << 31) return HARU_EINVAL;
   HARU_CUDA(cudaSetDevice(ctx->device));
@@ -282,6 +286,7 @@ int haru_ref_build(haru_ctx *ctx, const uint8_t *bases, size_t n_bases, const fl
   if (!ctx) return HARU_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->sticky) return ctx->sticky;
+  if (ctx->server) return HARU_EBUSY;  // as haru_ref_load
   if (!bases || !kmer_levels || k < 1 || k > 12 || n_bases < (size_t)k || scale_log2 < 1 || scale_log2 > 7)
     return HARU_EINVAL;
   const size_t per = n_bases - k + 1;

@@ -546,6 +546,11 @@ int Server::submit(uint64_t read_id, uint32_t channel, const void *ev, uint32_t 
     if (error_ != HARU_OK) return error_;
   }
   if (n > 0 && !ev) return HARU_EINVAL;
+  // a read uses at most its first serve_prefix events (HARU_MAX_READ_SAMPLES
+  // samples), so no chunk can contribute more: the rest is dropped here
+  // rather than copied, and a chunk larger than the staging budget is not
+  // refused as busy on every retry
+  n = std::min<uint32_t>(n, mode_ == 1 ? static_cast<uint32_t>(HARU_MAX_READ_SAMPLES) : static_cast<uint32_t>(prefix_));
   free_list(garbage_.exchange(nullptr, std::memory_order_acquire));
   const size_t cap = mode_ == 1 ? stage16_cap_ : stage_cap_;
   if (intake_events_.load() + host_events_.load() + n > cap * 4) return HARU_EBUSY;

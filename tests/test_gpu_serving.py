@@ -106,6 +106,34 @@ def test_flat_and_short_reads_are_rejected_alone(haru, ref):
         assert got[2].status == haru.HARU_EINVAL
         assert got[3].status == 0
         assert ctx.stream_poll(16, 1000) == []  # nothing pending: times out empty
+        # the serving loop keeps the reference it started with: replacing it
+        # is refused on the host, and serving goes on with the old one
+        for replace in (lambda: ctx.ref_load(ref[:1000]),
+                        lambda: ctx.ref_build(np.zeros(100, np.uint8), synth.pore_model(6), 6)):
+            with pytest.raises(haru.HaruError) as err:
+                replace()
+            assert err.value.code == haru.HARU_EBUSY
+        assert ctx.ref_length == ref.shape[0]
+        assert ctx.stream_submit(4, 3, good, time.monotonic_ns(), True) == 0
+        again = ctx.stream_poll(16, 10 ** 7)
+        assert [r.read_id for r in again] == [4]
+        assert again[0].cost == got[3].cost and again[0].end_col == got[3].end_col
+
+
+def test_oversized_chunk_is_cut_to_the_prefix(haru, ref):
+    """A chunk far larger than the staging budget (a whole read's events at
+    once, here with 8 slots) is accepted, and only its first serve_prefix
+    events are used: the decision equals that prefix aligned alone."""
+    q = synth.flowcell_schedule(1, 2.0, seed=7)[1].query(0)
+    chunk = np.concatenate([q, synth.random_signal(70_000, seed=13)]).astype(np.float32)
+    with haru.Context(serve_budget_bytes=8 * 1024) as ctx:
+        ctx.ref_load(ref)
+        assert ctx.stream_submit(1, 0, chunk, time.monotonic_ns(), True) == 0
+        got = ctx.stream_poll(16, 10 ** 7)
+        assert [r.read_id for r in got] == [1]
+        assert got[0].status == 0 and got[0].events == 250
+        c, j = ctx.sdtw_batch(haru.HARU_INT16, q[:250], np.array([0, 250], np.uint32))
+        assert got[0].cost == c[0] and got[0].end_col == j[0]
 
 
 def test_stage_counters_and_idle_sleeping_worker(haru, ref):
