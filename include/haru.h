@@ -93,7 +93,8 @@ typedef struct {
   float threshold;          /* accept iff cost <= threshold (z units; int16 compares floor(threshold * 2^k)) */
   int serve_precision;      /* HARU_FP32 or HARU_INT16 */
   size_t serve_budget_bytes;/* device memory for in-flight serving requests; 0 = 64 MiB */
-  uint32_t serve_max_batch; /* most requests launched together; 0 = 1024 */
+  uint32_t serve_max_batch; /* most requests launched together; 0 = 1024; at most the slots
+                               serve_budget_bytes gives (a batch holds admitted reads only) */
   uint32_t serve_prefix;    /* events per decision prefix; 0 = 250 (Section 4.1) */
   int units_target;         /* work units (query x reference segment) a batch is cut into, at least;
                                0 = 4 x SMs x warps_per_cta; 1 = never split the reference */
@@ -410,7 +411,10 @@ int haru_last_timing(haru_ctx *ctx, float *ms_prep, float *ms_sweep);
  * capture. Every call on every context of the process shares the one array
  * and it keeps the last call's contents: calls that overlap on the GPU (two
  * streams, two threads, two contexts on one device) race and must be
- * serialised by the caller. */
+ * serialised by the caller. The call reads the context's reference without
+ * holding the context for its whole run, so replacing the reference
+ * (haru_ref_load, haru_ref_build) from another thread during it races as
+ * well. */
 #define HARU_NOALLOC_MAX_QUERIES 1024
 int haru_sdtw_batch_noalloc(haru_ctx *ctx, int precision, const float *events, const uint32_t *offsets,
                             uint32_t nq, float *out_cost, int64_t *out_col, uintptr_t stream, uint32_t flags);

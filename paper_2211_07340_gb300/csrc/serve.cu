@@ -389,7 +389,6 @@ int Server::start(int mode) {
   prefix_ = c.serve_prefix ? static_cast<int>(c.serve_prefix) : 250;
   if (prefix_ < 1 || prefix_ > HARU_MAX_QUERY) return HARU_EINVAL;
   slot_len_ = (prefix_ + 31) / 32 * 32;
-  max_batch_ = c.serve_max_batch ? static_cast<int>(c.serve_max_batch) : 1024;
   spin_ns_ = c.serve_spin_us < 0 ? 0 : 1000ull * static_cast<uint64_t>(c.serve_spin_us ? c.serve_spin_us : 2000);
   precision_ = c.serve_precision == HARU_FP32 ? HARU_FP32 : HARU_INT16;
   threshold_ = c.threshold;
@@ -406,6 +405,9 @@ int Server::start(int mode) {
                           (mode_ == 1 ? static_cast<size_t>(HARU_MAX_READ_SAMPLES) * sizeof(int16_t) : 0);
   nslots_ = static_cast<int>(std::min<size_t>(budget / per_slot, 1u << 22));
   if (nslots_ < 1) return HARU_ENOMEM;
+  // a batch holds admitted reads, one per slot: never more than the slots
+  max_batch_ = static_cast<int>(
+      std::min<uint64_t>(c.serve_max_batch ? c.serve_max_batch : 1024u, static_cast<uint64_t>(nslots_)));
   lc_ = ctx_->launch_cfg();
   ref_ = ctx_->ref_view();
   stage_cap_ = static_cast<size_t>(std::max(nslots_, 64)) * slot_len_;

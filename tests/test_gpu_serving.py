@@ -126,7 +126,9 @@ def test_oversized_chunk_is_cut_to_the_prefix(haru, ref):
     events are used: the decision equals that prefix aligned alone."""
     q = synth.flowcell_schedule(1, 2.0, seed=7)[1].query(0)
     chunk = np.concatenate([q, synth.random_signal(70_000, seed=13)]).astype(np.float32)
-    with haru.Context(serve_budget_bytes=8 * 1024) as ctx:
+    # (a batch limit far above the 8 slots is cut to them: the loop does not
+    # reserve batch buffers for 10^8 requests)
+    with haru.Context(serve_budget_bytes=8 * 1024, serve_max_batch=10 ** 8) as ctx:
         ctx.ref_load(ref)
         assert ctx.stream_submit(1, 0, chunk, time.monotonic_ns(), True) == 0
         got = ctx.stream_poll(16, 10 ** 7)
