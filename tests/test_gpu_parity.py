@@ -96,6 +96,33 @@ def test_ragged_sizes_span_tiles(haru, tile, warps, stack):
     compare_fp32(c32, j32, ref, ev, off)
 
 
+@pytest.mark.parametrize("stack", [-1, 1])
+def test_every_query_length_1_to_512(haru, stack):
+    """One batch holding a query of every length 1..512 in shuffled order
+    (every strip height with every pad-row count; the short ones in stacked
+    strips when stacking is forced), on a reference of a few tiles with a
+    ragged tail: all four forms against the oracle."""
+    N = 6_007
+    ref = synth.random_signal(N, seed=21)
+    lengths = np.arange(1, haru.HARU_MAX_QUERY + 1)
+    np.random.default_rng(22).shuffle(lengths)
+    off = offsets_of(lengths)
+    ev = synth.random_signal(int(off[-1]), seed=23, scale=1.0, loc=0.0)
+    with haru.Context(stack_short=stack) as ctx:
+        ctx.ref_load(ref)
+        c16, j16 = ctx.sdtw_batch(haru.HARU_INT16, ev, off, raw=False)
+        c32, j32 = ctx.sdtw_batch(haru.HARU_FP32, ev, off, raw=False)
+        cw, jw = ctx.sdtw_batch(haru.HARU_INT16_ACC32, ev, off, raw=False)
+        cs, js, ss = ctx.sdtw_batch_span(haru.HARU_FP32, ev, off, raw=False)
+    compare_int16(c16, j16, ref, ev, off, normalize_q=False)
+    compare_fp32(c32, j32, ref, ev, off, normalize_q=False)
+    compare_int16(cw, jw, ref, ev, off, normalize_q=False, prec=oracle.PREC_I32)
+    np.testing.assert_array_equal(cs, c32)
+    np.testing.assert_array_equal(js, j32)
+    o = oracle.batch(oracle.PREC_F32, ref, ev, off, normalize_q=False, start=True)
+    np.testing.assert_array_equal(ss, o.start)
+
+
 def test_planted_copies_end_at_planted_column(haru):
     N = 5000
     ref = synth.random_signal(N, seed=8, scale=1.0, loc=0.0)  # z-values: within the int16 range at 2^6
