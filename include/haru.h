@@ -88,7 +88,9 @@ typedef struct {
                                or 12 (start-column batches run at most 8); other values = 8 */
   int tile_cols;            /* reference columns per shared-memory tile, 2048..16384; 0 = auto */
   int ctas_per_sm;          /* persistent CTAs per SM; 0 = as many as fit */
-  uint32_t wait_limit;      /* longest single device wait, microseconds, before HARU_ETIMEDOUT; 0 = 2 s */
+  uint32_t wait_limit;      /* longest single device wait, microseconds, before HARU_ETIMEDOUT; 0 = 2 s;
+                               values below 1000 act as 1000 (a timed-out CTA's drain of its copies in
+                               flight shares the limit and must outlast a tile copy) */
   /* serving */
   float threshold;          /* accept iff cost <= threshold (z units; int16 compares floor(threshold * 2^k)) */
   int serve_precision;      /* HARU_FP32 or HARU_INT16 */

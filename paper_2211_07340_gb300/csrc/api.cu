@@ -50,8 +50,12 @@ int pick_tile(const haru_config &cfg) {
   return t;
 }
 
+// At least 1 ms: a CTA whose wait ran out drains its reference copies still
+// in flight within the same limit before it exits, and a tile copy (at most
+// 67 KB) lands in microseconds, so the drain always outlasts it.
 unsigned long long wait_ns(const haru_config &cfg) {
-  return cfg.wait_limit ? static_cast<unsigned long long>(cfg.wait_limit) * 1000ull : 2000000000ull;
+  if (!cfg.wait_limit) return 2000000000ull;
+  return std::max<unsigned long long>(cfg.wait_limit, 1000ull) * 1000ull;
 }
 
 }  // namespace
